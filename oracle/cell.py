@@ -1,0 +1,280 @@
+"""One RF cell advanced by the phasor-PIC algorithm (Sec. 2.5, Fig.
+algorithm_workflow), plainly and in FP64 except for the particle step
+(float32 or float64, see oracle.particles).
+
+Time levels.  Global step s (0-based) takes positions x^s and potential phi^s
+(solved at t_s) to x^{s+1} and phi^{s+1}.  theta_s = 2 pi (s mod N_RF)/N_RF
+(Eq. et_reconstruct).  Cycle c runs steps s = c N_RF .. c N_RF + N_RF - 1:
+  * the current harmonics sample J_theta(t_s) (time-centred current at the
+    old positions) for s in the cycle;
+  * the turn charges sample Q_k(t_{s+1}) after each step's Poisson solve, so
+    the last sample of the cycle has theta = 0;
+  * both are projected with Eq. fourier (factor 2/N_RF).
+At the end of the cycle: two plasma-only Helmholtz solves (Eq.
+helmholtz_two_real), V_p (Eq. vpind), I_cap (Eq. icap), the sample-count check,
+powers (Eqs. pind, pcap, pcap_phasor, pport), the controller, the target
+network solve, relaxation (Eq. relaxation), residuals, and the composed field
+for the next cycle (Eq. compose).  phi at the cycle boundary is then re-solved
+with the new turn potentials so the first step of the next cycle sees them.
+"""
+import math
+import numpy as np
+
+from .constants import EPS0, MU0, QE, ME, M_AR, KB
+from .grid import CellGeometry
+from . import fields, circuit, particles
+
+
+class OracleCell:
+    def __init__(self, cfg, weights):
+        self.cfg = cfg
+        self.geo = CellGeometry(cfg)
+        g = self.geo.grid
+        self.g = g
+        self.omega = 2 * math.pi * cfg.freq
+        self.n_rf = int(round(1.0 / (cfg.freq * cfg.dt)))
+        if abs(cfg.freq * cfg.dt * self.n_rf - 1.0) >= 1e-10:      # Eq. phaseclosure
+            raise ValueError("phase closure violated")
+        self.N = self.geo.n_turns
+        # --- Poisson ----------------------------------------------------------
+        self.pdir = self.geo.poisson_dirichlet()
+        self.poisson = fields.PoissonSolver(g, self.pdir)
+        # --- Helmholtz, unit fields, Z_vac -------------------------------------
+        k2 = None
+        if cfg.full_helmholtz:
+            k2 = MU0 * EPS0 * self.omega ** 2 * self.geo.eps_node
+        self.helm = fields.HelmholtzSolver(g, k2)
+        self.U = fields.unit_fields(self.helm, self.geo.gk, self.omega)
+        self.zvac, self.eps_rec = fields.vacuum_impedance(g, self.geo.gk, self.U)
+        # --- circuit ------------------------------------------------------------
+        if cfg.r_rf_override >= 0:
+            self.r_rf = np.full(self.N, cfg.r_rf_override)
+        else:
+            self.r_rf = circuit.skin_resistance(cfg.turn_r, cfg.wire_radius, self.omega,
+                                                cfg.rho20, cfg.alpha_cu, cfg.t_coil_c)
+        self.zs = circuit.z_source(cfg.r_g, cfg.r_m, cfg.l_m, cfg.c_m, self.omega)
+        self.zturn = self.zvac + np.diag(self.r_rf)
+        self.c_stray = np.asarray(cfg.c_stray[:self.N], dtype=float)
+        self.A = circuit.network_matrix(self.zs, self.zturn, self.c_stray, self.omega)
+        self.vg_amp = cfg.v_g
+        self.vg = cfg.v_g * complex(math.cos(cfg.phase_g), math.sin(cfg.phase_g))
+        self.ctrl = None
+        if cfg.power_control:
+            self.ctrl = circuit.PowerController(cfg.p_target, cfg.gamma, cfg.n_trend, cfg.eps_p,
+                                                cfg.alpha_v, cfg.f_step, cfg.v_min, cfg.v_max)
+        # x^1: zero-load network solution
+        zeros = np.zeros(self.N, complex)
+        self.x = circuit.solve_target(self.A, self.vg, zeros, zeros)
+        self.Ecp = np.zeros((g.NZ, g.NR))
+        self.Essp = np.zeros((g.NZ, g.NR))
+        self._compose()
+        # --- particles ----------------------------------------------------------
+        self.weights = weights
+        self.P = [None, None]
+        self.next_uid = [0, 0]
+        self.window_q = np.zeros((g.NZ, g.NR))
+        self.s = 0
+        self.phi = np.zeros((g.NZ, g.NR))
+        self._reset_accumulators()
+        self.records = []
+
+    # ------------------------------------------------------------------------
+    def set_particles(self, sp, cell, dr, dz, vr, vt, vz, uid):
+        self.P[sp] = dict(cell=np.asarray(cell, np.int64).copy(), dr=np.array(dr), dz=np.array(dz),
+                          vr=np.array(vr), vt=np.array(vt), vz=np.array(vz),
+                          uid=np.asarray(uid, np.int64).copy())
+        self.next_uid[sp] = int(np.max(uid)) + 1 if len(uid) else 0
+
+    def theta(self, s):
+        return 2.0 * math.pi * (s % self.n_rf) / self.n_rf
+
+    def turn_potentials(self, th):
+        V = self.x[1 + self.N:]
+        return V.real * math.cos(th) + (-V.imag) * math.sin(th)      # Eq. dirichlet
+
+    def dirichlet_values(self, th):
+        vals = np.zeros((self.g.NZ, self.g.NR))
+        phik = self.turn_potentials(th)
+        for k, nodes in enumerate(self.geo.turn_nodes):
+            for (i, j) in nodes:
+                vals[i, j] = phik[k]
+        return vals
+
+    def deposit_charge(self, T):
+        """Q at the current positions (used once before the first step)."""
+        Q = np.zeros((self.g.NZ, self.g.NR))
+        for sp in (0, 1):
+            P = self.P[sp]
+            sc = particles.SpeciesConstants(self.cfg, sp, self.weights[sp], T)
+            live = P['cell'] >= 0
+            cell = P['cell'][live]
+            ir, iz = cell % self.cfg.nr, cell // self.cfg.nr
+            w = particles.bilinear(P['dr'][live].astype(T), P['dz'][live].astype(T), T)
+            for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), w):
+                np.add.at(Q, (iz + di, ir + dj), (sc.qw * wk).astype(np.float64))
+        return Q
+
+    def prime(self, T=np.float32):
+        """phi^0 from the initial positions and theta_0."""
+        Q = self.deposit_charge(T)
+        self.phi = self.poisson.solve(Q + self.window_q, self.dirichlet_values(self.theta(0)))
+
+    # ------------------------------------------------------------------------
+    def node_fields(self, th, T):
+        """Per-cell corner fields for the gather at phase th: E_r, E_z from phi;
+        E_theta = E_c cos - E_s^sto sin (Eq. et_reconstruct); B from Faraday."""
+        g = self.g
+        Er, Ez = fields.efield_from_phi(g, self.phi)
+        c, s = math.cos(th), math.sin(th)
+        Et = self.Ec * c - self.Ess * s
+        Br = self.Brc * c + self.Brs * s
+        Bz = self.Bzc * c + self.Bzs * s
+        if not self.cfg.magnetic_force:
+            Br = np.zeros_like(Br)
+            Bz = np.zeros_like(Bz)
+        nr, iw = self.cfg.nr, self.geo.i_win
+        F = np.zeros((iw * nr, 5, 4), T)
+        for comp, f in enumerate((Er, Ez, Et, Br, Bz)):
+            f32 = f.astype(T)
+            F[:, comp, 0] = f32[:iw, :nr].ravel()
+            F[:, comp, 1] = f32[:iw, 1:nr + 1].ravel()
+            F[:, comp, 2] = f32[1:iw + 1, :nr].ravel()
+            F[:, comp, 3] = f32[1:iw + 1, 1:nr + 1].ravel()
+        return F
+
+    def step(self, T=np.float32):
+        """One PIC step; returns per-step information."""
+        cfg, g = self.cfg, self.g
+        s = self.s
+        th_old = self.theta(s)
+        F = self.node_fields(th_old, T)
+        Q = np.zeros((g.NZ, g.NR))
+        J = np.zeros((g.NZ, g.NR))
+        stats = dict(p_ind=0.0, p_es=0.0, absorbed=0, pushed=0, nu_viol=0,
+                     coll=np.zeros((2, 3), np.int64))
+        events = []
+        for sp in (0, 1):
+            sc = particles.SpeciesConstants(cfg, sp, self.weights[sp], T)
+            ev = particles.push_species(self.P[sp], F, sc, self.geo, s, cfg.seed, T,
+                                        Q, J, self.window_q, stats)
+            events.extend(ev)
+        self._append(events, T)
+        # Poisson at t_{s+1}
+        th_new = self.theta(s + 1)
+        dv = self.dirichlet_values(th_new)
+        self.phi = self.poisson.solve(Q + self.window_q, dv)
+        Qk = fields.turn_charge(g, self.phi, self.geo.turn_nodes)
+        Vk = self.turn_potentials(th_new)
+        # accumulations (Eq. fourier, Eq. pind, Eq. pcap samples)
+        N = self.n_rf
+        with np.errstate(divide='ignore', invalid='ignore'):
+            Jd = np.where(self.geo.vol > 0, J / np.where(self.geo.vol > 0, self.geo.vol, 1.0), 0.0)
+        self.Jc += (2.0 / N) * Jd * math.cos(th_old)
+        self.Js += (2.0 / N) * Jd * math.sin(th_old)
+        self.Qc += (2.0 / N) * Qk * math.cos(th_new)
+        self.Qs += (2.0 / N) * Qk * math.sin(th_new)
+        self.p_ind += stats['p_ind'] / N
+        self.p_es += stats['p_es'] / N
+        self.samples_V.append(Vk)
+        self.samples_Q.append(Qk)
+        self.n_samples += 1
+        self.pushed += stats['pushed']
+        self.coll += stats['coll']
+        self.absorbed += stats['absorbed']
+        self.created += len(events)
+        self.s += 1
+        self.Q_last = Q
+        info = dict(stats=stats, events=len(events), Q=Q, J=J, Qk=Qk)
+        if self.s % N == 0:
+            info['record'] = self.period_end()
+        return info
+
+    def _append(self, events, T):
+        events = sorted(events, key=lambda e: e['parent'])
+        if not events:
+            return
+        n = len(events)
+        for sp in (0, 1):
+            P = self.P[sp]
+            uid0 = self.next_uid[sp]
+            new = dict(cell=np.array([e['cell'] for e in events], np.int64),
+                       dr=np.array([e['dr'] for e in events], T),
+                       dz=np.array([e['dz'] for e in events], T),
+                       vr=np.array([(e['ve'] if sp == 0 else e['vi'])[0] for e in events], T),
+                       vt=np.array([(e['ve'] if sp == 0 else e['vi'])[1] for e in events], T),
+                       vz=np.array([(e['ve'] if sp == 0 else e['vi'])[2] for e in events], T),
+                       uid=np.arange(uid0, uid0 + n, dtype=np.int64))
+            for key in P:
+                P[key] = np.concatenate([P[key], new[key].astype(P[key].dtype)])
+            self.next_uid[sp] = uid0 + n
+
+    # ------------------------------------------------------------------------
+    def _reset_accumulators(self):
+        g = self.g
+        self.Jc = np.zeros((g.NZ, g.NR))
+        self.Js = np.zeros((g.NZ, g.NR))
+        self.Qc = np.zeros(self.N)
+        self.Qs = np.zeros(self.N)
+        self.p_ind = 0.0
+        self.p_es = 0.0
+        self.samples_V = []
+        self.samples_Q = []
+        self.n_samples = 0
+        self.pushed = 0
+        self.coll = np.zeros((2, 3), np.int64)
+        self.absorbed = 0
+        self.created = 0
+
+    def _compose(self):
+        """Eq. compose with I_k = I_c - i I_s, and the B phasors."""
+        I = self.x[1:1 + self.N]
+        self.Ec = self.Ecp + np.tensordot(-I.imag, self.U, axes=1)
+        self.Ess = self.Essp + np.tensordot(I.real, self.U, axes=1)
+        self.Brc, self.Brs, self.Bzc, self.Bzs = fields.b_phasors(self.g, self.Ec, self.Ess,
+                                                                  self.omega)
+
+    def period_end(self):
+        cfg, N = self.cfg, self.N
+        # plasma-only Helmholtz solves (Eq. helmholtz_two_real)
+        rhs_c = MU0 * self.omega * self.Js
+        rhs_s = MU0 * self.omega * self.Jc
+        Ecp = self.helm.solve(rhs_c)
+        Essp = self.helm.solve(rhs_s)
+        vp = -(fields.project(self.g, self.geo.gk, Ecp) +
+               1j * fields.project(self.g, self.geo.gk, Essp))          # Eq. vpind
+        qhat = self.Qc - 1j * self.Qs
+        icap = 1j * self.omega * qhat                                     # Eq. icap
+        accepted = self.n_samples == self.n_rf
+        x_app = self.x.copy()
+        p_port = circuit.port_power(x_app, N)
+        p_cu = circuit.copper_power(x_app, N, self.r_rf)
+        p_cap, W = circuit.cap_power_trapezoid(np.array(self.samples_V), np.array(self.samples_Q),
+                                               cfg.freq)
+        p_cap_ph = circuit.cap_power_phasor(x_app, N, icap)
+        vg_applied = self.vg_amp
+        rec = dict(period=self.s // self.n_rf - 1, n_samples=self.n_samples, accepted=accepted,
+                   vp=vp, icap=icap, qhat=qhat, x_applied=x_app, vg=vg_applied,
+                   p_port=p_port, p_cu=p_cu, p_cap=p_cap, p_cap_ph=p_cap_ph,
+                   p_ind=self.p_ind, p_es=self.p_es, pushed=self.pushed,
+                   coll=self.coll.copy(), absorbed=self.absorbed, created=self.created,
+                   n_live=[int(np.count_nonzero(self.P[sp]['cell'] >= 0)) for sp in (0, 1)])
+        rec['eps_bal'] = abs(p_port - (self.p_ind + p_cap + p_cu)) / max(abs(p_port), 1e-300)
+        if accepted:
+            if self.ctrl is not None:
+                self.vg_amp = self.ctrl.update(self.vg_amp, p_port)
+                self.vg = self.vg_amp * complex(math.cos(cfg.phase_g), math.sin(cfg.phase_g))
+            xt = circuit.solve_target(self.A, self.vg, icap, vp)
+            self.x = (1.0 - cfg.alpha) * self.x + cfg.alpha * xt
+            rec['x_target'] = xt
+            self.Ecp, self.Essp = Ecp, Essp
+            self._compose()
+        rec['x_next'] = self.x.copy()
+        rec['vg_next'] = self.vg_amp
+        rec['r_kcl'], rec['r_kvl'] = circuit.residuals(self.x, self.zs, self.zturn, self.c_stray,
+                                                       self.omega, self.vg, icap, vp)
+        self._reset_accumulators()
+        # phi at the cycle boundary with the new turn potentials
+        self.phi = self.poisson.solve(self.Q_last + self.window_q,
+                                      self.dirichlet_values(self.theta(self.s)))
+        self.records.append(rec)
+        return rec
