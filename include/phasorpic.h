@@ -1,0 +1,297 @@
+/*
+ * phasorpic.h -- C ABI of libphasorpic.so, the B300 (sm_103a) hot path of the
+ * phasor-PIC coil-circuit coupling for inductively coupled plasmas
+ * (arXiv 2609.15043).
+ *
+ * One pp_cell is one axisymmetric (r, z) argon RF cell: an explicit PIC/MCC
+ * particle population (electrons and Ar+), its electrostatic Poisson problem
+ * with equipotential coil turns, the azimuthal phasor field of the coil and
+ * plasma currents, and the turn-resolved coil circuit that is updated once per
+ * RF period (Sec. 2.5, Fig. algorithm_workflow).
+ *
+ * Conventions (Sec. 2.1, Eq. phasor): exp(+i w t), peak phasors,
+ * X = X_c - i X_s.  Complex numbers cross the ABI as interleaved (re, im)
+ * doubles.  Circuit unknowns are ordered x = (I_f, I_1..I_N, V_1..V_N)
+ * (Eq. unknowns), 2N+1 complex values.
+ *
+ * Memory: the library allocates and owns all device memory of a cell
+ * (cudaMalloc in pp_init_cell, cudaFree in pp_destroy).  Every pointer
+ * argument of this header is a HOST pointer owned by the caller unless stated
+ * otherwise; the library never keeps it after the call returns.  `stream` is
+ * a cudaStream_t passed as void* (NULL = the legacy default stream); calls
+ * that take a stream enqueue work and return without waiting for it, calls
+ * that return data synchronise that stream first.
+ *
+ * Errors: every int-returning function returns PP_OK (0) or a negative PP_E_*
+ * code; pp_last_error() gives a one-line description (thread-local).  No call
+ * aborts, traps or waits without bound on the GPU: device-side failures
+ * (solver cap reached, event buffer full, sample count wrong) are recorded in
+ * a device status word that pp_get_status() returns.
+ */
+#ifndef PHASORPIC_H
+#define PHASORPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PP_MAX_TURNS 8
+#define PP_NSPECIES 2            /* 0 = electrons, 1 = Ar+ */
+
+#define PP_OK 0
+#define PP_E_CONFIG (-1)         /* invalid configuration: phase closure (Eq. phaseclosure),
+                                    shape normalisation (Eq. shape), geometry off grid lines */
+#define PP_E_NOCONV (-2)         /* a field solve hit its iteration cap */
+#define PP_E_SAMPLES (-3)        /* sample count != N_RF: circuit update rejected (Sec. 2.3) */
+#define PP_E_NAN (-4)            /* non-finite value in an uploaded array */
+#define PP_E_TIMEOUT (-5)        /* a bounded device wait expired */
+#define PP_E_CUDA (-6)           /* a CUDA runtime call failed */
+#define PP_E_ARG (-7)            /* bad argument (NULL pointer, index or size out of range) */
+#define PP_E_CAPACITY (-8)       /* particle or event storage exhausted */
+
+/* device status bits returned by pp_get_status */
+#define PP_ST_NOCONV 1u          /* Poisson refinement did not reach its tolerance */
+#define PP_ST_EVENTS 2u          /* ionisation events dropped (per-step event buffer full) */
+#define PP_ST_CAPACITY 4u        /* new particles dropped (particle capacity full) */
+#define PP_ST_SAMPLES 8u         /* a period ended with a wrong sample count */
+
+/*
+ * Cell configuration.  Plain data; every length in metres, time in seconds.
+ * Geometry (the readings of the paper's silent points): grounded electrode at
+ * z = 0, grounded side wall at r = r_max, grounded lid at z = z_max, a
+ * dielectric slab of relative permittivity eps_win over z_win_lo..z_win_hi on
+ * the full radius, and n_turns coil turns of wire radius wire_radius centred at
+ * (turn_r[k], z_coil) in the particle-free compartment above the slab.  nr, nz
+ * are CELL counts; z_win_lo, z_win_hi must lie on grid lines.  Particles live
+ * in 0 <= z < z_win_lo.
+ */
+typedef struct pp_config {
+    int32_t nr, nz;                  /* cells in r and z */
+    double r_max, z_max;
+    double z_win_lo, z_win_hi, eps_win, z_coil;
+    int32_t n_turns;
+    int32_t winding[PP_MAX_TURNS];   /* s_k = +-1 (Eq. shape) */
+    double turn_r[PP_MAX_TURNS];
+    double wire_radius;
+    double freq, dt;                 /* N_RF = nint(1/(f dt)) (Eq. nrf) */
+    int32_t full_helmholtz;          /* 1: keep mu0 eps0 eps_r w^2 (Eq. helmholtz_op); 0: MQS */
+    int32_t magnetic_force;          /* 1: RF B from Faraday's law acts in the push */
+    double pressure_pa, t_gas;       /* neutral argon background */
+    /* circuit (Sec. 2.4) */
+    double r_g, r_m, l_m, c_m;       /* Eq. zsource; C term dropped when c_m <= 0 */
+    double c_stray[PP_MAX_TURNS];    /* Eq. stray */
+    double rho20, alpha_cu, t_coil_c;/* Eq. skin (copper, temperature corrected) */
+    double r_rf_override;            /* >= 0: R_rf,k = this value for every turn */
+    double v_g, phase_g;             /* initial Thevenin peak amplitude and phase */
+    int32_t power_control;           /* 1: Eqs. pfilter, ptrend, pcontrol */
+    double p_target, gamma, n_trend, eps_p, alpha_v, f_step, v_min, v_max;
+    double alpha;                    /* relaxation factor (Eq. relaxation) */
+    /* particles */
+    double weight[PP_NSPECIES];      /* physical particles per macroparticle */
+    int64_t capacity[PP_NSPECIES];   /* macroparticle storage per species */
+    uint64_t seed;                   /* Philox key of the MCC draws */
+    int32_t sort_every[PP_NSPECIES]; /* steps between counting sorts (>= 1) */
+    int32_t poisson_max_iter;        /* FP64 refinement sweeps per step (>= 1) */
+    double poisson_tol;              /* relative FP64 residual target */
+} pp_config;
+
+/* Completed-period record (Sec. 2.4 diagnostics; Eqs. vpind, icap, pport,
+ * pind, pcap, pcap_phasor, power_imbalance, kclres, kvlres). */
+typedef struct pp_period_record {
+    int64_t period;                  /* 0-based index of the completed RF period */
+    int32_t n_samples;               /* turn-charge samples taken (must equal N_RF) */
+    int32_t accepted;                /* 1: circuit updated; 0: update rejected */
+    int32_t n_turns, pad0;
+    double vp[2 * PP_MAX_TURNS];     /* plasma back-emf V_p,k (complex) */
+    double icap[2 * PP_MAX_TURNS];   /* displacement current I_cap,k = i w Q_k */
+    double qhat[2 * PP_MAX_TURNS];   /* turn-charge phasor Q_k */
+    double x_applied[2 * (2 * PP_MAX_TURNS + 1)];  /* state applied in this period */
+    double x_next[2 * (2 * PP_MAX_TURNS + 1)];     /* state for the next period */
+    double vg, vg_next;              /* source amplitude applied / next */
+    double p_port, p_ind, p_cap, p_cap_ph, p_cu, p_es, eps_bal;
+    double r_kcl, r_kvl;             /* max normalised KCL / KVL residuals */
+    double particle_steps;           /* live particles pushed summed over the period's steps */
+    int64_t n_live[PP_NSPECIES];
+    int64_t coll[PP_NSPECIES][3];    /* e: elastic, excitation, ionisation; i: cx, isotropic, - */
+    int64_t absorbed, created, nu_violations;
+} pp_period_record;
+
+typedef struct pp_cell pp_cell;
+
+/* sizeof checks for bindings */
+int32_t pp_config_size(void);
+int32_t pp_record_size(void);
+
+/*
+ * pp_init_cell -- Sec. 2.5 initialisation: validates cfg (Eq. phaseclosure,
+ * Eq. shape normalisation, grid lines), builds the turn node sets, solves the
+ * N unit-current Helmholtz problems K U_k = g_k (Eq. unitfield) in FP64,
+ * projects Z_vac (Eq. zvac) and eps_rec (Eq. reciprocity), computes R_rf
+ * (Eq. skin), assembles the network (Eq. blockmatrix), solves the zero-load
+ * state x^1, and composes the first-cycle field (Eq. compose).  Allocates all
+ * device storage (particles: cfg->capacity per species, empty).  Uses the
+ * current CUDA device.  *out receives the handle (NULL on error).
+ */
+int pp_init_cell(const pp_config* cfg, pp_cell** out);
+
+/* pp_destroy -- frees every device allocation of the cell; NULL is a no-op. */
+int pp_destroy(pp_cell* cell);
+
+/* Thread-local text of the last error. */
+const char* pp_last_error(void);
+
+/*
+ * pp_set_particles -- replaces the population of one species with n
+ * macroparticles given as host SoA arrays: cell = iz*nr + ir, offsets dr, dz in
+ * [0, 1) inside the cell, velocities (vr, vtheta, vz) in m/s, unique uid.  The
+ * library sorts them by cell.  Returns PP_E_CAPACITY if n > capacity,
+ * PP_E_ARG if a cell index is outside the plasma region, PP_E_NAN on a
+ * non-finite value.  Synchronous.
+ */
+int pp_set_particles(pp_cell* cell, int species, int64_t n, const uint32_t* cell_idx,
+                     const float* dr, const float* dz, const float* vr, const float* vt,
+                     const float* vz, const uint32_t* uid);
+
+/*
+ * pp_get_particles -- copies the live macroparticles of one species (absorbed
+ * ones dropped, order unspecified) to host arrays of length `cap`; *n gets the
+ * count.  PP_E_CAPACITY if cap is too small.  Synchronises `stream`.
+ */
+int pp_get_particles(pp_cell* cell, int species, int64_t cap, int64_t* n, uint32_t* cell_idx,
+                     float* dr, float* dz, float* vr, float* vt, float* vz, uint32_t* uid,
+                     void* stream);
+
+/*
+ * pp_prime -- deposits the charge of the current populations and solves the
+ * Poisson problem at theta of the current step, so the next step gathers a
+ * consistent field.  Enqueued on `stream`.  Called implicitly by the first
+ * pp_advance_* after pp_set_particles.
+ */
+int pp_prime(pp_cell* cell, void* stream);
+
+/*
+ * pp_advance_steps -- advances n_steps PIC steps (Sec. 2.5): per step the
+ * field reconstruction at theta_n (Eq. et_reconstruct, Eq. dirichlet), the
+ * fused gather / cylindrical Boris push / boundary / null-collision MCC /
+ * deposition kernel, the append of ionisation products, the Poisson solve
+ * with equipotential turns, the Gauss-law turn charge (Eq. facecharge) and the
+ * harmonic and power accumulations (Eqs. fourier, pind, pcap).  When a step
+ * completes an RF period the period end runs on the device: two plasma-only
+ * Helmholtz solves (Eq. helmholtz_two_real), V_p (Eq. vpind), I_cap
+ * (Eq. icap), the sample-count check, powers, controller, target network
+ * solve, relaxation, residuals and the composed field for the next period.
+ * Enqueued on `stream`; control never returns to the host inside the call's
+ * device work.
+ */
+int pp_advance_steps(pp_cell* cell, int n_steps, void* stream);
+
+/* pp_advance_period -- n_periods whole RF periods; PP_E_ARG unless the cell
+ * sits on a period boundary. */
+int pp_advance_period(pp_cell* cell, int n_periods, void* stream);
+
+/*
+ * pp_set_circuit_state -- overwrites the applied circuit state x (2(2N+1)
+ * doubles, interleaved complex) and the source amplitude vg (peak volts),
+ * recomposes the azimuthal field with the current plasma-only part
+ * (Eq. compose).  Copies 16(2N+1) + 8 bytes host to device.  Synchronous.
+ */
+int pp_set_circuit_state(pp_cell* cell, const double* x, double vg);
+
+/* pp_get_circuit_state -- reads x (2(2N+1) doubles) and vg; synchronises `stream`. */
+int pp_get_circuit_state(pp_cell* cell, double* x, double* vg, void* stream);
+
+/*
+ * pp_get_turn_phasors -- the record of the most recently completed period
+ * (V_p, I_cap, Q, applied/next state, powers, residuals, counters).
+ * Copies sizeof(pp_period_record) + 4 bytes device to host.  PP_E_ARG if no
+ * period has completed.  Synchronises `stream`.
+ */
+int pp_get_turn_phasors(pp_cell* cell, pp_period_record* out, void* stream);
+
+/*
+ * pp_get_vacuum_impedance -- Z_vac (N*N complex, row-major, Eq. zvac), the
+ * reciprocity error (Eq. reciprocity) and R_rf,k (Eq. skin) computed at init.
+ * Any output pointer may be NULL.
+ */
+int pp_get_vacuum_impedance(pp_cell* cell, double* zvac, double* eps_rec, double* r_rf);
+
+/* Node grids (FP64, (nz+1)*(nr+1), row-major in z) readable by pp_get_grid. */
+#define PP_GRID_PHI 0            /* electrostatic potential of the last solve */
+#define PP_GRID_EC 1             /* composed E_c */
+#define PP_GRID_ESS 2            /* composed stored sine array E_s^(sto) = -E_s */
+#define PP_GRID_JC 3             /* running cosine harmonic of J_theta (A/m^2) */
+#define PP_GRID_JS 4             /* running sine harmonic of J_theta */
+#define PP_GRID_WINDOW 5         /* permanent window surface charge (C) */
+#define PP_GRID_CHARGE 6         /* charge deposited in the last step (C) */
+#define PP_GRID_JMOM 7           /* q w vbar_theta deposited in the last step (A m) */
+#define PP_GRID_U0 16            /* unit field U_k is PP_GRID_U0 + k */
+
+int pp_get_grid(pp_cell* cell, int which, double* host, int64_t n, void* stream);
+
+/* pp_set_potential -- overwrites phi (FP64 node grid); used to start two
+ * implementations from the same field.  Synchronous. */
+int pp_set_potential(pp_cell* cell, const double* phi);
+
+/*
+ * pp_poisson_solve -- standalone Poisson solve on the cell's geometry
+ * (Eq. poisson with chi = 0, Eq. epseff, Eq. axis_electrostatic_bc): node
+ * charges q (C, (nz+1)*(nr+1)), turn potentials turn_phi[N]; writes phi (node
+ * grid) and the Gauss-law turn charges qk[N] (Eq. facecharge).  Any output
+ * may be NULL.  *iters gets the refinement sweeps used, *rel_res the final
+ * relative FP64 residual.  Synchronous.  Does not change the cell's state.
+ */
+int pp_poisson_solve(pp_cell* cell, const double* q, const double* turn_phi, double* phi,
+                     double* qk, int* iters, double* rel_res);
+
+/*
+ * pp_helmholtz_solve -- standalone FP64 solve of L E = rhs (Eq. helmholtz_op,
+ * E = 0 on the axis and outer boundary, Eq. axis_inductive_bc) on the cell's
+ * grid; rhs and e are node grids.  Synchronous.
+ */
+int pp_helmholtz_solve(pp_cell* cell, const double* rhs, double* e);
+
+/* pp_get_status -- device status bits (PP_ST_*) accumulated since init;
+ * synchronises `stream`. */
+int pp_get_status(pp_cell* cell, uint32_t* status, void* stream);
+
+/* pp_get_counters -- cumulative counters: [0] particle steps, [1] absorbed,
+ * [2] created pairs, [3..5] electron elastic/excitation/ionisation,
+ * [6..7] ion cx/isotropic, [8] nu_max violations, [9] steps done, [10] live e,
+ * [11] live ions.  out has 12 entries.  Synchronises `stream`. */
+int pp_get_counters(pp_cell* cell, int64_t* out, void* stream);
+
+/*
+ * pp_get_poisson_stats -- diagnostics of the most recent Poisson solve: *sweeps
+ * gets the FP64 residual evaluations made (refinement sweeps + 1) and rel[k]
+ * (16 entries) the relative residual max|b - A phi| / max(|b| + sum|A_ij phi_j|)
+ * before sweep k (turn nodes contribute their Dirichlet mismatch).
+ * Synchronises `stream`.
+ */
+int pp_get_poisson_stats(pp_cell* cell, int* sweeps, double* rel, void* stream);
+
+/*
+ * pp_set_profiling -- when enable != 0 every later step records CUDA events on
+ * its stream around five phases: [0] the fused particle kernel, [1] the
+ * Poisson refinement, [2] counting sorts, [3] the other per-step kernels,
+ * [4] the period end.  pp_get_phase_times sums the recorded intervals (ms,
+ * 5 entries; counts: intervals per phase, may be NULL) and clears them; it
+ * waits for the recorded events.
+ */
+int pp_set_profiling(pp_cell* cell, int enable);
+int pp_get_phase_times(pp_cell* cell, double* ms, int64_t* counts);
+
+/* pp_launch_count -- kernels launched by the library in this process. */
+int64_t pp_launch_count(void);
+
+/* pp_n_rf -- steps per RF period; pp_step_index -- steps completed. */
+int pp_n_rf(pp_cell* cell);
+int64_t pp_step_index(pp_cell* cell);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHASORPIC_H */

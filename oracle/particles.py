@@ -208,13 +208,13 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     vt2 = np.where(rp > zero, ca * vny - sa * vnx, vny).astype(T)
     drn = dr + delta
     dzn = dz + c
-    kr = np.floor(drn)
+    kr = np.clip(np.floor(drn), T(-1048576.0), T(1048576.0))     # beyond this: outside anyway
     drn = (drn - kr).astype(T)
     ir2 = ir + kr.astype(np.int64)
     fix = drn >= one
     drn = np.where(fix, drn - one, drn).astype(T)
     ir2 = ir2 + fix
-    kz = np.floor(dzn)
+    kz = np.clip(np.floor(dzn), T(-1048576.0), T(1048576.0))
     dzn = (dzn - kz).astype(T)
     iz2 = iz + kz.astype(np.int64)
     fix = dzn >= one

@@ -1,0 +1,490 @@
+// Field kernels: separable direct solver (radial generalised eigenbasis x
+// tridiagonal in z), the Poisson FP64 residual refinement with a capacitance
+// correction for the equipotential turn nodes, the Helmholtz FP64 solve, node
+// fields for the gather, turn charges and the per-step harmonic accumulation.
+#include "pp_internal.h"
+
+#include <cmath>
+
+namespace pp {
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double kahan_add(double& sum, double& comp, double v) {
+    double y = v - comp;
+    double t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+    return t;
+}
+
+// ---------------------------------------------------------------- GEMM
+// C[rows x N] = A[rows x K] * B[K x N], row-major, 32x32 tiles.
+template <typename T>
+__global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
+                        int rows, int K, int N, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ T As[32][33];
+    __shared__ T Bs[32][33];
+    int tx = threadIdx.x, ty = threadIdx.y;          // 32 x 8
+    int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    T acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int q = 0; q < 4; ++q) {
+            int r = ty + 8 * q;
+            As[r][tx] = (r0 + r < rows && k0 + tx < K) ? A[(size_t)(r0 + r) * K + k0 + tx] : T(0);
+            Bs[r][tx] = (k0 + r < K && c0 + tx < N) ? B[(size_t)(k0 + r) * N + c0 + tx] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            T b = Bs[k][tx];
+            for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * b;
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        int r = r0 + ty + 8 * q, cc = c0 + tx;
+        if (r < rows && cc < N) C[(size_t)r * N + cc] = acc[q];
+    }
+}
+
+// Thomas sweep per mode with precomputed factors.  A block takes MB modes:
+// all of their rows of f, c' and 1/denominator are staged in shared memory
+// with coalesced row loads, one warp runs the two dependent recurrences out of
+// shared memory (one lane per mode), and the result is written back row-wise.
+template <typename T>
+__global__ void tri_solve(const T* __restrict__ f, T* __restrict__ x, const T* __restrict__ cp,
+                          const T* __restrict__ invd, const T* __restrict__ lo, int rows, int M, int MB,
+                          const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    T* sf = reinterpret_cast<T*>(smem_raw);          // rows x MB
+    T* sc = sf + (size_t)rows * MB;
+    T* sd = sc + (size_t)rows * MB;
+    T* sl = sd + (size_t)rows * MB;                  // rows
+    const int m0 = blockIdx.x * MB;
+    const int nm = min(MB, M - m0);
+    for (int q = threadIdx.x; q < rows * MB; q += blockDim.x) {
+        int i = q / MB, mm = q % MB;
+        if (mm < nm) {
+            size_t k = (size_t)i * M + m0 + mm;
+            sf[q] = f[k];
+            sc[q] = cp[k];
+            sd[q] = invd[k];
+        }
+    }
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) sl[i] = lo[i];
+    __syncthreads();
+    if (threadIdx.x < nm) {
+        const int mm = threadIdx.x;
+        T y = 0;
+        for (int i = 0; i < rows; ++i) {
+            y = (sf[i * MB + mm] - sl[i] * y) * sd[i * MB + mm];
+            sf[i * MB + mm] = y;
+        }
+        T xn = sf[(rows - 1) * MB + mm];
+        for (int i = rows - 2; i >= 0; --i) {
+            xn = sf[i * MB + mm] - sc[i * MB + mm] * xn;
+            sf[i * MB + mm] = xn;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < rows * MB; q += blockDim.x) {
+        int i = q / MB, mm = q % MB;
+        if (mm < nm) x[(size_t)i * M + m0 + mm] = sf[q];
+    }
+}
+
+template <typename T>
+static int tri_modes_per_block(int rows) {
+    // 3 row arrays per mode in at most ~200 KB of shared memory
+    int mb = 32;
+    while (mb > 1 && (size_t)(3 * mb + 1) * rows * sizeof(T) > 200 * 1024) mb >>= 1;
+    return mb;
+}
+
+template <typename T>
+void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, const int* skip) {
+    dim3 blk(32, 8), grd((s.M + 31) / 32, (s.rows + 31) / 32);
+    gemm_rm<T><<<grd, blk, 0, st>>>(rhs, s.Vf, s.t0, s.rows, s.M, s.M, skip);
+    int mb = tri_modes_per_block<T>(s.rows);
+    size_t shm = (size_t)(3 * mb + 1) * s.rows * sizeof(T);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        cudaFuncSetAttribute(tri_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set[sizeof(T) == 8] = true;
+    }
+    tri_solve<T><<<(s.M + mb - 1) / mb, 256, shm, st>>>(s.t0, s.t1, s.cp, s.invd, s.lo, s.rows, s.M, mb, skip);
+    gemm_rm<T><<<grd, blk, 0, st>>>(s.t1, s.Vb, out, s.rows, s.M, s.M, skip);
+    count_launch(3);
+}
+template void sep_solve<float>(const SepSolver<float>&, const float*, float*, cudaStream_t, const int*);
+template void sep_solve<double>(const SepSolver<double>&, const double*, double*, cudaStream_t, const int*);
+
+// ---------------------------------------------------------------- Poisson
+__device__ __forceinline__ double turn_target(const DevState* st, const double* ext, int k, int nt,
+                                              double cs, double sn) {
+    if (ext) return ext[k];
+    // Eq. dirichlet: phi_k = V_c cos + V_s sin with V = V_c - i V_s
+    double vr = st->x[2 * (1 + nt + k)], vi = st->x[2 * (1 + nt + k) + 1];
+    return vr * cs + (-vi) * sn;
+}
+
+struct PoisArgs {
+    const double* phi;
+    const float* rho;
+    const double* win;
+    const double* eps_row;
+    const double* az;
+    const double* arp;
+    const double* arm;
+    const signed char* turn_mask;   // per node: -1 or turn index
+    float* r32;
+    int NR, NZ, M;
+    double inv2pieps0;
+    unsigned long long* norm;      // [2]: max|r|, max term scale
+    const int* done;
+    const DevState* st;            // turn potentials from the applied circuit state
+    const double* ext;             // or from an explicit array
+    int nt;
+    double cs, sn;
+};
+
+// r = b - A phi on the interior unknowns (i = 1..NZ-2, j = 0..NR-2).  Turn
+// nodes contribute their Dirichlet mismatch (target - phi) times the diagonal
+// coefficient to the norm and get r = 0 in the FP32 right-hand side (the
+// capacitance step imposes their values).  The relative residual is
+// max|r| / max(|b| + sum |A_ij phi_j|) (a componentwise scale).
+__global__ void poisson_residual(PoisArgs a) {
+    if (*a.done) return;
+    int rows = a.NZ - 2;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    double rmax = 0, smax = 0;
+    if (idx < rows * a.M) {
+        int i = idx / a.M + 1, j = idx % a.M;
+        int n = i * a.NR + j;
+        double epz = a.eps_row[i], emz = a.eps_row[i - 1];
+        double eb = 0.5 * (emz + epz);
+        int k = a.turn_mask[n];
+        if (k >= 0) {
+            a.r32[idx] = 0.f;
+            double diag = a.az[j] * (epz + emz) + eb * (a.arp[j] + a.arm[j]);
+            double tgt = turn_target(a.st, a.ext, k, a.nt, a.cs, a.sn);
+            rmax = fabs(tgt - a.phi[n]) * diag;
+            smax = fabs(tgt) * diag;
+        } else {
+            double pc = a.phi[n];
+            double t1 = a.az[j] * epz * (a.phi[n + a.NR] - pc);
+            double t2 = a.az[j] * emz * (a.phi[n - a.NR] - pc);
+            double t3 = eb * a.arp[j] * (a.phi[n + 1] - pc);
+            double t4 = (j > 0) ? eb * a.arm[j] * (a.phi[n - 1] - pc) : 0.0;
+            double b = -((double)a.rho[n] + a.win[n]) * a.inv2pieps0;
+            double r = b - (((t1 + t2) + t3) + t4);
+            a.r32[idx] = (float)r;
+            rmax = fabs(r);
+            smax = fabs(b) + fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&a.norm[0], rmax);
+        atomic_max_nonneg(&a.norm[1], smax);
+    }
+}
+
+// decides convergence from the norms of this sweep (runs before the solve)
+__global__ void poisson_check(DevState* st, int sweep, double tol, int* done, int final_sweep) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (*done) return;
+    double r = __longlong_as_double((long long)st->pnorm[2 * sweep]);
+    double s = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
+    double rel = (s > 0) ? r / s : 0.0;
+    st->prel = rel;
+    st->piters = sweep;
+    if (rel <= tol) {
+        *done = 1;
+    } else if (final_sweep) {
+        st->status |= PP_ST_NOCONV;
+    }
+}
+
+// sigma = G^-1 (target - phi_T - d0_T)
+__global__ void poisson_cap(const DevState* st, const double* ext, const double* phi, const float* d0,
+                            const int* tn_node, const int* tn_int, const int* tn_k, const double* Ginv,
+                            double* sigma, int K, int nt, double cs, double sn, const int* done) {
+    if (*done) return;
+    __shared__ double rT[kMaxCapNodes];
+    int t = threadIdx.x;
+    if (t < K) rT[t] = turn_target(st, ext, tn_k[t], nt, cs, sn) - phi[tn_node[t]] - (double)d0[tn_int[t]];
+    __syncthreads();
+    if (t < K) {
+        double s = 0;
+        for (int u = 0; u < K; ++u) s += Ginv[t * K + u] * rT[u];
+        sigma[t] = s;
+    }
+}
+
+__global__ void poisson_update(double* phi, const float* d0, const float* Z, const double* sigma, int K,
+                               int rows, int M, int NR, const signed char* turn_mask, const DevState* st,
+                               const double* ext, int nt, double cs, double sn, const int* done) {
+    if (*done) return;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * M) return;
+    int i = idx / M + 1, j = idx % M;
+    int n = i * NR + j;
+    int k = turn_mask[n];
+    if (k >= 0) {
+        phi[n] = turn_target(st, ext, k, nt, cs, sn);
+        return;
+    }
+    double d = (double)d0[idx];
+    size_t stride = (size_t)rows * M;
+    for (int t = 0; t < K; ++t) d += sigma[t] * (double)Z[t * stride + idx];
+    phi[n] += d;
+}
+
+// ---------------------------------------------------------------- node fields
+// per plasma cell 5 float4 (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10, 11)
+__global__ void field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
+                           const double* __restrict__ Ess, const double* __restrict__ B, float* F,
+                           int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
+                           double sn, int magnetic) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (i_win + 1) * NR) return;
+    int i = n / NR, j = n % NR;
+    double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
+    double Er;
+    if (j == 0) Er = 0.0;
+    else if (j == NR - 1) Er = -(phi[n] - phi[n - 1]) / dr;
+    else Er = -(phi[n + 1] - phi[n - 1]) / (2.0 * dr);
+    double Et = Ec[n] * cs - Ess[n] * sn;
+    double Br = 0.0, Bz = 0.0;
+    if (magnetic) {
+        Br = B[n] * cs + B[nnodes + n] * sn;
+        Bz = B[2 * nnodes + n] * cs + B[3 * nnodes + n] * sn;
+    }
+    float v[5] = {(float)Er, (float)Ez, (float)Et, (float)Br, (float)Bz};
+    // node (i, j) is corner 00 of cell (i, j), 01 of (i, j-1), 10 of (i-1, j), 11 of (i-1, j-1)
+    for (int corner = 0; corner < 4; ++corner) {
+        int ci = i - (corner >> 1), cj = j - (corner & 1);
+        if (ci < 0 || cj < 0 || ci >= i_win || cj >= nr) continue;
+        int cell = ci * nr + cj;
+        for (int comp = 0; comp < 5; ++comp) F[((size_t)cell * 5 + comp) * 4 + corner] = v[comp];
+    }
+}
+
+// ---------------------------------------------------------------- turn charge and accumulation
+// One block: Q_k (Eq. facecharge) from the current phi, the sample's
+// harmonics (Eq. fourier), the trapezoid of Eq. pcap and the power sums.
+__global__ void turn_sample(DevState* st, const double* phi, const int* ft, const int* fnb, const int* fk,
+                            const double* fc, int nfaces, int nt, double cs, double sn, double two_over_n,
+                            double inv_n, int n_rf) {
+    __shared__ double q[PP_MAX_TURNS];
+    if (threadIdx.x < PP_MAX_TURNS) q[threadIdx.x] = 0;
+    __syncthreads();
+    for (int f = threadIdx.x; f < nfaces; f += blockDim.x)
+        atomicAdd(&q[fk[f]], fc[f] * (phi[ft[f]] - phi[fnb[f]]));
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < nt; ++k) {
+        double V = turn_target(st, nullptr, k, nt, cs, sn);
+        double Q = q[k];
+        kahan_add(st->qc[k], st->qc_c[k], two_over_n * Q * cs);
+        kahan_add(st->qs[k], st->qs_c[k], two_over_n * Q * sn);
+        if (st->n_samples == 0) {
+            st->v_first[k] = V;
+            st->q_first[k] = Q;
+        } else {
+            st->w[k] += 0.5 * (V + st->v_prev[k]) * (Q - st->q_prev[k]);
+        }
+        st->v_prev[k] = V;
+        st->q_prev[k] = Q;
+    }
+    st->n_samples += 1;
+    kahan_add(st->p_ind, st->p_ind_c, st->p_ind_step * inv_n);
+    kahan_add(st->p_es, st->p_es_c, st->p_es_step * inv_n);
+    st->p_ind_step = 0;
+    st->p_es_step = 0;
+}
+
+// J_c += (2/N) cos(theta) J, J_s += (2/N) sin(theta) J over the plasma nodes
+__global__ void accumulate_nodes(const float* jm, const double* vol, double* Jc, double* Js, double* Jcc,
+                                 double* Jsc, int nn, double wc, double ws) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    double J = (double)jm[n] / vol[n];
+    kahan_add(Jc[n], Jcc[n], wc * J);
+    kahan_add(Js[n], Jsc[n], ws * J);
+}
+
+// ---------------------------------------------------------------- Helmholtz glue
+__global__ void nodes_to_interior(const double* src, double* dst, int NZ, int NR, int j0, int M,
+                                  double scale, const double* w) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int rows = NZ - 2;
+    if (idx >= rows * M) return;
+    int i = idx / M + 1, j = idx % M + j0;
+    dst[idx] = scale * src[i * NR + j];
+}
+
+__global__ void interior_to_nodes(const double* src, double* dst, int NZ, int NR, int j0, int M) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= NZ * NR) return;
+    int i = n / NR, j = n % NR;
+    double v = 0.0;
+    if (i >= 1 && i <= NZ - 2 && j >= j0 && j < j0 + M) v = src[(size_t)(i - 1) * M + (j - j0)];
+    dst[n] = v;
+}
+
+void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
+                         cudaStream_t st) {
+    int rows = c->hs.rows, M = c->hs.M;
+    int nint = rows * M;
+    double* stage = c->d_hstage;
+    nodes_to_interior<<<(nint + 255) / 256, 256, 0, st>>>(rhs_nodes, stage, c->NZ, c->NR, 1, M, scale,
+                                                           nullptr);
+    sep_solve<double>(c->hs, stage, stage + nint, st, nullptr);
+    interior_to_nodes<<<(c->nnodes + 255) / 256, 256, 0, st>>>(stage + nint, out_nodes, c->NZ, c->NR, 1, M);
+    count_launch(2);
+}
+
+// ---------------------------------------------------------------- compose and B
+// Eq. compose: E_c = E_c^(p) + sum I_s,k U_k, E_ss = E_ss^(p) + sum I_c,k U_k
+// with I_k = I_c - i I_s (so I_s = -Im I_k, I_c = Re I_k).
+__global__ void compose_kernel(const DevState* st, double* Ec, double* Ess, double* Ecp, double* Essp,
+                               const double* Ecp_new, const double* Essp_new, const double* U, int nn,
+                               int nt, int use_new) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    if (use_new && st->accepted) {
+        Ecp[n] = Ecp_new[n];
+        Essp[n] = Essp_new[n];
+    }
+    double ec = Ecp[n], es = Essp[n];
+    for (int k = 0; k < nt; ++k) {
+        double ire = st->x[2 * (1 + k)], iim = st->x[2 * (1 + k) + 1];
+        double u = U[(size_t)k * nn + n];
+        ec += (-iim) * u;
+        es += ire * u;
+    }
+    Ec[n] = ec;
+    Ess[n] = es;
+}
+
+// B phasors from Faraday's law: B_r(t) = Brc cos + Brs sin with Brc = dEss/dz / w,
+// Brs = dEc/dz / w; B_z(t) = Bzc cos + Bzs sin with Bzc = -(1/R) d(R Ess)/dR / w,
+// Bzs = -(1/R) d(R Ec)/dR / w.
+__global__ void bphasor_kernel(const double* Ec, const double* Ess, double* B, int NZ, int NR, double dz,
+                               double dr, double omega) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    int nn = NZ * NR;
+    if (n >= nn) return;
+    int i = n / NR, j = n % NR;
+    auto ddz = [&](const double* f) {
+        if (i == 0) return (f[n + NR] - f[n]) / dz;
+        if (i == NZ - 1) return (f[n] - f[n - NR]) / dz;
+        return (f[n + NR] - f[n - NR]) / (2.0 * dz);
+    };
+    auto curl = [&](const double* f) {
+        if (j == 0) return 2.0 * (f[n + 1] - f[n]) / dr;
+        double R = j * dr;
+        if (j == NR - 1) return (R * f[n] - (R - dr) * f[n - 1]) / (dr * R);
+        return ((R + dr) * f[n + 1] - (R - dr) * f[n - 1]) / (2.0 * dr * R);
+    };
+    B[n] = ddz(Ess) / omega;
+    B[nn + n] = ddz(Ec) / omega;
+    B[2 * nn + n] = -curl(Ess) / omega;
+    B[3 * nn + n] = -curl(Ec) / omega;
+}
+
+void launch_compose(Cell* c, bool from_new, cudaStream_t st) {
+    int nn = c->nnodes;
+    compose_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_st, c->d_Ec, c->d_Ess, c->d_Ecp, c->d_Essp,
+                                                     c->d_Ecp_new, c->d_Essp_new, c->d_U, nn, c->nturns,
+                                                     from_new ? 1 : 0);
+    bphasor_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_Ec, c->d_Ess, c->d_Br, c->NZ, c->NR, c->dz, c->dr,
+                                                     c->omega);
+    count_launch(2);
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
+    turn_sample<<<1, 256, 0, st>>>(c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
+                                   c->nfaces, c->nturns, cs, sn, 2.0 / c->n_rf, 1.0 / c->n_rf, c->n_rf);
+    count_launch();
+}
+
+void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
+    int nn = (c->i_win + 1) * c->NR;
+    accumulate_nodes<<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
+                                                       c->d_Js_c, nn, wc, ws);
+    count_launch();
+}
+
+void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
+    int n = (c->i_win + 1) * c->NR;
+    field_prep<<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->NR, c->nr,
+                                                c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
+                                                c->cfg.magnetic_force);
+    count_launch();
+}
+
+int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
+                   const double* d_targets) {
+    int rows = c->ps.rows, M = c->ps.M;
+    int nint = rows * M;
+    int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
+    DevState* dst = c->d_st;
+    cudaMemsetAsync(&dst->pnorm[0], 0, sizeof(dst->pnorm), st);
+    cudaMemsetAsync(&dst->pdone, 0, sizeof(int), st);
+    const int* done = &dst->pdone;
+    const double* ext = external_targets ? d_targets : nullptr;
+    PoisArgs a;
+    a.phi = c->d_phi;
+    a.rho = c->d_rho;
+    a.win = c->d_win;
+    a.eps_row = c->d_eps_row;
+    a.az = c->d_az;
+    a.arp = c->d_arp;
+    a.arm = c->d_arm;
+    a.turn_mask = c->d_turn_mask;
+    a.r32 = c->d_r32;
+    a.NR = c->NR;
+    a.NZ = c->NZ;
+    a.M = M;
+    a.inv2pieps0 = 1.0 / (2.0 * kPi * kEps0);
+    a.done = done;
+    a.st = dst;
+    a.ext = ext;
+    a.nt = c->nturns;
+    a.cs = cs;
+    a.sn = sn;
+    int K = c->ntn;
+    for (int it = 0; it <= maxit; ++it) {
+        a.norm = &dst->pnorm[2 * it];
+        poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
+        poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, &dst->pdone, it == maxit ? 1 : 0);
+        count_launch(2);
+        if (it == maxit) break;
+        // d0 = P(r): the second GEMM writes t0 after the tridiagonal sweep has
+        // consumed it, so t0 holds d0 afterwards
+        sep_solve<float>(c->ps, c->d_r32, c->ps.t0, st, done);
+        poisson_cap<<<1, kMaxCapNodes, 0, st>>>(dst, ext, c->d_phi, c->ps.t0, c->d_tn_node, c->d_tn_int,
+                                                c->d_tn_k, c->d_Ginv, c->d_sigma, K, c->nturns, cs, sn, done);
+        poisson_update<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Z, c->d_sigma, K, rows, M,
+                                                            c->NR, c->d_turn_mask, dst, ext, c->nturns, cs,
+                                                            sn, done);
+        count_launch(2);
+    }
+    return 0;
+}
+
+}  // namespace pp

@@ -1,0 +1,227 @@
+// Internal structures of libphasorpic.so (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/phasorpic.h"
+
+namespace pp {
+
+// ---------------------------------------------------------------- constants
+// The paper's Test 3 values of eps0 and mu0 (used in its code and references);
+// CODATA for the rest.
+constexpr double kEps0 = 8.8542e-12;
+constexpr double kMu0 = 1.2566e-6;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kMAr = 39.948 * kAmu;
+constexpr double kKb = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kEExc = 11.55f;   // eV
+constexpr float kEIon = 15.76f;   // eV
+constexpr uint32_t kDead = 0xFFFFFFFFu;
+
+constexpr int kPushThreads = 256;
+constexpr int kPPT = 8;                           // particles per thread per chunk
+constexpr int kChunk = kPushThreads * kPPT;
+constexpr int kTileRows = 8;                      // node rows of the shared deposit tile
+constexpr int kMaxNR = 513;                       // node columns supported by the tile
+constexpr int kEventCap = 8192;                   // ionisation events per step
+constexpr int kMaxCapNodes = 64;                  // turn nodes handled by the capacitance matrix
+
+// ---------------------------------------------------------------- particles
+struct ParticleBuf {
+    uint32_t* cell;
+    float* dr;
+    float* dz;
+    float* vr;
+    float* vt;
+    float* vz;
+    uint32_t* uid;
+};
+
+struct SpeciesConst {   // float constants of one species (rounded once from FP64)
+    float qmh, dtr, dtz, qw, numax, pnull, ng, ce, inv_ce, loss, vth_gas;
+};
+
+struct Event {          // one ionisation: new e- and Ar+ at the parent's position
+    uint32_t parent, cell;
+    float dr, dz;
+    float ve[3], vi[3];
+};
+
+// cumulative counters (unsigned long long), index = pp_get_counters order
+enum {
+    C_PSTEPS = 0, C_ABSORBED, C_CREATED, C_E_EL, C_E_EX, C_E_IZ, C_I_CX, C_I_ISO, C_NUVIOL,
+    C_NCOUNT = 9
+};
+
+// device-resident scalars of one cell
+struct DevState {
+    double x[2 * (2 * PP_MAX_TURNS + 1)];    // applied circuit state
+    double vg_amp;
+    double pf_prev;
+    int has_pf;
+    int n_samples;
+    double qc[PP_MAX_TURNS], qs[PP_MAX_TURNS], qc_c[PP_MAX_TURNS], qs_c[PP_MAX_TURNS];
+    double w[PP_MAX_TURNS];
+    double v_first[PP_MAX_TURNS], q_first[PP_MAX_TURNS], v_prev[PP_MAX_TURNS], q_prev[PP_MAX_TURNS];
+    double p_ind, p_ind_c, p_es, p_es_c;
+    double p_ind_step, p_es_step;            // summed by the push kernel
+    unsigned long long cnt[C_NCOUNT];        // cumulative
+    unsigned long long per[C_NCOUNT];        // this period
+    unsigned long long live[2];              // live macroparticles per species
+    unsigned int status;
+    int n_events;                            // events recorded this step
+    int accepted;                            // last period end accepted
+    long long period;
+    int has_record;
+    pp_period_record rec;
+    // Poisson refinement bookkeeping (per sweep: max|r|, max term scale)
+    unsigned long long pnorm[2 * 16];
+    int pdone;
+    int piters;
+    double prel;
+};
+
+// FP32 or FP64 separable solver: radial generalised eigenbasis x tridiagonal in z
+template <typename T>
+struct SepSolver {
+    int rows = 0, M = 0;        // unknown rows (z) and radial unknowns
+    T* Vf = nullptr;            // forward transform (M x M): ft = f * Vf
+    T* Vb = nullptr;            // backward transform (M x M): x = psi * Vb
+    T* cp = nullptr;            // Thomas factors c'_i per (row, mode)
+    T* invd = nullptr;          // 1 / denominator per (row, mode)
+    T* lo = nullptr;            // sub-diagonal per row (mode independent)
+    T* t0 = nullptr;            // scratch rows x M
+    T* t1 = nullptr;
+};
+
+struct Cell {
+    pp_config cfg;
+    int nr = 0, nz = 0, NR = 0, NZ = 0, nnodes = 0;
+    int i_win = 0, i_win_hi = 0, n_rf = 0, nturns = 0;
+    double dr = 0, dz = 0, omega = 0;
+    int64_t s = 0;                        // steps completed
+    bool primed = false;
+    int sort_count[2] = {0, 0};
+
+    // host-side geometry and circuit
+    std::vector<std::vector<int>> turn_nodes;     // full node indices per turn
+    std::vector<double> eps_row;                  // eps of cell row i (z-only dependence)
+    std::vector<double> zvac;                     // 2 N^2
+    double eps_rec = 0;
+    std::vector<double> r_rf;
+    SpeciesConst sc[2];
+
+    // particles
+    ParticleBuf pb[2][2];
+    int cur[2] = {0, 0};
+    int64_t cap[2] = {0, 0};
+    int* d_nslot = nullptr;                 // [2] used slots (live + absorbed since last sort)
+    uint32_t* d_next_uid = nullptr;         // [2]
+    uint32_t* d_hist = nullptr;             // counting-sort bins (ncell + 2)
+    Event* d_events = nullptr;
+
+    // grids
+    double* d_phi = nullptr;
+    float* d_F = nullptr;                   // 5 float4 per plasma cell
+    float* d_rho = nullptr;                 // node charge of the step (C)
+    float* d_jm = nullptr;                  // node current moment (A m)
+    double* d_win = nullptr;                // window surface charge (C)
+    double* d_vol = nullptr;                // node weighting volumes (plasma rows)
+    double *d_Ec = nullptr, *d_Ess = nullptr, *d_Ecp = nullptr, *d_Essp = nullptr;
+    double *d_Ecp_new = nullptr, *d_Essp_new = nullptr;
+    double *d_Br = nullptr;                 // 4 node grids: Brc, Brs, Bzc, Bzs
+    double *d_U = nullptr;                  // N unit fields
+    double *d_Jc = nullptr, *d_Js = nullptr, *d_Jc_c = nullptr, *d_Js_c = nullptr;
+    double* d_eps_row = nullptr;            // eps per cell row (nz)
+    double* d_az = nullptr;                 // per column: A_z/(2 pi dz)
+    double* d_arp = nullptr;                // per column: A_R+/(2 pi dr)
+    double* d_arm = nullptr;                // per column: A_R-/(2 pi dr)
+    double* d_R = nullptr;                  // node radii
+
+    // turn charge faces (Eq. facecharge)
+    int nfaces = 0;
+    int* d_face_t = nullptr;                // turn node
+    int* d_face_nb = nullptr;               // neighbour node
+    int* d_face_k = nullptr;                // turn index
+    double* d_face_c = nullptr;             // eps0 eps_f A_f / d_f
+    // turn nodes (flattened) for projections and Dirichlet values
+    int ntn = 0;
+    int* d_tn_node = nullptr;               // full node index
+    int* d_tn_int = nullptr;                // interior index of the Poisson unknowns
+    int* d_tn_k = nullptr;                  // turn index
+    double* d_gk_val = nullptr;             // g_k at that node
+    signed char* d_turn_mask = nullptr;     // per node: turn index or -1
+
+    // Poisson: FP32 separable inner solve + capacitance correction
+    SepSolver<float> ps;
+    float* d_r32 = nullptr;                 // residual (interior layout)
+    double* d_rT = nullptr;                 // turn-node residuals
+    double* d_sigma = nullptr;
+    double* d_Ginv = nullptr;               // ntn x ntn
+    float* d_Z = nullptr;                   // ntn x (rows*M)
+    // Helmholtz FP64
+    SepSolver<double> hs;
+    double* d_hstage = nullptr;             // 2 x interior Helmholtz staging
+    double* d_ext_targets = nullptr;        // turn potentials for standalone solves
+
+    // device state
+    DevState* d_st = nullptr;
+    DevState* h_st = nullptr;               // pinned host mirror for reads
+
+    // circuit constants (device)
+    double* d_Ainv = nullptr;               // (2N+1)^2 complex inverse of the network matrix
+    double* d_zturn = nullptr;              // N^2 complex
+    double* d_circ = nullptr;               // misc: zs(2), r_rf[N], c_stray[N]
+
+    // phase timing (CUDA events on the launching stream), enabled on request
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;      // pairs: [2k] start, [2k+1] stop
+    std::vector<int> ev_phase;             // phase of pair k
+    size_t ev_used = 0;
+
+    std::vector<void*> allocs;
+    template <typename T>
+    T* alloc(size_t n) {
+        void* p = nullptr;
+        if (n == 0) n = 1;
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, n * sizeof(T));
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+};
+
+void set_error(const std::string& s);
+extern unsigned long long g_launches;     // kernels launched by this library (host count)
+inline void count_launch(int n = 1) { g_launches += (unsigned long long)n; }
+
+enum { PH_PUSH = 0, PH_POISSON, PH_SORT, PH_OTHER, PH_PERIOD, PH_N };
+
+// ---------------------------------------------------------------- setup (host)
+int setup_cell(Cell* c);
+
+// ---------------------------------------------------------------- launchers
+void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st);
+void launch_push(Cell* c, uint32_t step, cudaStream_t st);
+void launch_append(Cell* c, cudaStream_t st);
+void launch_sort(Cell* c, int sp, cudaStream_t st);
+void launch_deposit_only(Cell* c, cudaStream_t st);
+int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
+                   const double* d_targets);
+void launch_turn_sample(Cell* c, double cs_new, double sn_new, cudaStream_t st);
+void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st);
+void period_end(Cell* c, cudaStream_t st);
+template <typename T>
+void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, const int* skip);
+void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
+                         cudaStream_t st);
+void launch_compose(Cell* c, bool from_new, cudaStream_t st);
+
+}  // namespace pp

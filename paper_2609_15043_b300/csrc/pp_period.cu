@@ -1,0 +1,237 @@
+// Period end (Sec. 2.4-2.5): plasma-only back-emf, displacement currents,
+// sample-count check, powers, power controller, target network solve,
+// relaxation and residuals -- one thread of one block, FP64 complex.
+#include "pp_internal.h"
+
+namespace pp {
+
+struct Cx {
+    double r, i;
+};
+__device__ __forceinline__ Cx cadd(Cx a, Cx b) { return Cx{a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ Cx csub(Cx a, Cx b) { return Cx{a.r - b.r, a.i - b.i}; }
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) { return Cx{a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ Cx cscale(Cx a, double s) { return Cx{a.r * s, a.i * s}; }
+__device__ __forceinline__ double cabs2(Cx a) { return a.r * a.r + a.i * a.i; }
+
+struct PeriodArgs {
+    DevState* st;
+    const double* Ecp;        // plasma-only E_c of the completed period (node grid)
+    const double* Essp;       // plasma-only stored sine array
+    const int* tn_node;
+    const int* tn_k;
+    const double* gk_val;
+    int ntn;
+    int N, NR, n_rf;
+    double dr, dz, omega, freq;
+    const double* Ainv;       // (2N+1)^2 complex
+    const double* zturn;      // N^2 complex
+    const double* circ;       // zs (2), r_rf[N], c_stray[N]
+    int power_control;
+    double p_target, gamma, n_trend, eps_p, alpha_v, f_step, v_min, v_max, alpha, phase_g;
+    const int* nslot;
+};
+
+__global__ void period_circuit(PeriodArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    DevState* st = a.st;
+    const int N = a.N, NX = 2 * N + 1;
+    const double two_pi = 6.283185307179586;
+    // V_p,k = -int g_k (E_c^p + i E_ss^p) dV (Eq. vpind)
+    Cx vp[PP_MAX_TURNS], icap[PP_MAX_TURNS], qh[PP_MAX_TURNS];
+    for (int k = 0; k < N; ++k) vp[k] = Cx{0, 0};
+    for (int t = 0; t < a.ntn; ++t) {
+        int n = a.tn_node[t], k = a.tn_k[t];
+        double R = (n % a.NR) * a.dr;
+        double w = a.gk_val[t] * two_pi * R * a.dz * a.dr;
+        vp[k].r -= w * a.Ecp[n];
+        vp[k].i -= w * a.Essp[n];
+    }
+    // Q = Q_c - i Q_s, I_cap = i w Q = w Q_s + i w Q_c (Eq. icap)
+    for (int k = 0; k < N; ++k) {
+        qh[k] = Cx{st->qc[k], -st->qs[k]};
+        icap[k] = Cx{a.omega * st->qs[k], a.omega * st->qc[k]};
+    }
+    const bool accepted = st->n_samples == a.n_rf;
+    Cx x[2 * PP_MAX_TURNS + 1];
+    for (int q = 0; q < NX; ++q) x[q] = Cx{st->x[2 * q], st->x[2 * q + 1]};
+    const double* rrf = a.circ + 2;
+    const double* cst = a.circ + 2 + N;
+    // powers of the completed period (Eqs. pport, pcap, pcap_phasor, pind)
+    double p_port = 0.5 * (x[1 + N].r * x[0].r + x[1 + N].i * x[0].i);
+    double p_cu = 0;
+    for (int k = 0; k < N; ++k) p_cu += 0.5 * rrf[k] * cabs2(x[1 + k]);
+    double p_cap_ph = 0;
+    for (int k = 0; k < N; ++k) p_cap_ph += 0.5 * (x[1 + N + k].r * icap[k].r + x[1 + N + k].i * icap[k].i);
+    double wsum = 0;
+    for (int k = 0; k < N; ++k)
+        wsum += st->w[k] + 0.5 * (st->v_first[k] + st->v_prev[k]) * (st->q_first[k] - st->q_prev[k]);
+    double p_cap = a.freq * wsum;
+    double p_ind = st->p_ind, p_es = st->p_es;
+    pp_period_record& rec = st->rec;
+    rec.period = st->period;
+    rec.n_samples = st->n_samples;
+    rec.accepted = accepted ? 1 : 0;
+    rec.n_turns = N;
+    for (int k = 0; k < N; ++k) {
+        rec.vp[2 * k] = vp[k].r;
+        rec.vp[2 * k + 1] = vp[k].i;
+        rec.icap[2 * k] = icap[k].r;
+        rec.icap[2 * k + 1] = icap[k].i;
+        rec.qhat[2 * k] = qh[k].r;
+        rec.qhat[2 * k + 1] = qh[k].i;
+    }
+    for (int q = 0; q < NX; ++q) {
+        rec.x_applied[2 * q] = x[q].r;
+        rec.x_applied[2 * q + 1] = x[q].i;
+    }
+    rec.vg = st->vg_amp;
+    rec.p_port = p_port;
+    rec.p_ind = p_ind;
+    rec.p_cap = p_cap;
+    rec.p_cap_ph = p_cap_ph;
+    rec.p_cu = p_cu;
+    rec.p_es = p_es;
+    double denom = fabs(p_port) > 1e-300 ? fabs(p_port) : 1e-300;
+    rec.eps_bal = fabs(p_port - (p_ind + p_cap + p_cu)) / denom;
+    rec.particle_steps = (double)st->per[C_PSTEPS];
+    rec.coll[0][0] = (int64_t)st->per[C_E_EL];
+    rec.coll[0][1] = (int64_t)st->per[C_E_EX];
+    rec.coll[0][2] = (int64_t)st->per[C_E_IZ];
+    rec.coll[1][0] = (int64_t)st->per[C_I_CX];
+    rec.coll[1][1] = (int64_t)st->per[C_I_ISO];
+    rec.coll[1][2] = 0;
+    rec.absorbed = (int64_t)st->per[C_ABSORBED];
+    rec.created = (int64_t)st->per[C_CREATED];
+    rec.nu_violations = (int64_t)st->per[C_NUVIOL];
+    rec.n_live[0] = st->live[0];
+    rec.n_live[1] = st->live[1];
+
+    Cx vg = Cx{st->vg_amp * cos(a.phase_g), st->vg_amp * sin(a.phase_g)};
+    if (accepted) {
+        if (a.power_control) {   // Eqs. pfilter, ptrend, pcontrol + limiter + bounds
+            double prev = st->has_pf ? st->pf_prev : p_port;
+            double pf = a.gamma * p_port + (1.0 - a.gamma) * prev;
+            double pc = pf + a.n_trend * (pf - prev);
+            if (pc < a.eps_p) pc = a.eps_p;
+            double vo = st->vg_amp;
+            double vd = vo * sqrt(a.p_target / pc);
+            double vn = vo + a.alpha_v * (vd - vo);
+            double lo = (1.0 - a.f_step) * vo, hi = (1.0 + a.f_step) * vo;
+            vn = vn < lo ? lo : (vn > hi ? hi : vn);
+            vn = vn < a.v_min ? a.v_min : (vn > a.v_max ? a.v_max : vn);
+            st->vg_amp = vn;
+            st->pf_prev = pf;
+            st->has_pf = 1;
+            vg = Cx{vn * cos(a.phase_g), vn * sin(a.phase_g)};
+        }
+        // x_target = A^-1 (V_g, I_cap, V_p) (Eqs. blockmatrix, target)
+        Cx b[2 * PP_MAX_TURNS + 1];
+        b[0] = vg;
+        for (int k = 0; k < N; ++k) {
+            b[1 + k] = icap[k];
+            b[1 + N + k] = vp[k];
+        }
+        for (int r = 0; r < NX; ++r) {
+            Cx s = Cx{0, 0};
+            for (int q = 0; q < NX; ++q)
+                s = cadd(s, cmul(Cx{a.Ainv[2 * (r * NX + q)], a.Ainv[2 * (r * NX + q) + 1]}, b[q]));
+            x[r] = cadd(cscale(x[r], 1.0 - a.alpha), cscale(s, a.alpha));   // Eq. relaxation
+        }
+        for (int q = 0; q < NX; ++q) {
+            st->x[2 * q] = x[q].r;
+            st->x[2 * q + 1] = x[q].i;
+        }
+    } else {
+        st->status |= PP_ST_SAMPLES;
+    }
+    // residuals with the new state, new source and the period's loads (Eqs. kclres, kvlres)
+    double zsr = a.circ[0], zsi = a.circ[1];
+    double si = sqrt(cabs2(x[0]));
+    double sv = sqrt(cabs2(vg));
+    si = si > 1e-300 ? si : 1e-300;
+    sv = sv > 1e-300 ? sv : 1e-300;
+    double rkcl = 0, rkvl = 0;
+    for (int k = 0; k < N; ++k) {
+        Cx iin = (k == 0) ? x[0] : x[k];
+        Cx r = csub(csub(iin, x[1 + k]), icap[k]);
+        r = csub(r, cmul(Cx{0, a.omega * cst[k]}, x[1 + N + k]));
+        double m = sqrt(cabs2(r)) / si;
+        rkcl = m > rkcl ? m : rkcl;
+        Cx vnext = (k + 1 < N) ? x[1 + N + k + 1] : Cx{0, 0};
+        Cx rv = csub(x[1 + N + k], vnext);
+        for (int l = 0; l < N; ++l)
+            rv = csub(rv, cmul(Cx{a.zturn[2 * (k * N + l)], a.zturn[2 * (k * N + l) + 1]}, x[1 + l]));
+        rv = csub(rv, vp[k]);
+        m = sqrt(cabs2(rv)) / sv;
+        rkvl = m > rkvl ? m : rkvl;
+    }
+    Cx r0 = csub(csub(vg, cmul(Cx{zsr, zsi}, x[0])), x[1 + N]);
+    double m0 = sqrt(cabs2(r0)) / sv;
+    rkvl = m0 > rkvl ? m0 : rkvl;
+    rec.r_kcl = rkcl;
+    rec.r_kvl = rkvl;
+    for (int q = 0; q < NX; ++q) {
+        rec.x_next[2 * q] = x[q].r;
+        rec.x_next[2 * q + 1] = x[q].i;
+    }
+    rec.vg_next = st->vg_amp;
+    st->accepted = accepted ? 1 : 0;
+    st->has_record = 1;
+    st->period += 1;
+    // reset the period accumulators
+    for (int k = 0; k < PP_MAX_TURNS; ++k) {
+        st->qc[k] = st->qs[k] = st->qc_c[k] = st->qs_c[k] = st->w[k] = 0;
+        st->v_first[k] = st->q_first[k] = st->v_prev[k] = st->q_prev[k] = 0;
+    }
+    st->n_samples = 0;
+    st->p_ind = st->p_ind_c = st->p_es = st->p_es_c = 0;
+    for (int q = 0; q < C_NCOUNT; ++q) st->per[q] = 0;
+}
+
+void period_end(Cell* c, cudaStream_t st) {
+    double scale = kMu0 * c->omega;
+    // Eq. helmholtz_two_real: L E_c^p = mu0 w J_s, L E_ss^p = mu0 w J_c
+    helmholtz_solve_dev(c, c->d_Js, c->d_Ecp_new, scale, st);
+    helmholtz_solve_dev(c, c->d_Jc, c->d_Essp_new, scale, st);
+    PeriodArgs a;
+    a.st = c->d_st;
+    a.Ecp = c->d_Ecp_new;
+    a.Essp = c->d_Essp_new;
+    a.tn_node = c->d_tn_node;
+    a.tn_k = c->d_tn_k;
+    a.gk_val = c->d_gk_val;
+    a.ntn = c->ntn;
+    a.N = c->nturns;
+    a.NR = c->NR;
+    a.n_rf = c->n_rf;
+    a.dr = c->dr;
+    a.dz = c->dz;
+    a.omega = c->omega;
+    a.freq = c->cfg.freq;
+    a.Ainv = c->d_Ainv;
+    a.zturn = c->d_zturn;
+    a.circ = c->d_circ;
+    a.power_control = c->cfg.power_control;
+    a.p_target = c->cfg.p_target;
+    a.gamma = c->cfg.gamma;
+    a.n_trend = c->cfg.n_trend;
+    a.eps_p = c->cfg.eps_p;
+    a.alpha_v = c->cfg.alpha_v;
+    a.f_step = c->cfg.f_step;
+    a.v_min = c->cfg.v_min;
+    a.v_max = c->cfg.v_max;
+    a.alpha = c->cfg.alpha;
+    a.phase_g = c->cfg.phase_g;
+    a.nslot = c->d_nslot;
+    period_circuit<<<1, 32, 0, st>>>(a);
+    count_launch();
+    launch_compose(c, true, st);
+    size_t nb = sizeof(double) * c->nnodes;
+    cudaMemsetAsync(c->d_Jc, 0, nb, st);
+    cudaMemsetAsync(c->d_Js, 0, nb, st);
+    cudaMemsetAsync(c->d_Jc_c, 0, nb, st);
+    cudaMemsetAsync(c->d_Js_c, 0, nb, st);
+}
+
+}  // namespace pp

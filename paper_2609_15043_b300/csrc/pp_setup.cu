@@ -1,0 +1,616 @@
+// Host-side initialisation of a cell (Sec. 2.5 "initialisation"): validation,
+// turn node sets and face lists, radial eigenbases of the separable solvers,
+// unit fields and Z_vac, the network inverse and the first-cycle state.
+#include "pp_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+
+namespace pp {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- linear algebra
+// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major);
+// returns eigenvalues in w and eigenvectors as the columns of V
+static void jacobi_eig(std::vector<double> A, int n, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    double norm = 0;
+    for (double v : A) norm += v * v;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off <= 1e-30 * norm) break;
+        for (int p = 0; p < n; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {      // columns p, q
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {      // rows p, q
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// Gauss-Jordan inverse with partial pivoting; returns false if singular
+template <typename T>
+static bool invert(std::vector<T>& A, int n) {
+    std::vector<T> I((size_t)n * n, T(0));
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = T(1);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::abs(A[(size_t)r * n + c]) > std::abs(A[(size_t)piv * n + c])) piv = r;
+        if (std::abs(A[(size_t)piv * n + c]) == 0.0) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+                std::swap(I[(size_t)c * n + k], I[(size_t)piv * n + k]);
+            }
+        T d = A[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) {
+            A[(size_t)c * n + k] /= d;
+            I[(size_t)c * n + k] /= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            T f = A[(size_t)r * n + c];
+            if (f == T(0)) continue;
+            for (int k = 0; k < n; ++k) {
+                A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+                I[(size_t)r * n + k] -= f * I[(size_t)c * n + k];
+            }
+        }
+    }
+    A = I;
+    return true;
+}
+
+// generalised symmetric-definite radial problem T v = mu D v, D diagonal > 0
+static void radial_basis(const std::vector<double>& T, const std::vector<double>& D, int M,
+                         std::vector<double>& mu, std::vector<double>& Vout) {
+    std::vector<double> S((size_t)M * M);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+            S[(size_t)i * M + j] = T[(size_t)i * M + j] / std::sqrt(D[i] * D[j]);
+    std::vector<double> W;
+    jacobi_eig(S, M, mu, W);
+    Vout.resize((size_t)M * M);
+    for (int j = 0; j < M; ++j)
+        for (int m = 0; m < M; ++m) Vout[(size_t)j * M + m] = W[(size_t)j * M + m] / std::sqrt(D[j]);
+}
+
+template <typename T>
+static T* upload(Cell* c, const std::vector<double>& h) {
+    T* d = c->alloc<T>(h.size());
+    if (!d) return nullptr;
+    std::vector<T> tmp(h.begin(), h.end());
+    cudaMemcpy(d, tmp.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+    return d;
+}
+
+// Thomas factors of a_i x_{i-1} + d_i x_i + c_i x_{i+1} per mode (row-major [row][mode])
+static void thomas_factors(const std::vector<double>& lo, const std::vector<double>& up,
+                           const std::vector<double>& diag, int rows, int M, std::vector<double>& cp,
+                           std::vector<double>& invd) {
+    cp.assign((size_t)rows * M, 0.0);
+    invd.assign((size_t)rows * M, 0.0);
+    for (int m = 0; m < M; ++m) {
+        double cprev = 0;
+        for (int i = 0; i < rows; ++i) {
+            double den = diag[(size_t)i * M + m] - (i ? lo[i] * cprev : 0.0);
+            invd[(size_t)i * M + m] = 1.0 / den;
+            cprev = (i + 1 < rows) ? up[i] / den : 0.0;
+            cp[(size_t)i * M + m] = cprev;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- cross sections (FP64)
+static void sigma_e64(double x, double& el, double& ex, double& iz) {
+    double y = x - 0.23, y2 = y * y;
+    el = (0.1 + 14.0 * y2 / (y2 + 4.0)) / (1.0 + x / 50.0);
+    double ye = x - 11.55;
+    ex = (x > 11.55) ? 1.2 * ye / (ye * ye / 30.0 + ye + 8.0) : 0.0;
+    double yi = x - 15.76;
+    iz = (x > 15.76) ? 3.0 * yi / (yi * yi / 60.0 + yi + 30.0) : 0.0;
+}
+
+static void species_constants(Cell* c) {
+    const pp_config& f = c->cfg;
+    double n_gas = f.pressure_pa / (kKb * f.t_gas);
+    // nu_max: electrons max over x = 1000 k / 100000 eV (k = 0..100000) x 1.05;
+    // ions at the relative speed of a 1 keV ion (sigma g increases with g) x 1.05
+    double nue = 0;
+    for (int k = 0; k <= 100000; ++k) {
+        double x = 1000.0 * k / 100000.0;
+        double se, sx, si;
+        sigma_e64(x, se, sx, si);
+        double g = std::sqrt(2.0 * kQe * x / kMe);
+        double nu = n_gas * 1e-20 * (se + sx + si) * g;
+        nue = std::max(nue, nu);
+    }
+    nue *= 1.05;
+    double gcap = std::sqrt(2.0 * kQe * 1000.0 / kMAr);
+    double sq = std::sqrt(1000.0);
+    double scx = 2.0 + 3.0 / (1.0 + sq), siso = 1.0 + 2.0 / (1.0 + sq);
+    double nui = n_gas * 1e-19 * (scx + siso) * gcap * 1.05;
+    for (int sp = 0; sp < 2; ++sp) {
+        double q = sp == 0 ? -kQe : kQe;
+        double m = sp == 0 ? kMe : kMAr;
+        double nu = sp == 0 ? nue : nui;
+        SpeciesConst& s = c->sc[sp];
+        s.qmh = (float)(q / m * f.dt / 2.0);
+        s.dtr = (float)(f.dt / c->dr);
+        s.dtz = (float)(f.dt / c->dz);
+        s.qw = (float)(q * f.weight[sp]);
+        s.numax = (float)nu;
+        s.pnull = (float)(-std::expm1(-nu * f.dt));
+        s.ng = (float)(n_gas * (sp == 0 ? 1e-20 : 1e-19));
+        s.ce = (float)(0.5 * m / kQe);
+        s.inv_ce = (float)(kQe / (0.5 * m));
+        s.loss = (float)(2.0 * kMe / kMAr);
+        s.vth_gas = (float)std::sqrt(kKb * f.t_gas / kMAr);
+    }
+}
+
+static int on_grid(double x, double h, int* k) {
+    double q = x / h;
+    if (std::fabs(q - std::round(q)) > 1e-9) return 0;
+    *k = (int)std::lround(q);
+    return 1;
+}
+
+static int fail(const char* msg) {
+    set_error(msg);
+    return PP_E_CONFIG;
+}
+
+// ---------------------------------------------------------------- setup
+int setup_cell(Cell* c) {
+    pp_config& f = c->cfg;
+    if (f.nr < 2 || f.nz < 4 || f.r_max <= 0 || f.z_max <= 0) return fail("grid sizes must be positive");
+    if (f.nr + 1 > kMaxNR) return fail("nr exceeds the supported radial node count");
+    if (f.n_turns < 1 || f.n_turns > PP_MAX_TURNS) return fail("n_turns out of range");
+    if (f.freq <= 0 || f.dt <= 0) return fail("freq and dt must be positive");
+    c->nr = f.nr;
+    c->nz = f.nz;
+    c->NR = f.nr + 1;
+    c->NZ = f.nz + 1;
+    c->nnodes = c->NR * c->NZ;
+    c->dr = f.r_max / f.nr;
+    c->dz = f.z_max / f.nz;
+    c->omega = 2.0 * kPi * f.freq;
+    c->nturns = f.n_turns;
+    // Eq. nrf and Eq. phaseclosure
+    c->n_rf = (int)std::lround(1.0 / (f.freq * f.dt));
+    if (!(std::fabs(f.freq * f.dt * c->n_rf - 1.0) < 1e-10)) return fail("phase closure violated: |f dt N_RF - 1| >= 1e-10");
+    if (!on_grid(f.z_win_lo, c->dz, &c->i_win) || !on_grid(f.z_win_hi, c->dz, &c->i_win_hi))
+        return fail("window planes must lie on grid lines");
+    if (c->i_win < 2 || c->i_win_hi <= c->i_win || c->i_win_hi >= f.nz) return fail("window slab out of range");
+    if (f.weight[0] <= 0 || f.weight[1] <= 0) return fail("macroparticle weights must be positive");
+    if (f.capacity[0] < 1 || f.capacity[1] < 1) return fail("capacities must be positive");
+    if (f.capacity[0] > 0x7fffffff - kChunk || f.capacity[1] > 0x7fffffff - kChunk) return fail("capacity too large");
+    if (f.sort_every[0] < 1 || f.sort_every[1] < 1) return fail("sort_every must be >= 1");
+    if (f.alpha <= 0 || f.alpha > 1) return fail("relaxation factor must be in (0, 1]");
+    if (f.poisson_tol <= 0) f.poisson_tol = 1e-10;
+    if (f.poisson_max_iter < 1) f.poisson_max_iter = 4;
+    const int NR = c->NR, NZ = c->NZ, N = c->nturns;
+    const double dr = c->dr, dz = c->dz;
+
+    // ---- permittivity per cell row (the slab spans the full radius)
+    c->eps_row.assign(f.nz, 1.0);
+    for (int i = c->i_win; i < c->i_win_hi; ++i) c->eps_row[i] = f.eps_win;
+
+    // ---- turn node sets (Eq. shape): nodes within the wire disc, else nearest
+    std::vector<int> owner(c->nnodes, -1);
+    c->turn_nodes.assign(N, {});
+    for (int k = 0; k < N; ++k) {
+        std::vector<int>& nodes = c->turn_nodes[k];
+        double rk = f.turn_r[k];
+        for (int i = 1; i <= NZ - 2; ++i)
+            for (int j = 0; j <= NR - 2; ++j) {
+                double d2 = (j * dr - rk) * (j * dr - rk) + (i * dz - f.z_coil) * (i * dz - f.z_coil);
+                if (d2 <= f.wire_radius * f.wire_radius) nodes.push_back(i * NR + j);
+            }
+        if (nodes.empty()) {
+            double best = 1e300;
+            int bn = -1;
+            for (int i = 1; i <= NZ - 2; ++i)
+                for (int j = 0; j <= NR - 2; ++j) {
+                    double d2 = (j * dr - rk) * (j * dr - rk) + (i * dz - f.z_coil) * (i * dz - f.z_coil);
+                    if (d2 < best) {
+                        best = d2;
+                        bn = i * NR + j;
+                    }
+                }
+            nodes.push_back(bn);
+        }
+        for (int n : nodes) {
+            if (owner[n] >= 0) return fail("a conductor node belongs to two turns");
+            if (n / NR <= c->i_win) return fail("a turn reaches into the plasma region");
+            owner[n] = k;
+        }
+        if (f.winding[k] != 1 && f.winding[k] != -1) return fail("winding signs must be +1 or -1");
+        double sum = 0;
+        for (size_t q = 0; q < nodes.size(); ++q) sum += f.winding[k] / (nodes.size() * dz * dr) * dz * dr;
+        if (std::fabs(sum - f.winding[k]) > 1e-12) return fail("shape normalisation failed");
+    }
+    std::vector<int> tn_node, tn_int, tn_k;
+    std::vector<double> gk_val;
+    const int rows = NZ - 2, M = NR - 1;
+    for (int k = 0; k < N; ++k)
+        for (int n : c->turn_nodes[k]) {
+            tn_node.push_back(n);
+            tn_int.push_back((n / NR - 1) * M + (n % NR));
+            tn_k.push_back(k);
+            gk_val.push_back(f.winding[k] / (c->turn_nodes[k].size() * dz * dr));
+        }
+    c->ntn = (int)tn_node.size();
+    if (c->ntn > kMaxCapNodes) return fail("too many turn nodes for the capacitance correction");
+    std::vector<signed char> mask(c->nnodes, -1);
+    for (int t = 0; t < c->ntn; ++t) mask[tn_node[t]] = (signed char)tn_k[t];
+
+    // ---- faces of Eq. facecharge with the areas of Eq. areas
+    std::vector<int> ft, fnb, fk;
+    std::vector<double> fc;
+    auto area_z = [&](int j) { return j == 0 ? kPi * (dr / 2) * (dr / 2) : 2 * kPi * (j * dr) * dr; };
+    for (int k = 0; k < N; ++k)
+        for (int n : c->turn_nodes[k]) {
+            int i = n / NR, j = n % NR;
+            const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+            for (int q = 0; q < 4; ++q) {
+                if (j == 0 && dj[q] == -1) continue;
+                int ii = i + di[q], jj = j + dj[q];
+                if (ii < 0 || ii >= NZ || jj < 0 || jj >= NR) continue;
+                int nb = ii * NR + jj;
+                if (owner[nb] == k) continue;
+                double A, d, eps;
+                if (di[q] != 0) {
+                    A = area_z(j);
+                    d = dz;
+                    eps = c->eps_row[di[q] > 0 ? i : i - 1];
+                } else {
+                    A = 2 * kPi * (j * dr + dj[q] * dr / 2) * dz;
+                    d = dr;
+                    eps = 0.5 * (c->eps_row[i - 1] + c->eps_row[i]);
+                }
+                ft.push_back(n);
+                fnb.push_back(nb);
+                fk.push_back(k);
+                fc.push_back(kEps0 * eps * A / d);
+            }
+        }
+    c->nfaces = (int)ft.size();
+
+    // ---- node weighting volumes (V = int S dV) of the plasma rows
+    std::vector<double> vol(c->nnodes, 0.0);
+    for (int i = 0; i <= c->i_win; ++i)
+        for (int j = 0; j < NR; ++j) {
+            double vr = 2 * kPi * (j * dr) * dr;
+            if (j == 0) vr = kPi * dr * dr / 3.0;
+            if (j == NR - 1) vr = kPi * (f.r_max * dr - dr * dr / 3.0);
+            double vz = (i == 0 || i == c->i_win) ? dz / 2.0 : dz;
+            vol[i * NR + j] = vz * vr;
+        }
+
+    // ---- per-column FV factors of the Poisson operator divided by 2 pi
+    std::vector<double> az(NR), arp(NR), arm(NR), Rn(NR);
+    for (int j = 0; j < NR; ++j) {
+        Rn[j] = j * dr;
+        az[j] = (j == 0 ? dr * dr / 8.0 : j * dr * dr) / dz;
+        arp[j] = (j * dr + dr / 2) * dz / dr;
+        arm[j] = (j == 0) ? 0.0 : (j * dr - dr / 2) * dz / dr;
+    }
+
+    // ---- allocations
+    for (int sp = 0; sp < 2; ++sp) {
+        c->cap[sp] = f.capacity[sp];
+        for (int b = 0; b < 2; ++b) {
+            ParticleBuf& p = c->pb[sp][b];
+            size_t n = (size_t)c->cap[sp];
+            p.cell = c->alloc<uint32_t>(n);
+            p.dr = c->alloc<float>(n);
+            p.dz = c->alloc<float>(n);
+            p.vr = c->alloc<float>(n);
+            p.vt = c->alloc<float>(n);
+            p.vz = c->alloc<float>(n);
+            p.uid = c->alloc<uint32_t>(n);
+            if (!p.uid) {
+                set_error("cudaMalloc failed for the particle store");
+                return PP_E_CUDA;
+            }
+        }
+    }
+    c->d_nslot = c->alloc<int>(2);
+    c->d_next_uid = c->alloc<uint32_t>(2);
+    c->d_hist = c->alloc<uint32_t>((size_t)c->i_win * c->nr + 2);
+    c->d_events = c->alloc<Event>(kEventCap);
+    c->d_phi = c->alloc<double>(c->nnodes);
+    c->d_F = c->alloc<float>((size_t)c->i_win * c->nr * 20);
+    c->d_rho = c->alloc<float>(c->nnodes);
+    c->d_jm = c->alloc<float>(c->nnodes);
+    c->d_win = c->alloc<double>(c->nnodes);
+    c->d_vol = upload<double>(c, vol);
+    c->d_Ec = c->alloc<double>(c->nnodes);
+    c->d_Ess = c->alloc<double>(c->nnodes);
+    c->d_Ecp = c->alloc<double>(c->nnodes);
+    c->d_Essp = c->alloc<double>(c->nnodes);
+    c->d_Ecp_new = c->alloc<double>(c->nnodes);
+    c->d_Essp_new = c->alloc<double>(c->nnodes);
+    c->d_Br = c->alloc<double>((size_t)4 * c->nnodes);
+    c->d_U = c->alloc<double>((size_t)N * c->nnodes);
+    c->d_Jc = c->alloc<double>(c->nnodes);
+    c->d_Js = c->alloc<double>(c->nnodes);
+    c->d_Jc_c = c->alloc<double>(c->nnodes);
+    c->d_Js_c = c->alloc<double>(c->nnodes);
+    c->d_eps_row = upload<double>(c, c->eps_row);
+    c->d_az = upload<double>(c, az);
+    c->d_arp = upload<double>(c, arp);
+    c->d_arm = upload<double>(c, arm);
+    c->d_R = upload<double>(c, Rn);
+    {
+        std::vector<double> tmp;
+        c->d_face_c = upload<double>(c, fc);
+        c->d_face_t = c->alloc<int>(ft.size());
+        c->d_face_nb = c->alloc<int>(fnb.size());
+        c->d_face_k = c->alloc<int>(fk.size());
+        cudaMemcpy(c->d_face_t, ft.data(), sizeof(int) * ft.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_face_nb, fnb.data(), sizeof(int) * fnb.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_face_k, fk.data(), sizeof(int) * fk.size(), cudaMemcpyHostToDevice);
+        c->d_tn_node = c->alloc<int>(c->ntn);
+        c->d_tn_int = c->alloc<int>(c->ntn);
+        c->d_tn_k = c->alloc<int>(c->ntn);
+        cudaMemcpy(c->d_tn_node, tn_node.data(), sizeof(int) * c->ntn, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_tn_int, tn_int.data(), sizeof(int) * c->ntn, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_tn_k, tn_k.data(), sizeof(int) * c->ntn, cudaMemcpyHostToDevice);
+        c->d_gk_val = upload<double>(c, gk_val);
+        c->d_turn_mask = c->alloc<signed char>(c->nnodes);
+        cudaMemcpy(c->d_turn_mask, mask.data(), c->nnodes, cudaMemcpyHostToDevice);
+    }
+    c->d_st = c->alloc<DevState>(1);
+    if (cudaMallocHost(&c->h_st, sizeof(DevState)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return PP_E_CUDA;
+    }
+    memset(c->h_st, 0, sizeof(DevState));
+    c->d_ext_targets = c->alloc<double>(PP_MAX_TURNS);
+    if (!c->d_st || !c->d_Js_c) {
+        set_error("cudaMalloc failed for the field grids");
+        return PP_E_CUDA;
+    }
+
+    // ---- Poisson FP32 separable solver (radial unknowns j = 0..NR-2)
+    {
+        std::vector<double> T((size_t)M * M, 0.0), D(M);
+        for (int j = 0; j < M; ++j) {
+            double bj = (j + 0.5) * dr, bm = (j > 0) ? (j - 0.5) * dr : 0.0;
+            T[(size_t)j * M + j] = -(bj + bm);
+            if (j + 1 < M) T[(size_t)j * M + j + 1] = bj;
+            if (j > 0) T[(size_t)j * M + j - 1] = bm;
+            D[j] = (j == 0) ? dr * dr / 8.0 : j * dr * dr;
+        }
+        std::vector<double> mu, V;
+        radial_basis(T, D, M, mu, V);
+        std::vector<double> Vt((size_t)M * M);
+        for (int j = 0; j < M; ++j)
+            for (int m = 0; m < M; ++m) Vt[(size_t)m * M + j] = V[(size_t)j * M + m];
+        std::vector<double> lo(rows), up(rows), diag((size_t)rows * M), cp, invd;
+        for (int ii = 0; ii < rows; ++ii) {
+            int i = ii + 1;
+            double ep = c->eps_row[i], em = c->eps_row[i - 1], eb = 0.5 * (ep + em);
+            lo[ii] = (ii > 0) ? em / dz : 0.0;
+            up[ii] = ep / dz;
+            for (int m = 0; m < M; ++m) diag[(size_t)ii * M + m] = -(ep + em) / dz + (dz / dr) * eb * mu[m];
+        }
+        thomas_factors(lo, up, diag, rows, M, cp, invd);
+        SepSolver<float>& s = c->ps;
+        s.rows = rows;
+        s.M = M;
+        s.Vf = upload<float>(c, V);
+        s.Vb = upload<float>(c, Vt);
+        s.cp = upload<float>(c, cp);
+        s.invd = upload<float>(c, invd);
+        s.lo = upload<float>(c, lo);
+        s.t0 = c->alloc<float>((size_t)rows * M);
+        s.t1 = c->alloc<float>((size_t)rows * M);
+        c->d_r32 = c->alloc<float>((size_t)rows * M);
+        c->d_sigma = c->alloc<double>(kMaxCapNodes);
+        c->d_rT = c->alloc<double>(kMaxCapNodes);
+    }
+    // ---- Helmholtz FP64 separable solver (radial unknowns j = 1..NR-2)
+    {
+        int MH = NR - 2;
+        std::vector<double> T((size_t)MH * MH, 0.0), D(MH);
+        for (int jj = 0; jj < MH; ++jj) {
+            int j = jj + 1;
+            double R = j * dr, bj = R + dr / 2, bm = R - dr / 2;
+            T[(size_t)jj * MH + jj] = -(bj + bm) / (dr * dr) - 1.0 / R;
+            if (jj + 1 < MH) T[(size_t)jj * MH + jj + 1] = bj / (dr * dr);
+            if (jj > 0) T[(size_t)jj * MH + jj - 1] = bm / (dr * dr);
+            D[jj] = R;
+        }
+        std::vector<double> mu, V;
+        radial_basis(T, D, MH, mu, V);
+        std::vector<double> Vf((size_t)MH * MH), Vb((size_t)MH * MH);
+        for (int jj = 0; jj < MH; ++jj)
+            for (int m = 0; m < MH; ++m) {
+                Vf[(size_t)jj * MH + m] = D[jj] * V[(size_t)jj * MH + m];
+                Vb[(size_t)m * MH + jj] = V[(size_t)jj * MH + m];
+            }
+        double k2base = f.full_helmholtz ? kMu0 * kEps0 * c->omega * c->omega : 0.0;
+        std::vector<double> lo(rows), up(rows), diag((size_t)rows * MH), cp, invd;
+        for (int ii = 0; ii < rows; ++ii) {
+            int i = ii + 1;
+            double epsn = 0.5 * (c->eps_row[i - 1] + c->eps_row[i]);
+            lo[ii] = (ii > 0) ? 1.0 / (dz * dz) : 0.0;
+            up[ii] = 1.0 / (dz * dz);
+            for (int m = 0; m < MH; ++m) diag[(size_t)ii * MH + m] = -2.0 / (dz * dz) + mu[m] + k2base * epsn;
+        }
+        thomas_factors(lo, up, diag, rows, MH, cp, invd);
+        SepSolver<double>& s = c->hs;
+        s.rows = rows;
+        s.M = MH;
+        s.Vf = upload<double>(c, Vf);
+        s.Vb = upload<double>(c, Vb);
+        s.cp = upload<double>(c, cp);
+        s.invd = upload<double>(c, invd);
+        s.lo = upload<double>(c, lo);
+        s.t0 = c->alloc<double>((size_t)rows * MH);
+        s.t1 = c->alloc<double>((size_t)rows * MH);
+        c->d_hstage = c->alloc<double>((size_t)2 * rows * MH);
+    }
+    if (!c->d_hstage) {
+        set_error("cudaMalloc failed for the solver storage");
+        return PP_E_CUDA;
+    }
+
+    species_constants(c);
+
+    // ---- unit fields K U_k = g_k (Eq. unitfield) and Z_vac (Eq. zvac)
+    std::vector<double> gk((size_t)c->nnodes, 0.0);
+    std::vector<double> Uh((size_t)N * c->nnodes);
+    double* d_g = c->alloc<double>(c->nnodes);
+    for (int k = 0; k < N; ++k) {
+        std::fill(gk.begin(), gk.end(), 0.0);
+        double g = f.winding[k] / (c->turn_nodes[k].size() * dz * dr);
+        for (int n : c->turn_nodes[k]) gk[n] = g;
+        cudaMemcpy(d_g, gk.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
+        helmholtz_solve_dev(c, d_g, c->d_U + (size_t)k * c->nnodes, kMu0 * c->omega, 0);
+    }
+    cudaMemcpy(Uh.data(), c->d_U, sizeof(double) * N * c->nnodes, cudaMemcpyDeviceToHost);
+    c->zvac.assign(2 * N * N, 0.0);
+    double zmax = 0, dmax = 0;
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l < N; ++l) {
+            double s = 0;
+            double g = f.winding[k] / (c->turn_nodes[k].size() * dz * dr);
+            for (int n : c->turn_nodes[k]) s += g * Uh[(size_t)l * c->nnodes + n] * 2 * kPi * ((n % NR) * dr) * dz * dr;
+            c->zvac[2 * (k * N + l)] = 0.0;
+            c->zvac[2 * (k * N + l) + 1] = -s;        // -i * s
+        }
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l < N; ++l) {
+            zmax = std::max(zmax, std::fabs(c->zvac[2 * (k * N + l) + 1]));
+            dmax = std::max(dmax, std::fabs(c->zvac[2 * (k * N + l) + 1] - c->zvac[2 * (l * N + k) + 1]));
+        }
+    c->eps_rec = zmax > 0 ? dmax / zmax : 0.0;
+
+    // ---- R_rf (Eq. skin), Z_source (Eq. zsource), network (Eq. blockmatrix)
+    c->r_rf.assign(N, 0.0);
+    if (f.r_rf_override >= 0) {
+        for (int k = 0; k < N; ++k) c->r_rf[k] = f.r_rf_override;
+    } else {
+        double rho = f.rho20 * (1.0 + f.alpha_cu * (f.t_coil_c - 20.0));
+        double delta = std::sqrt(2.0 * rho / (c->omega * kMu0));
+        double inner = std::max(f.wire_radius - delta, 0.0);
+        for (int k = 0; k < N; ++k)
+            c->r_rf[k] = rho * 2 * kPi * f.turn_r[k] / (kPi * (f.wire_radius * f.wire_radius - inner * inner));
+    }
+    double xs = c->omega * f.l_m;
+    if (f.c_m > 0) xs -= 1.0 / (c->omega * f.c_m);
+    cd zs(f.r_g + f.r_m, xs);
+    const int NX = 2 * N + 1;
+    std::vector<cd> A((size_t)NX * NX, cd(0, 0));
+    std::vector<cd> zt((size_t)N * N);
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l < N; ++l)
+            zt[(size_t)k * N + l] = cd(c->zvac[2 * (k * N + l)], c->zvac[2 * (k * N + l) + 1]) + (k == l ? c->r_rf[k] : 0.0);
+    A[0] = zs;
+    A[1 + N] = 1.0;
+    for (int k = 0; k < N; ++k) {
+        int r = 1 + k;
+        A[(size_t)r * NX + (k == 0 ? 0 : k)] = 1.0;          // I_in,k
+        A[(size_t)r * NX + 1 + k] = -1.0;
+        A[(size_t)r * NX + 1 + N + k] = cd(0, -c->omega * f.c_stray[k]);
+        int r2 = 1 + N + k;
+        for (int l = 0; l < N; ++l) A[(size_t)r2 * NX + 1 + l] = -zt[(size_t)k * N + l];
+        A[(size_t)r2 * NX + 1 + N + k] = 1.0;
+        if (k + 1 < N) A[(size_t)r2 * NX + 1 + N + k + 1] = -1.0;
+    }
+    std::vector<cd> Ainv = A;
+    if (!invert(Ainv, NX)) return fail("network matrix is singular");
+    std::vector<double> ainv(2 * NX * NX), ztv(2 * N * N), circ(2 + 2 * N);
+    for (int q = 0; q < NX * NX; ++q) {
+        ainv[2 * q] = Ainv[q].real();
+        ainv[2 * q + 1] = Ainv[q].imag();
+    }
+    for (int q = 0; q < N * N; ++q) {
+        ztv[2 * q] = zt[q].real();
+        ztv[2 * q + 1] = zt[q].imag();
+    }
+    circ[0] = zs.real();
+    circ[1] = zs.imag();
+    for (int k = 0; k < N; ++k) {
+        circ[2 + k] = c->r_rf[k];
+        circ[2 + N + k] = f.c_stray[k];
+    }
+    c->d_Ainv = upload<double>(c, ainv);
+    c->d_zturn = upload<double>(c, ztv);
+    c->d_circ = upload<double>(c, circ);
+
+    // ---- x^1: zero-load network solution
+    cd vg(f.v_g * std::cos(f.phase_g), f.v_g * std::sin(f.phase_g));
+    DevState* h = c->h_st;
+    for (int q = 0; q < NX; ++q) {
+        cd x = Ainv[(size_t)q * NX + 0] * vg;
+        h->x[2 * q] = x.real();
+        h->x[2 * q + 1] = x.imag();
+    }
+    h->vg_amp = f.v_g;
+    cudaMemcpy(c->d_st, h, sizeof(DevState), cudaMemcpyHostToDevice);
+    launch_compose(c, false, 0);
+
+    // ---- capacitance correction: Z_t = P(e_t), G = Z_T, G^-1
+    {
+        int K = c->ntn;
+        size_t nint = (size_t)rows * M;
+        c->d_Z = c->alloc<float>((size_t)K * nint);
+        std::vector<float> e(nint, 0.0f);
+        for (int t = 0; t < K; ++t) {
+            std::fill(e.begin(), e.end(), 0.0f);
+            e[tn_int[t]] = 1.0f;
+            cudaMemcpy(c->d_r32, e.data(), sizeof(float) * nint, cudaMemcpyHostToDevice);
+            sep_solve<float>(c->ps, c->d_r32, c->d_Z + (size_t)t * nint, 0, nullptr);
+        }
+        std::vector<float> Zh((size_t)K * nint);
+        cudaMemcpy(Zh.data(), c->d_Z, sizeof(float) * K * nint, cudaMemcpyDeviceToHost);
+        std::vector<double> G((size_t)K * K);
+        for (int t = 0; t < K; ++t)
+            for (int u = 0; u < K; ++u) G[(size_t)t * K + u] = Zh[(size_t)u * nint + tn_int[t]];
+        if (!invert(G, K)) return fail("capacitance matrix is singular");
+        c->d_Ginv = upload<double>(c, G);
+    }
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        set_error(std::string("CUDA error during init: ") + cudaGetErrorString(err));
+        return PP_E_CUDA;
+    }
+    return PP_OK;
+}
+
+}  // namespace pp

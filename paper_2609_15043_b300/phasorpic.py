@@ -1,0 +1,343 @@
+"""ctypes binding of libphasorpic.so (include/phasorpic.h): argument
+marshalling only.  Every step of the hot path runs in the library's CUDA
+kernels; there is no Python or CPU fallback -- importing this module raises
+if the library is missing or fails to load.
+
+Arrays cross the boundary as host numpy buffers; streams as integer
+cudaStream_t handles (0 = legacy default stream; pass
+``torch.cuda.current_stream().cuda_stream`` to run on torch's stream).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphasorpic.so")
+
+MAX_TURNS = 8
+NSPECIES = 2
+
+PP_OK = 0
+ERRORS = {-1: "PP_E_CONFIG", -2: "PP_E_NOCONV", -3: "PP_E_SAMPLES", -4: "PP_E_NAN", -5: "PP_E_TIMEOUT",
+          -6: "PP_E_CUDA", -7: "PP_E_ARG", -8: "PP_E_CAPACITY"}
+ST_NOCONV, ST_EVENTS, ST_CAPACITY, ST_SAMPLES = 1, 2, 4, 8
+
+GRID_PHI, GRID_EC, GRID_ESS, GRID_JC, GRID_JS, GRID_WINDOW, GRID_CHARGE, GRID_JMOM = range(8)
+GRID_U0 = 16
+
+EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp_last_error",
+           "pp_set_particles", "pp_get_particles", "pp_prime", "pp_advance_steps", "pp_advance_period",
+           "pp_set_circuit_state", "pp_get_circuit_state", "pp_get_turn_phasors",
+           "pp_get_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
+           "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
+           "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index"]
+PHASES = ["push", "poisson", "sort", "other", "period_end"]
+
+
+class PPConfig(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int32), ("nz", C.c_int32),
+        ("r_max", C.c_double), ("z_max", C.c_double),
+        ("z_win_lo", C.c_double), ("z_win_hi", C.c_double), ("eps_win", C.c_double), ("z_coil", C.c_double),
+        ("n_turns", C.c_int32),
+        ("winding", C.c_int32 * MAX_TURNS),
+        ("turn_r", C.c_double * MAX_TURNS),
+        ("wire_radius", C.c_double),
+        ("freq", C.c_double), ("dt", C.c_double),
+        ("full_helmholtz", C.c_int32), ("magnetic_force", C.c_int32),
+        ("pressure_pa", C.c_double), ("t_gas", C.c_double),
+        ("r_g", C.c_double), ("r_m", C.c_double), ("l_m", C.c_double), ("c_m", C.c_double),
+        ("c_stray", C.c_double * MAX_TURNS),
+        ("rho20", C.c_double), ("alpha_cu", C.c_double), ("t_coil_c", C.c_double),
+        ("r_rf_override", C.c_double),
+        ("v_g", C.c_double), ("phase_g", C.c_double),
+        ("power_control", C.c_int32),
+        ("p_target", C.c_double), ("gamma", C.c_double), ("n_trend", C.c_double), ("eps_p", C.c_double),
+        ("alpha_v", C.c_double), ("f_step", C.c_double), ("v_min", C.c_double), ("v_max", C.c_double),
+        ("alpha", C.c_double),
+        ("weight", C.c_double * NSPECIES),
+        ("capacity", C.c_int64 * NSPECIES),
+        ("seed", C.c_uint64),
+        ("sort_every", C.c_int32 * NSPECIES),
+        ("poisson_max_iter", C.c_int32),
+        ("poisson_tol", C.c_double),
+    ]
+
+
+class PPRecord(C.Structure):
+    _fields_ = [
+        ("period", C.c_int64), ("n_samples", C.c_int32), ("accepted", C.c_int32),
+        ("n_turns", C.c_int32), ("pad0", C.c_int32),
+        ("vp", C.c_double * (2 * MAX_TURNS)), ("icap", C.c_double * (2 * MAX_TURNS)),
+        ("qhat", C.c_double * (2 * MAX_TURNS)),
+        ("x_applied", C.c_double * (2 * (2 * MAX_TURNS + 1))),
+        ("x_next", C.c_double * (2 * (2 * MAX_TURNS + 1))),
+        ("vg", C.c_double), ("vg_next", C.c_double),
+        ("p_port", C.c_double), ("p_ind", C.c_double), ("p_cap", C.c_double), ("p_cap_ph", C.c_double),
+        ("p_cu", C.c_double), ("p_es", C.c_double), ("eps_bal", C.c_double),
+        ("r_kcl", C.c_double), ("r_kvl", C.c_double),
+        ("particle_steps", C.c_double),
+        ("n_live", C.c_int64 * NSPECIES),
+        ("coll", (C.c_int64 * 3) * NSPECIES),
+        ("absorbed", C.c_int64), ("created", C.c_int64), ("nu_violations", C.c_int64),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libphasorpic.so is not built (run paper_2609_15043_b300/build_lib.py); "
+                          "there is no fallback implementation")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, V = C.POINTER, C.c_int, C.c_double, C.c_void_p
+    sig = {
+        "pp_config_size": (C.c_int32, []),
+        "pp_record_size": (C.c_int32, []),
+        "pp_init_cell": (I, [P(PPConfig), P(V)]),
+        "pp_destroy": (I, [V]),
+        "pp_last_error": (C.c_char_p, []),
+        "pp_set_particles": (I, [V, I, C.c_int64, V, V, V, V, V, V, V]),
+        "pp_get_particles": (I, [V, I, C.c_int64, P(C.c_int64), V, V, V, V, V, V, V, V]),
+        "pp_prime": (I, [V, V]),
+        "pp_advance_steps": (I, [V, I, V]),
+        "pp_advance_period": (I, [V, I, V]),
+        "pp_set_circuit_state": (I, [V, V, D]),
+        "pp_get_circuit_state": (I, [V, V, P(D), V]),
+        "pp_get_turn_phasors": (I, [V, P(PPRecord), V]),
+        "pp_get_vacuum_impedance": (I, [V, V, P(D), V]),
+        "pp_get_grid": (I, [V, I, V, C.c_int64, V]),
+        "pp_set_potential": (I, [V, V]),
+        "pp_poisson_solve": (I, [V, V, V, V, V, P(I), P(D)]),
+        "pp_helmholtz_solve": (I, [V, V, V]),
+        "pp_get_status": (I, [V, P(C.c_uint32), V]),
+        "pp_get_counters": (I, [V, V, V]),
+        "pp_get_poisson_stats": (I, [V, P(I), V, V]),
+        "pp_set_profiling": (I, [V, I]),
+        "pp_get_phase_times": (I, [V, V, V]),
+        "pp_launch_count": (C.c_int64, []),
+        "pp_n_rf": (I, [V]),
+        "pp_step_index": (C.c_int64, [V]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.pp_config_size() != C.sizeof(PPConfig) or lib.pp_record_size() != C.sizeof(PPRecord):
+        raise ImportError("libphasorpic.so struct layout does not match the binding")
+    return lib
+
+
+lib = _load()
+
+
+class PhasorPICError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != PP_OK:
+        msg = lib.pp_last_error().decode(errors="replace")
+        raise PhasorPICError("%s: %s (%s)" % (what, ERRORS.get(rc, rc), msg))
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def make_config(cfg, capacity=None, weight=None, poisson_max_iter=4, poisson_tol=1e-10):
+    """pp_config from a workloads.CellConfig."""
+    c = PPConfig()
+    c.nr, c.nz = cfg.nr, cfg.nz
+    c.r_max, c.z_max = cfg.r_max, cfg.z_max
+    c.z_win_lo, c.z_win_hi, c.eps_win, c.z_coil = cfg.z_win_lo, cfg.z_win_hi, cfg.eps_win, cfg.z_coil
+    n = len(cfg.turn_r)
+    c.n_turns = n
+    for k in range(n):
+        c.turn_r[k] = cfg.turn_r[k]
+        c.winding[k] = cfg.winding[k]
+    c.wire_radius = cfg.wire_radius
+    c.freq, c.dt = cfg.freq, cfg.dt
+    c.full_helmholtz, c.magnetic_force = cfg.full_helmholtz, cfg.magnetic_force
+    c.pressure_pa, c.t_gas = cfg.pressure_pa, cfg.t_gas
+    c.r_g, c.r_m, c.l_m, c.c_m = cfg.r_g, cfg.r_m, cfg.l_m, cfg.c_m
+    for k in range(MAX_TURNS):
+        c.c_stray[k] = cfg.c_stray[k] if k < len(cfg.c_stray) else 0.0
+    c.rho20, c.alpha_cu, c.t_coil_c, c.r_rf_override = cfg.rho20, cfg.alpha_cu, cfg.t_coil_c, cfg.r_rf_override
+    c.v_g, c.phase_g = cfg.v_g, cfg.phase_g
+    c.power_control = cfg.power_control
+    c.p_target, c.gamma, c.n_trend, c.eps_p = cfg.p_target, cfg.gamma, cfg.n_trend, cfg.eps_p
+    c.alpha_v, c.f_step, c.v_min, c.v_max, c.alpha = cfg.alpha_v, cfg.f_step, cfg.v_min, cfg.v_max, cfg.alpha
+    w = workloads.macro_weight(cfg) if weight is None else weight
+    cap = int(cfg.n_init * cfg.capacity_factor) + 4096 if capacity is None else capacity
+    for s in range(2):
+        c.weight[s] = w
+        c.capacity[s] = cap
+    c.seed = cfg.seed
+    c.sort_every[0], c.sort_every[1] = cfg.sort_every_e, cfg.sort_every_i
+    c.poisson_max_iter = poisson_max_iter
+    c.poisson_tol = poisson_tol
+    return c
+
+
+class Cell:
+    """One RF cell on the current CUDA device (pp_init_cell ... pp_destroy)."""
+
+    def __init__(self, cfg, **kw):
+        self.cfg = cfg
+        self.pcfg = make_config(cfg, **kw)
+        h = C.c_void_p()
+        _check(lib.pp_init_cell(C.byref(self.pcfg), C.byref(h)), "pp_init_cell")
+        self.h = h
+        self.n_turns = len(cfg.turn_r)
+        self.NZ, self.NR = cfg.nz + 1, cfg.nr + 1
+
+    def close(self):
+        if self.h:
+            lib.pp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_rf(self):
+        return lib.pp_n_rf(self.h)
+
+    @property
+    def step_index(self):
+        return lib.pp_step_index(self.h)
+
+    def set_particles(self, sp, p):
+        n = len(p["cell"])
+        arr = {k: np.ascontiguousarray(p[k], dtype=np.uint32 if k in ("cell", "uid") else np.float32)
+               for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")}
+        _check(lib.pp_set_particles(self.h, sp, n, *[_ptr(arr[k]) for k in
+                                                     ("cell", "dr", "dz", "vr", "vt", "vz", "uid")]),
+               "pp_set_particles")
+
+    def get_particles(self, sp, cap=None, stream=0):
+        if cap is None:
+            cap = int(self.pcfg.capacity[sp])
+        out = {k: np.empty(cap, np.uint32 if k in ("cell", "uid") else np.float32)
+               for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")}
+        n = C.c_int64()
+        _check(lib.pp_get_particles(self.h, sp, cap, C.byref(n),
+                                    *[_ptr(out[k]) for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")],
+                                    C.c_void_p(stream)), "pp_get_particles")
+        return {k: v[:n.value] for k, v in out.items()}
+
+    def prime(self, stream=0):
+        _check(lib.pp_prime(self.h, C.c_void_p(stream)), "pp_prime")
+
+    def advance_steps(self, n, stream=0):
+        _check(lib.pp_advance_steps(self.h, n, C.c_void_p(stream)), "pp_advance_steps")
+
+    def advance_period(self, n=1, stream=0):
+        _check(lib.pp_advance_period(self.h, n, C.c_void_p(stream)), "pp_advance_period")
+
+    def set_circuit_state(self, x, vg):
+        x = np.ascontiguousarray(np.asarray(x, complex).view(np.float64))
+        _check(lib.pp_set_circuit_state(self.h, _ptr(x), float(vg)), "pp_set_circuit_state")
+
+    def circuit_state(self, stream=0):
+        x = np.zeros(2 * (2 * self.n_turns + 1))
+        vg = C.c_double()
+        _check(lib.pp_get_circuit_state(self.h, _ptr(x), C.byref(vg), C.c_void_p(stream)),
+               "pp_get_circuit_state")
+        return x.view(complex), vg.value
+
+    def turn_phasors(self, stream=0):
+        r = PPRecord()
+        _check(lib.pp_get_turn_phasors(self.h, C.byref(r), C.c_void_p(stream)), "pp_get_turn_phasors")
+        return record_dict(r, self.n_turns)
+
+    def vacuum_impedance(self):
+        z = np.zeros(2 * self.n_turns * self.n_turns)
+        e = C.c_double()
+        rrf = np.zeros(self.n_turns)
+        _check(lib.pp_get_vacuum_impedance(self.h, _ptr(z), C.byref(e), _ptr(rrf)), "pp_get_vacuum_impedance")
+        return z.view(complex).reshape(self.n_turns, self.n_turns), e.value, rrf
+
+    def grid(self, which, stream=0):
+        out = np.zeros(self.NZ * self.NR)
+        _check(lib.pp_get_grid(self.h, which, _ptr(out), out.size, C.c_void_p(stream)), "pp_get_grid")
+        return out.reshape(self.NZ, self.NR)
+
+    def set_potential(self, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        _check(lib.pp_set_potential(self.h, _ptr(phi)), "pp_set_potential")
+
+    def poisson_solve(self, q, turn_phi):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        tp = np.ascontiguousarray(turn_phi, dtype=np.float64)
+        phi = np.zeros(self.NZ * self.NR)
+        qk = np.zeros(self.n_turns)
+        it = C.c_int()
+        rel = C.c_double()
+        _check(lib.pp_poisson_solve(self.h, _ptr(q), _ptr(tp), _ptr(phi), _ptr(qk), C.byref(it), C.byref(rel)),
+               "pp_poisson_solve")
+        return phi.reshape(self.NZ, self.NR), qk, it.value, rel.value
+
+    def helmholtz_solve(self, rhs):
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        e = np.zeros(self.NZ * self.NR)
+        _check(lib.pp_helmholtz_solve(self.h, _ptr(rhs), _ptr(e)), "pp_helmholtz_solve")
+        return e.reshape(self.NZ, self.NR)
+
+    def status(self, stream=0):
+        s = C.c_uint32()
+        _check(lib.pp_get_status(self.h, C.byref(s), C.c_void_p(stream)), "pp_get_status")
+        return s.value
+
+    def counters(self, stream=0):
+        out = np.zeros(12, np.int64)
+        _check(lib.pp_get_counters(self.h, _ptr(out), C.c_void_p(stream)), "pp_get_counters")
+        keys = ["particle_steps", "absorbed", "created", "e_elastic", "e_excitation", "e_ionisation",
+                "i_cx", "i_isotropic", "nu_violations", "steps", "live_e", "live_i"]
+        return dict(zip(keys, out.tolist()))
+
+
+def _poisson_stats(self, stream=0):
+    n = C.c_int()
+    rel = np.zeros(16)
+    _check(lib.pp_get_poisson_stats(self.h, C.byref(n), _ptr(rel), C.c_void_p(stream)), "pp_get_poisson_stats")
+    return rel[:n.value]
+
+
+Cell.poisson_stats = _poisson_stats
+
+
+def _set_profiling(self, on=True):
+    _check(lib.pp_set_profiling(self.h, 1 if on else 0), "pp_set_profiling")
+
+
+def _phase_times(self):
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), np.int64)
+    _check(lib.pp_get_phase_times(self.h, _ptr(ms), _ptr(cnt)), "pp_get_phase_times")
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PHASES)}
+
+
+Cell.set_profiling = _set_profiling
+Cell.phase_times = _phase_times
+
+
+def launch_count():
+    return int(lib.pp_launch_count())
+
+
+def record_dict(r, n):
+    cplx = lambda a, m: np.array(a[:2 * m]).view(complex)
+    return dict(period=r.period, n_samples=r.n_samples, accepted=bool(r.accepted),
+                vp=cplx(r.vp, n), icap=cplx(r.icap, n), qhat=cplx(r.qhat, n),
+                x_applied=cplx(r.x_applied, 2 * n + 1), x_next=cplx(r.x_next, 2 * n + 1),
+                vg=r.vg, vg_next=r.vg_next, p_port=r.p_port, p_ind=r.p_ind, p_cap=r.p_cap,
+                p_cap_ph=r.p_cap_ph, p_cu=r.p_cu, p_es=r.p_es, eps_bal=r.eps_bal,
+                r_kcl=r.r_kcl, r_kvl=r.r_kvl, particle_steps=r.particle_steps,
+                n_live=list(r.n_live), coll=np.array([list(r.coll[0]), list(r.coll[1])]),
+                absorbed=r.absorbed, created=r.created, nu_violations=r.nu_violations)
