@@ -56,6 +56,19 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(ms, psteps, dist):
+    """Whole-job timing: the max of the per-rank device times and the sum of
+    the particle-steps of all ranks (CPU tensors, any backend)."""
+    import torch
+    if dist is None:
+        return ms, float(psteps)
+    t = torch.tensor([ms], dtype=torch.float64)
+    p = torch.tensor([float(psteps)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(p[0])
+
+
 def workload_desc(cfg, name):
     return ("%s: %dx%d cells over r<=%.2f m, z<=%.2f m, %d macroparticles/species, %d turns, Ar %.0f mTorr, "
             "dt=T/%d%s" % (name, cfg.nr, cfg.nz, cfg.r_max, cfg.z_max, cfg.n_init, len(cfg.turn_r),
@@ -212,7 +225,8 @@ def run_ours(args, cfg, ws, rank, local):
     dist = None
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        # timing reductions run on CPU tensors: gloo for them, no data-path collective
+        dist.init_process_group("gloo")
     from paper_2609_15043_b300 import phasorpic as pp, workloads
     cfg = cfg.replace(seed=cfg.seed + rank)
     cell = pp.Cell(cfg)
@@ -251,13 +265,7 @@ def run_ours(args, cfg, ws, rank, local):
     launches = pp.launch_count() - l0
     c1 = cell.counters()
     psteps = c1["particle_steps"] - c0["particle_steps"]
-    t = torch.tensor([ms, float(psteps)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        t[0] = tmax[0]
-    ms_all, ps_all = float(t[0]), float(t[1])
+    ms_all, ps_all = reduce_over_ranks(ms, psteps, dist)
     value = ps_all / (ms_all / 1e3)
 
     # ---- end to end through the C ABI with host buffers

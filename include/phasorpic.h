@@ -57,6 +57,7 @@ extern "C" {
 #define PP_ST_EVENTS 2u          /* ionisation events dropped (per-step event buffer full) */
 #define PP_ST_CAPACITY 4u        /* new particles dropped (particle capacity full) */
 #define PP_ST_SAMPLES 8u         /* a period ended with a wrong sample count */
+#define PP_ST_TIMEOUT 16u        /* a bounded device wait expired (a staged copy did not complete) */
 
 /*
  * Cell configuration.  Plain data; every length in metres, time in seconds.

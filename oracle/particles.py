@@ -10,8 +10,9 @@ from the textbook methods:
     z), then the move in that frame, r' = |(r + dx, dy)|, and the velocity
     rotated by the angle between the old and new radial directions;
   * null-collision MCC (Vahedi & Surendra 1995, cited in Sec. 3.4): a particle
-    is a candidate with probability P_null = 1 - exp(-nu_max dt); its process
-    is chosen by comparing u * nu_max with the cumulative real frequencies.
+    is a candidate with probability P_null = 1 - exp(-nu_max dt) (uniform from
+    Philox2x32-10); a candidate's process is chosen by comparing u * nu_max
+    with the cumulative real frequencies (uniforms from Philox4x32-10).
 
 The step is written once over a dtype T.  With T = float32 every operation is
 a single IEEE float32 operation in the order the kernels use, so integer
@@ -202,8 +203,9 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     den = rho + rp
     with np.errstate(divide='ignore', invalid='ignore'):
         delta = np.where(den > zero, (a * (rho + x1) + b * b) / den, zero).astype(T)
-        ca = np.where(rp > zero, x1 / rp, one).astype(T)
-        sa = np.where(rp > zero, b / rp, zero).astype(T)
+        inv = np.where(rp > zero, one / rp, zero).astype(T)
+        ca = np.where(rp > zero, x1 * inv, one).astype(T)
+        sa = np.where(rp > zero, b * inv, zero).astype(T)
     vr2 = np.where(rp > zero, ca * vnx + sa * vny, vnx).astype(T)
     vt2 = np.where(rp > zero, ca * vny - sa * vnx, vny).astype(T)
     drn = dr + delta
@@ -241,7 +243,8 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
 
     # --- null-collision MCC at the new position -------------------------------
     uid = P['uid'][idx]
-    u0, u1, u2, u3 = philox.draws(uid, step, 0, sc.sp, seed, T)
+    u0 = philox.null_draw(uid, step, sc.sp, seed, T)
+    _, u1, u2, u3 = philox.draws(uid, step, 0, sc.sp, seed, T)
     cand = alive & (u0 < sc.pnull)
     events = []
     ci = np.nonzero(cand)[0]

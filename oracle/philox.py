@@ -11,7 +11,10 @@ The draws the PIC step consumes are addressed by
     counter = (uid, step, call, species),  key = (seed & 0xffffffff, seed >> 32)
 so a particle's random numbers depend only on its identity and the step, never
 on its position in memory (the kernels keep particles in cell order, the oracle
-in any order).
+in any order).  The null-collision test of every particle uses the cheaper
+Philox2x32-10 (same paper) at counter (uid, step | species << 31) under the key
+(seed & 0xffffffff) ^ (seed >> 32); the draws of actual collision candidates
+come from Philox4x32-10.
 
 Uniform conversion: u = ((x >> 9) + 0.5) * 2**-23, which lies in (0, 1) and is
 exact in float32 (at most 24 significant bits).
@@ -45,6 +48,37 @@ def philox4x32(c0, c1, c2, c3, k0, k1, rounds=10):
         lo1 = (p1 & _MASK).astype(np.uint32)
         c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
     return c0, c1, c2, c3
+
+
+M2 = np.uint64(0xD256D193)
+
+
+def philox2x32(c0, c1, k, rounds=10):
+    """Philox2x32-R (same paper): round (c0, c1; k) -> (hi(M c0) ^ k ^ c1,
+    lo(M c0)) with M = 0xD256D193, key bumped by 0x9E3779B9 between rounds."""
+    c0 = np.array(c0, dtype=np.uint32)
+    c1 = np.array(c1, dtype=np.uint32)
+    c0, c1 = np.broadcast_arrays(c0, c1)
+    c0, c1 = np.array(c0, dtype=np.uint32), np.array(c1, dtype=np.uint32)
+    k = int(k) & 0xFFFFFFFF
+    for r in range(rounds):
+        if r > 0:
+            k = (k + int(W0)) & 0xFFFFFFFF
+        p = M2 * c0.astype(np.uint64)
+        hi = (p >> _SH).astype(np.uint32)
+        lo = (p & _MASK).astype(np.uint32)
+        c0, c1 = hi ^ np.uint32(k) ^ c1, lo
+    return c0, c1
+
+
+def null_draw(uid, step, species, seed, dtype=np.float32):
+    """The per-particle uniform of the null-collision test: first output of
+    Philox2x32-10 at counter (uid, step | species << 31) under the key
+    (seed & 0xffffffff) ^ (seed >> 32)."""
+    uid = np.asarray(uid, dtype=np.uint32)
+    c1 = np.uint32((step & 0x7FFFFFFF) | (species << 31))
+    out, _ = philox2x32(uid, np.full(uid.shape, c1, np.uint32), (seed & 0xFFFFFFFF) ^ ((seed >> 32) & 0xFFFFFFFF))
+    return to_uniform(out, dtype)
 
 
 def to_uniform(x, dtype=np.float32):

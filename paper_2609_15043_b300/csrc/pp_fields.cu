@@ -127,6 +127,7 @@ template void sep_solve<float>(const SepSolver<float>&, const float*, float*, cu
 template void sep_solve<double>(const SepSolver<double>&, const double*, double*, cudaStream_t, const int*);
 
 // ---------------------------------------------------------------- Poisson
+
 __device__ __forceinline__ double turn_target(const DevState* st, const double* ext, int k, int nt,
                                               double cs, double sn) {
     if (ext) return ext[k];
@@ -485,6 +486,11 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
         count_launch(2);
     }
     return 0;
+}
+
+// FP32 inner solve alone (used at initialisation for the capacitance columns)
+void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st) {
+    sep_solve<float>(c->ps, rhs, out, st, nullptr);
 }
 
 }  // namespace pp

@@ -122,6 +122,7 @@ struct Cell {
     ParticleBuf pb[2][2];
     int cur[2] = {0, 0};
     int64_t cap[2] = {0, 0};
+    uint32_t div_magic = 0, div_shift = 0;  // cell / nr by multiply-high and shift
     int* d_nslot = nullptr;                 // [2] used slots (live + absorbed since last sort)
     uint32_t* d_next_uid = nullptr;         // [2]
     uint32_t* d_hist = nullptr;             // counting-sort bins (ncell + 2)
@@ -215,6 +216,7 @@ void launch_sort(Cell* c, int sp, cudaStream_t st);
 void launch_deposit_only(Cell* c, cudaStream_t st);
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
                    const double* d_targets);
+void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st);
 void launch_turn_sample(Cell* c, double cs_new, double sn_new, cudaStream_t st);
 void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st);
 void period_end(Cell* c, cudaStream_t st);

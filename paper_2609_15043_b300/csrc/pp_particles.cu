@@ -30,6 +30,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// Philox2x32-10 (same paper): round (c0, c1; k) -> (hi(M c0) ^ k ^ c1, lo(M c0)),
+// M = 0xD256D193, key bumped by 0x9E3779B9; first output only
+__device__ __forceinline__ uint32_t philox2x32_10(uint32_t c0, uint32_t c1, uint32_t k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) k += 0x9E3779B9u;
+        uint32_t hi = __umulhi(0xD256D193u, c0), lo = 0xD256D193u * c0;
+        c0 = hi ^ k ^ c1;
+        c1 = lo;
+    }
+    return c0;
+}
+
 // ((x >> 9) + 0.5) * 2^-23, exact in float32, in (0, 1)
 __device__ __forceinline__ float u01(uint32_t x) {
     return (float)(int)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
@@ -85,7 +98,59 @@ __device__ __forceinline__ void gauss3(float a, float b, float c, float d, float
     n2 = rc * cd;
 }
 
+// ---------------------------------------------------------------- TMA bulk copies
+// 1-D bulk copies between global and shared memory (cp.async.bulk), completed
+// through an mbarrier transaction count; sizes and addresses are multiples of
+// 16 bytes (chunk bases are multiples of kChunk elements; storage is padded).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait: false when the phase did not complete within the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t addr = smem_u32(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // ---------------------------------------------------------------- deposition
+// Register accumulator of the bilinear node weights of one cell.  A thread's
+// particles are consecutive in the cell-sorted store, so most of them share
+// the accumulated cell.
+struct DepAcc {
+    int iz, ir;       // accumulated cell; iz = -1 when empty
+    float v0, v1, v2, v3;
+};
+
 struct Tile {
     float* s;      // shared rows [lo, lo + rows)
     int lo, rows;
@@ -93,14 +158,18 @@ struct Tile {
     int NR;
 };
 
-__device__ __forceinline__ void add4(const Tile& t, int iz, int ir, float v0, float v1, float v2, float v3) {
+// shared and global targets take separate branches so that each compiles to
+// the native atomic of its state space (a pointer that may be either would
+// force generic atomics)
+__device__ __forceinline__ void tile_add4(const Tile& t, int iz, int ir, float v0, float v1, float v2, float v3) {
     int r0 = iz - t.lo;
     if (r0 >= 0 && r0 + 1 < t.rows) {
-        float* p = t.s + r0 * t.NR + ir;
-        atomicAdd(p, v0);
-        atomicAdd(p + 1, v1);
-        atomicAdd(p + t.NR, v2);
-        atomicAdd(p + t.NR + 1, v3);
+        uint32_t a = smem_u32(t.s + r0 * t.NR + ir);
+        uint32_t b = a + 4u * (uint32_t)t.NR;
+        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v0));
+        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a + 4u), "f"(v1));
+        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b), "f"(v2));
+        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b + 4u), "f"(v3));
     } else {
         float* p = t.g + iz * t.NR + ir;
         atomicAdd(p, v0);
@@ -110,34 +179,79 @@ __device__ __forceinline__ void add4(const Tile& t, int iz, int ir, float v0, fl
     }
 }
 
-// Warp-aggregated bilinear deposit: the largest group of lanes that share a
-// cell is summed by a butterfly and written once; the other lanes add their
-// own four values.  All 32 lanes must call it.
-__device__ __forceinline__ void deposit4(bool act, int iz, int ir, float v0, float v1, float v2, float v3,
-                                         const Tile& t) {
-    const unsigned full = 0xffffffffu;
-    int lane = threadIdx.x & 31;
-    int key = act ? iz * t.NR + ir : -1;
-    unsigned peers = __match_any_sync(full, key);
-    int leader = __ffs(peers) - 1;
-    unsigned gsize = __popc(peers);
-    unsigned code = act ? ((gsize << 5) | (unsigned)(31 - leader)) : 0u;
-    unsigned best = __reduce_max_sync(full, code);
-    bool agg = false;
-    if ((best >> 5) >= 2u) {
-        int bl = 31 - (int)(best & 31u);
-        agg = act && (leader == bl);
-        float s0 = agg ? v0 : 0.f, s1 = agg ? v1 : 0.f, s2 = agg ? v2 : 0.f, s3 = agg ? v3 : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(full, s0, o);
-            s1 += __shfl_xor_sync(full, s1, o);
-            s2 += __shfl_xor_sync(full, s2, o);
-            s3 += __shfl_xor_sync(full, s3, o);
-        }
-        if (lane == bl) add4(t, iz, ir, s0, s1, s2, s3);
+// current deposit: the run of sorted old cells only moves forward, so a new
+// cell flushes the previous one
+__device__ __forceinline__ void dep_run(DepAcc& a, const Tile& t, int iz, int ir, float v0, float v1, float v2,
+                                        float v3) {
+    if (iz != a.iz || ir != a.ir) {
+        if (a.iz >= 0) tile_add4(t, a.iz, a.ir, a.v0, a.v1, a.v2, a.v3);
+        a.iz = iz;
+        a.ir = ir;
+        a.v0 = v0;
+        a.v1 = v1;
+        a.v2 = v2;
+        a.v3 = v3;
+    } else {
+        a.v0 += v0;
+        a.v1 += v1;
+        a.v2 += v2;
+        a.v3 += v3;
     }
-    if (act && !agg) add4(t, iz, ir, v0, v1, v2, v3);
+}
+
+// charge deposit at the new positions: particles that left the accumulated
+// cell add their own values directly and leave the accumulator in place
+__device__ __forceinline__ void dep_home(DepAcc& a, const Tile& t, int iz, int ir, float v0, float v1, float v2,
+                                         float v3) {
+    if (a.iz < 0) {
+        a.iz = iz;
+        a.ir = ir;
+        a.v0 = v0;
+        a.v1 = v1;
+        a.v2 = v2;
+        a.v3 = v3;
+    } else if (iz == a.iz && ir == a.ir) {
+        a.v0 += v0;
+        a.v1 += v1;
+        a.v2 += v2;
+        a.v3 += v3;
+    } else {
+        tile_add4(t, iz, ir, v0, v1, v2, v3);
+    }
+}
+
+// End-of-chunk flush: segmented inclusive scan over the warp's lanes (lanes
+// hold consecutive particle runs, so equal cells sit in adjacent lanes); the
+// last lane of every segment adds the segment's sums.  All lanes call it.
+__device__ __forceinline__ void dep_flush_warp(DepAcc& a, const Tile& t) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int key = (a.iz >= 0) ? a.iz * t.NR + a.ir : -1;
+    int kl = __shfl_up_sync(full, key, 1);
+    unsigned f = (lane == 0 || kl != key) ? 1u : 0u;    // segment head
+    const unsigned head = f;
+    float s0 = a.v0, s1 = a.v1, s2 = a.v2, s3 = a.v3;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float u0 = __shfl_up_sync(full, s0, o);
+        float u1 = __shfl_up_sync(full, s1, o);
+        float u2 = __shfl_up_sync(full, s2, o);
+        float u3 = __shfl_up_sync(full, s3, o);
+        unsigned fu = __shfl_up_sync(full, f, o);
+        if (lane >= o) {
+            if (!f) {
+                s0 += u0;
+                s1 += u1;
+                s2 += u2;
+                s3 += u3;
+            }
+            f |= fu;
+        }
+    }
+    unsigned next_head = __shfl_down_sync(full, head, 1);
+    bool tail = (lane == 31) || next_head;
+    if (tail && key >= 0) tile_add4(t, a.iz, a.ir, s0, s1, s2, s3);
+    a.iz = -1;
 }
 
 // ---------------------------------------------------------------- push kernel
@@ -150,41 +264,194 @@ struct PushArgs {
     float* jm;
     double* win;
     int nr, NR, i_win;
+    uint32_t div_magic, div_shift;  // cell / nr = umulhi(cell, magic) >> shift
     uint32_t step, key0, key1;
     Event* ev;
     DevState* st;
 };
 
-__global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
-    __shared__ float t_rho[kTileRows * kMaxNR];
-    __shared__ float t_jm[kTileRows * kMaxNR];
+// shared-memory layout of one block (dynamic)
+struct PushSmem {
+    static constexpr int kArrays = 7;        // cell, dr, dz, vr, vt, vz, uid
+    static size_t bytes(int NR) {
+        return sizeof(float) * kChunk * kArrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
+               256;
+    }
+};
+
+__device__ __forceinline__ void electron_collision(const PushArgs& a, const SpeciesConst& S, uint32_t uid,
+                                                   float& vx, float& vy, float& vz, uint32_t cell, float drn,
+                                                   float dzn, unsigned* cnt) {
+    U4 u = draw4(uid, a.step, 0u, 0u, a.key0, a.key1);
+    float x = vx, y = vy, z = vz;
+    float v2 = x * x + y * y + z * z;
+    float g = sqrtf(v2);
+    float en = v2 * S.ce;
+    float s_el, s_ex, s_iz;
+    sigma_e(en, s_el, s_ex, s_iz);
+    float nu_el = S.ng * s_el * g;
+    float nu_ex = S.ng * s_ex * g;
+    float nu_iz = S.ng * s_iz * g;
+    float r = u.b * S.numax;
+    float c1 = nu_el, c2 = c1 + nu_ex, c3 = c2 + nu_iz;
+    if (c3 > S.numax) ++cnt[5];
+    int proc = (r < c1) ? 0 : (r < c2) ? 1 : (r < c3) ? 2 : 3;
+    if (proc == 3) return;
+    const float one = 1.0f;
+    float dx, dy, dzz;
+    iso_dir(u.c, u.d, dx, dy, dzz);
+    float gn;
+    if (proc == 0) {
+        float cosx = (g > 0.0f) ? (x * dx + y * dy + z * dzz) / g : 0.0f;
+        gn = g * sqrtf(one - S.loss * (one - cosx));
+        ++cnt[0];
+    } else if (proc == 1) {
+        gn = sqrtf(fmaxf(en - kEExc, 0.0f) * S.inv_ce);
+        ++cnt[1];
+    } else {
+        float eh = fmaxf(en - kEIon, 0.0f) * 0.5f;
+        gn = sqrtf(eh * S.inv_ce);
+        ++cnt[2];
+        U4 a1 = draw4(uid, a.step, 1u, 0u, a.key0, a.key1);
+        U4 b1 = draw4(uid, a.step, 2u, 0u, a.key0, a.key1);
+        float ex_, ey_, ez_, g0, g1, g2;
+        iso_dir(a1.a, a1.b, ex_, ey_, ez_);
+        gauss3(a1.c, a1.d, b1.a, b1.b, g0, g1, g2);
+        int slot = atomicAdd(&a.st->n_events, 1);
+        if (slot < kEventCap) {
+            Event e;
+            e.parent = uid;
+            e.cell = cell;
+            e.dr = drn;
+            e.dz = dzn;
+            e.ve[0] = gn * ex_;
+            e.ve[1] = gn * ey_;
+            e.ve[2] = gn * ez_;
+            e.vi[0] = a.sp[1].vth_gas * g0;
+            e.vi[1] = a.sp[1].vth_gas * g1;
+            e.vi[2] = a.sp[1].vth_gas * g2;
+            a.ev[slot] = e;
+        } else {
+            atomicOr(&a.st->status, (unsigned)PP_ST_EVENTS);
+        }
+    }
+    vx = gn * dx;
+    vy = gn * dy;
+    vz = gn * dzz;
+}
+
+__device__ __forceinline__ void ion_collision(const PushArgs& a, const SpeciesConst& S, uint32_t uid, float& vx,
+                                              float& vy, float& vz, unsigned* cnt) {
+    U4 u = draw4(uid, a.step, 0u, 1u, a.key0, a.key1);
+    U4 a1 = draw4(uid, a.step, 1u, 1u, a.key0, a.key1);
+    float g0, g1, g2;
+    gauss3(a1.a, a1.b, a1.c, a1.d, g0, g1, g2);
+    float vnxn = S.vth_gas * g0, vnyn = S.vth_gas * g1, vnzn = S.vth_gas * g2;
+    float x = vx, y = vy, z = vz;
+    float gx = x - vnxn, gy = y - vnyn, gz = z - vnzn;
+    float g2s = gx * gx + gy * gy + gz * gz;
+    float g = sqrtf(g2s);
+    float en = g2s * S.ce;
+    float s_cx, s_iso;
+    sigma_i(en, s_cx, s_iso);
+    float nu_cx = S.ng * s_cx * g;
+    float nu_iso = S.ng * s_iso * g;
+    float r = u.b * S.numax;
+    float c1 = nu_cx, c2 = c1 + nu_iso;
+    if (c2 > S.numax) ++cnt[5];
+    if (r < c1) {
+        vx = vnxn;
+        vy = vnyn;
+        vz = vnzn;
+        ++cnt[3];
+    } else if (r < c2) {
+        float dx, dy, dzz;
+        iso_dir(u.c, u.d, dx, dy, dzz);
+        float hg = g * 0.5f;
+        vx = (x + vnxn) * 0.5f + hg * dx;
+        vy = (y + vnyn) * 0.5f + hg * dy;
+        vz = (z + vnzn) * 0.5f + hg * dzz;
+        ++cnt[4];
+    }
+}
+
+// One block owns a chunk of kChunk consecutive particles of one species at a
+// time: TMA bulk copies bring the seven SoA slices into shared memory, each
+// thread advances kPPT consecutive particles (gather, Boris, current and
+// charge deposits accumulated in registers, move, boundaries, null test), the
+// few collision candidates are then processed densely, and bulk copies write
+// the six updated slices back.
+__global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t* s_cell = reinterpret_cast<uint32_t*>(smem);
+    float* s_dr = reinterpret_cast<float*>(s_cell + kChunk);
+    float* s_dz = s_dr + kChunk;
+    float* s_vr = s_dz + kChunk;
+    float* s_vt = s_vr + kChunk;
+    float* s_vz = s_vt + kChunk;
+    uint32_t* s_uid = reinterpret_cast<uint32_t*>(s_vz + kChunk);
+    float* t_rho = reinterpret_cast<float*>(s_uid + kChunk);
+    float* t_jm = t_rho + kTileRows * a.NR;
+    uint16_t* s_cand = reinterpret_cast<uint16_t*>(t_jm + kTileRows * a.NR);
+    __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_min[kPushThreads / 32], s_max[kPushThreads / 32];
+    __shared__ int s_ncand;
+    __shared__ int s_ok;
     __shared__ float s_f[kPushThreads / 32][2];
-    __shared__ unsigned s_c[kPushThreads / 32][9];
+    __shared__ unsigned s_c[kPushThreads / 32][10];
 
     const int n0 = a.nslot[0], n1 = a.nslot[1];
     const int ce = (n0 + kChunk - 1) / kChunk, ci = (n1 + kChunk - 1) / kChunk;
     const int nr = a.nr, NR = a.NR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = threadIdx.x;
+
+    if (t == 0) {
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     float acc_ind = 0.f, acc_es = 0.f;
-    unsigned c_push = 0, c_abs = 0, c_abs1 = 0, c_el = 0, c_ex = 0, c_iz = 0, c_cx = 0, c_iso = 0, c_viol = 0;
+    // counters: 0 el/cx, 1 ex/iso, 2 iz, 3 cx, 4 iso, 5 nu violations, 6 pushed, 7 absorbed e, 8 absorbed i
+    unsigned cnt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t parity = 0;
 
     for (int chunk = blockIdx.x; chunk < ce + ci; chunk += gridDim.x) {
         const int sp = chunk < ce ? 0 : 1;
         const int base = (chunk - (sp ? ce : 0)) * kChunk;
         const int n = sp ? n1 : n0;
+        const int nact = min(kChunk, n - base);
         const ParticleBuf P = a.p[sp];
         const SpeciesConst S = a.sp[sp];
+        const uint32_t bytes = (uint32_t)((nact * 4 + 15) & ~15);
 
-        uint32_t cells[kPPT];
+        // ---- stage the chunk (previous bulk stores must have read their smem)
+        if (t == 0) {
+            bulk_wait_read();
+            mbar_expect_tx(&s_bar, 7u * bytes);
+            bulk_g2s(s_cell, P.cell + base, bytes, &s_bar);
+            bulk_g2s(s_dr, P.dr + base, bytes, &s_bar);
+            bulk_g2s(s_dz, P.dz + base, bytes, &s_bar);
+            bulk_g2s(s_vr, P.vr + base, bytes, &s_bar);
+            bulk_g2s(s_vt, P.vt + base, bytes, &s_bar);
+            bulk_g2s(s_vz, P.vz + base, bytes, &s_bar);
+            bulk_g2s(s_uid, P.uid + base, bytes, &s_bar);
+            s_ncand = 0;
+        }
+        bool ok = mbar_wait(&s_bar, parity);
+        if (!ok) {
+            atomicOr(&a.st->status, (unsigned)PP_ST_TIMEOUT);
+            mbar_wait(&s_bar, parity);        // give the copies in flight a second bounded wait
+        }
+        parity ^= 1u;
+        if (t == 0) s_ok = ok ? 1 : 0;
+        // ---- tile rows from the chunk's cell range
         int lmin = INT_MAX, lmax = -1;
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            int idx = base + k * kPushThreads + threadIdx.x;
-            cells[k] = (idx < n) ? P.cell[idx] : kDead;
-            if (cells[k] != kDead) {
-                int iz = (int)(cells[k] / (uint32_t)nr);
+        for (int q = t; q < nact; q += kPushThreads) {
+            uint32_t c = s_cell[q];
+            if (c != kDead) {
+                int iz = (int)(__umulhi(c, a.div_magic) >> a.div_shift);
                 lmin = min(lmin, iz);
                 lmax = max(lmax, iz);
             }
@@ -196,54 +463,60 @@ __global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
             s_max[warp] = lmax;
         }
         __syncthreads();
+        if (!s_ok) break;
         int bmin = INT_MAX, bmax = -1;
         for (int w = 0; w < kPushThreads / 32; ++w) {
             bmin = min(bmin, s_min[w]);
             bmax = max(bmax, s_max[w]);
         }
-        int tlo = max(bmin - 1, 0);
-        int thi = min(bmax + 2, a.i_win);
-        int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
-        for (int q = threadIdx.x; q < trows * NR; q += kPushThreads) {
+        const int tlo = max(bmin - 1, 0);
+        const int thi = min(bmax + 2, a.i_win);
+        const int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
+        for (int q = t; q < trows * NR; q += kPushThreads) {
             t_rho[q] = 0.f;
             t_jm[q] = 0.f;
         }
         __syncthreads();
-        Tile tj{t_jm, tlo, trows, a.jm, NR};
-        Tile tq{t_rho, tlo, trows, a.rho, NR};
+        const Tile tj{t_jm, tlo, trows, a.jm, NR};
+        const Tile tq{t_rho, tlo, trows, a.rho, NR};
 
+        // ---- phase A: thread-contiguous push
+        DepAcc dj{-1, 0, 0.f, 0.f, 0.f, 0.f};
+        DepAcc dq{-1, 0, 0.f, 0.f, 0.f, 0.f};
+        uint32_t fcell = kDead;
+        float4 f0, f1, f2, f3, f4;
+        // thread t owns particles t*kPPT .. t*kPPT + 7 and visits them starting
+        // at offset t/4: the 32 lanes of a warp then hit 32 different banks
+        const int p0 = t * kPPT, rot = (t >> 2) & (kPPT - 1);
 #pragma unroll 1
         for (int k = 0; k < kPPT; ++k) {
-            const int idx = base + k * kPushThreads + threadIdx.x;
-            const bool live = cells[k] != kDead;
-            int iz = 0, ir = 0;
-            float dr = 0.f, dz = 0.f, vr = 0.f, vt = 0.f, vz = 0.f;
-            uint32_t uid = 0;
-            if (live) {
-                iz = (int)(cells[k] / (uint32_t)nr);
-                ir = (int)(cells[k] - (uint32_t)iz * (uint32_t)nr);
-                dr = P.dr[idx];
-                dz = P.dz[idx];
-                vr = P.vr[idx];
-                vt = P.vt[idx];
-                vz = P.vz[idx];
-                uid = P.uid[idx];
+            const int p = p0 + ((k + rot) & (kPPT - 1));
+            if (p >= nact) continue;
+            const uint32_t cell = s_cell[p];
+            if (cell == kDead) continue;
+            const int iz = (int)(__umulhi(cell, a.div_magic) >> a.div_shift);
+            const int ir = (int)cell - iz * nr;
+            const float dr = s_dr[p], dz = s_dz[p];
+            const float vr = s_vr[p], vt = s_vt[p], vz = s_vz[p];
+            if (cell != fcell) {
+                const float4* f = reinterpret_cast<const float4*>(a.F) + (size_t)cell * 5;
+                f0 = __ldg(f);
+                f1 = __ldg(f + 1);
+                f2 = __ldg(f + 2);
+                f3 = __ldg(f + 3);
+                f4 = __ldg(f + 4);
+                fcell = cell;
             }
-            // ---- gather (bilinear weights at the old position)
+            // gather (bilinear weights at the old position)
             const float one = 1.0f;
             float wa = one - dr, wb = one - dz;
             float w00 = wa * wb, w01 = dr * wb, w10 = wa * dz, w11 = dr * dz;
-            float Er = 0.f, Ez = 0.f, Et = 0.f, Br = 0.f, Bz = 0.f;
-            if (live) {
-                const float4* f = reinterpret_cast<const float4*>(a.F) + (size_t)cells[k] * 5;
-                float4 q0 = __ldg(f), q1 = __ldg(f + 1), q2 = __ldg(f + 2), q3 = __ldg(f + 3), q4 = __ldg(f + 4);
-                Er = w00 * q0.x + w01 * q0.y + w10 * q0.z + w11 * q0.w;
-                Ez = w00 * q1.x + w01 * q1.y + w10 * q1.z + w11 * q1.w;
-                Et = w00 * q2.x + w01 * q2.y + w10 * q2.z + w11 * q2.w;
-                Br = w00 * q3.x + w01 * q3.y + w10 * q3.z + w11 * q3.w;
-                Bz = w00 * q4.x + w01 * q4.y + w10 * q4.z + w11 * q4.w;
-            }
-            // ---- Boris in the local frame (x = r, y = theta, z); B_theta = 0
+            float Er = w00 * f0.x + w01 * f0.y + w10 * f0.z + w11 * f0.w;
+            float Ez = w00 * f1.x + w01 * f1.y + w10 * f1.z + w11 * f1.w;
+            float Et = w00 * f2.x + w01 * f2.y + w10 * f2.z + w11 * f2.w;
+            float Br = w00 * f3.x + w01 * f3.y + w10 * f3.z + w11 * f3.w;
+            float Bz = w00 * f4.x + w01 * f4.y + w10 * f4.z + w11 * f4.w;
+            // Boris in the local frame (x = r, y = theta, z); B_theta = 0
             float hx = S.qmh * Er, hy = S.qmh * Et, hz = S.qmh * Ez;
             float vmx = vr + hx, vmy = vt + hy, vmz = vz + hz;
             float tx = S.qmh * Br, tz = S.qmh * Bz;
@@ -257,18 +530,16 @@ __global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
             float vpy = vmy + (v1z * sx - v1x * sz);
             float vpz = vmz - v1y * sx;
             float vnx = vpx + hx, vny = vpy + hy, vnz = vpz + hz;
-            // ---- current moment at the old position, time-centred velocity
+            // current moment at the old position, time-centred velocity
             float vbt = (vt + vny) * 0.5f;
             float vbr = (vr + vnx) * 0.5f;
             float vbz = (vz + vnz) * 0.5f;
             float jmv = S.qw * vbt;
-            if (live) {
-                acc_ind += jmv * Et;
-                acc_es += S.qw * (vbr * Er + vbz * Ez);
-                ++c_push;
-            }
-            deposit4(live, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11, tj);
-            // ---- move (cell units); r' = |(r + a, b)| written as r + delta
+            acc_ind += jmv * Et;
+            acc_es += S.qw * (vbr * Er + vbz * Ez);
+            ++cnt[6];
+            dep_run(dj, tj, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
+            // move (cell units): r' = |(r + a, b)| written as r + delta
             float am = vnx * S.dtr, bm = vny * S.dtr, cm = vnz * S.dtz;
             float rho = (float)ir + dr;
             float x1 = rho + am;
@@ -277,7 +548,8 @@ __global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
             float delta = (den > 0.0f) ? (am * (rho + x1) + bm * bm) / den : 0.0f;
             float vr2 = vnx, vt2 = vny;
             if (rp > 0.0f) {
-                float ca = x1 / rp, sa = bm / rp;
+                float inv = one / rp;
+                float ca = x1 * inv, sa = bm * inv;
                 vr2 = ca * vnx + sa * vny;
                 vt2 = ca * vny - sa * vnx;
             }
@@ -303,136 +575,70 @@ __global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
                 ir2 = 0;
                 drn = 0.0f;
             }
-            // ---- boundaries: electrode z < 0, wall r >= R, window z >= z_win
-            bool alive = live;
-            if (live) {
-                bool he = iz2 < 0;
-                bool hw = !he && ir2 >= nr;
-                bool hd = !he && !hw && iz2 >= a.i_win;
-                if (hd) {
-                    float rpos = (float)ir2 + drn;
-                    int j0 = (int)floorf(rpos);
-                    float fr = rpos - (float)j0;
-                    atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
-                    atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
-                }
-                if (he || hw || hd) {
-                    alive = false;
-                    ++c_abs;
-                    if (sp) ++c_abs1;
-                }
+            // boundaries: electrode z < 0, wall r >= R, window z >= z_win
+            bool he = iz2 < 0;
+            bool hw = !he && ir2 >= nr;
+            bool hd = !he && !hw && iz2 >= a.i_win;
+            if (hd) {
+                float rpos = (float)ir2 + drn;
+                int j0 = (int)floorf(rpos);
+                float fr = rpos - (float)j0;
+                atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
+                atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
             }
-            // ---- null-collision MCC at the new position
-            float ovr = vr2, ovt = vt2, ovz = vnz;
+            const bool alive = !(he || hw || hd);
+            uint32_t ncell = kDead;
             if (alive) {
-                U4 u = draw4(uid, a.step, 0u, (uint32_t)sp, a.key0, a.key1);
-                if (u.a < S.pnull) {
-                    float x = vr2, y = vt2, z = vnz;
-                    if (sp == 0) {
-                        float v2 = x * x + y * y + z * z;
-                        float g = sqrtf(v2);
-                        float en = v2 * S.ce;
-                        float s_el, s_ex, s_iz;
-                        sigma_e(en, s_el, s_ex, s_iz);
-                        float nu_el = S.ng * s_el * g;
-                        float nu_ex = S.ng * s_ex * g;
-                        float nu_iz = S.ng * s_iz * g;
-                        float r = u.b * S.numax;
-                        float c1 = nu_el, c2 = c1 + nu_ex, c3 = c2 + nu_iz;
-                        if (c3 > S.numax) ++c_viol;
-                        int proc = (r < c1) ? 0 : (r < c2) ? 1 : (r < c3) ? 2 : 3;
-                        if (proc < 3) {
-                            float dx, dy, dzz;
-                            iso_dir(u.c, u.d, dx, dy, dzz);
-                            float gn;
-                            if (proc == 0) {
-                                float cosx = (g > 0.0f) ? (x * dx + y * dy + z * dzz) / g : 0.0f;
-                                gn = g * sqrtf(one - S.loss * (one - cosx));
-                                ++c_el;
-                            } else if (proc == 1) {
-                                gn = sqrtf(fmaxf(en - kEExc, 0.0f) * S.inv_ce);
-                                ++c_ex;
-                            } else {
-                                float eh = fmaxf(en - kEIon, 0.0f) * 0.5f;
-                                gn = sqrtf(eh * S.inv_ce);
-                                ++c_iz;
-                                U4 a1 = draw4(uid, a.step, 1u, 0u, a.key0, a.key1);
-                                U4 b1 = draw4(uid, a.step, 2u, 0u, a.key0, a.key1);
-                                float ex_, ey_, ez_, g0, g1, g2;
-                                iso_dir(a1.a, a1.b, ex_, ey_, ez_);
-                                gauss3(a1.c, a1.d, b1.a, b1.b, g0, g1, g2);
-                                int slot = atomicAdd(&a.st->n_events, 1);
-                                if (slot < kEventCap) {
-                                    Event e;
-                                    e.parent = uid;
-                                    e.cell = (uint32_t)(iz2 * nr + ir2);
-                                    e.dr = drn;
-                                    e.dz = dzn;
-                                    e.ve[0] = gn * ex_;
-                                    e.ve[1] = gn * ey_;
-                                    e.ve[2] = gn * ez_;
-                                    e.vi[0] = a.sp[1].vth_gas * g0;
-                                    e.vi[1] = a.sp[1].vth_gas * g1;
-                                    e.vi[2] = a.sp[1].vth_gas * g2;
-                                    a.ev[slot] = e;
-                                } else {
-                                    atomicOr(&a.st->status, (unsigned)PP_ST_EVENTS);
-                                }
-                            }
-                            ovr = gn * dx;
-                            ovt = gn * dy;
-                            ovz = gn * dzz;
-                        }
-                    } else {
-                        U4 a1 = draw4(uid, a.step, 1u, 1u, a.key0, a.key1);
-                        float g0, g1, g2;
-                        gauss3(a1.a, a1.b, a1.c, a1.d, g0, g1, g2);
-                        float vnxn = S.vth_gas * g0, vnyn = S.vth_gas * g1, vnzn = S.vth_gas * g2;
-                        float gx = x - vnxn, gy = y - vnyn, gz = z - vnzn;
-                        float g2s = gx * gx + gy * gy + gz * gz;
-                        float g = sqrtf(g2s);
-                        float en = g2s * S.ce;
-                        float s_cx, s_iso;
-                        sigma_i(en, s_cx, s_iso);
-                        float nu_cx = S.ng * s_cx * g;
-                        float nu_iso = S.ng * s_iso * g;
-                        float r = u.b * S.numax;
-                        float c1 = nu_cx, c2 = c1 + nu_iso;
-                        if (c2 > S.numax) ++c_viol;
-                        if (r < c1) {
-                            ovr = vnxn;
-                            ovt = vnyn;
-                            ovz = vnzn;
-                            ++c_cx;
-                        } else if (r < c2) {
-                            float dx, dy, dzz;
-                            iso_dir(u.c, u.d, dx, dy, dzz);
-                            float hg = g * 0.5f;
-                            ovr = (x + vnxn) * 0.5f + hg * dx;
-                            ovt = (y + vnyn) * 0.5f + hg * dy;
-                            ovz = (z + vnzn) * 0.5f + hg * dzz;
-                            ++c_iso;
-                        }
-                    }
+                ncell = (uint32_t)(iz2 * nr + ir2);
+                float wa2 = one - drn, wb2 = one - dzn;
+                dep_home(dq, tq, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
+                         S.qw * (drn * dzn));
+                // null-collision test; candidates are processed densely below
+                uint32_t r = philox2x32_10(s_uid[p], (a.step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
+                                           a.key0 ^ a.key1);
+                if (u01(r) < S.pnull) {
+                    int slot = atomicAdd(&s_ncand, 1);
+                    s_cand[slot] = (uint16_t)p;
                 }
+            } else {
+                ++cnt[7 + sp];
             }
-            // ---- charge at the new position
-            float wa2 = one - drn, wb2 = one - dzn;
-            float q00 = S.qw * (wa2 * wb2), q01 = S.qw * (drn * wb2), q10 = S.qw * (wa2 * dzn),
-                  q11 = S.qw * (drn * dzn);
-            deposit4(alive, iz2, ir2, q00, q01, q10, q11, tq);
-            // ---- store
-            if (live) {
-                P.cell[idx] = alive ? (uint32_t)(iz2 * nr + ir2) : kDead;
-                P.dr[idx] = alive ? drn : 0.0f;
-                P.dz[idx] = alive ? dzn : 0.0f;
-                P.vr[idx] = ovr;
-                P.vt[idx] = ovt;
-                P.vz[idx] = ovz;
-            }
+            s_cell[p] = ncell;
+            s_dr[p] = alive ? drn : 0.0f;
+            s_dz[p] = alive ? dzn : 0.0f;
+            s_vr[p] = vr2;
+            s_vt[p] = vt2;
+            s_vz[p] = vnz;
+        }
+        dep_flush_warp(dj, tj);
+        dep_flush_warp(dq, tq);
+        __syncthreads();
+        // ---- phase B: collisions of the candidates
+        const int nc = s_ncand;
+        for (int c = t; c < nc; c += kPushThreads) {
+            const int p = s_cand[c];
+            float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
+            if (sp == 0)
+                electron_collision(a, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], cnt);
+            else
+                ion_collision(a, S, s_uid[p], vx, vy, vzz, cnt);
+            s_vr[p] = vx;
+            s_vt[p] = vy;
+            s_vz[p] = vzz;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < trows * NR; q += kPushThreads) {
+        // ---- write back (bulk) and flush the node tiles
+        if (t == 0) {
+            fence_async_smem();
+            bulk_s2g(P.cell + base, s_cell, bytes);
+            bulk_s2g(P.dr + base, s_dr, bytes);
+            bulk_s2g(P.dz + base, s_dz, bytes);
+            bulk_s2g(P.vr + base, s_vr, bytes);
+            bulk_s2g(P.vt + base, s_vt, bytes);
+            bulk_s2g(P.vz + base, s_vz, bytes);
+            bulk_commit();
+        }
+        for (int q = t; q < trows * NR; q += kPushThreads) {
             float vq = t_rho[q], vj = t_jm[q];
             int gidx = (tlo + q / NR) * NR + (q % NR);
             if (vq != 0.f) atomicAdd(&a.rho[gidx], vq);
@@ -440,39 +646,44 @@ __global__ void __launch_bounds__(kPushThreads) push_kernel(PushArgs a) {
         }
         __syncthreads();
     }
+    if (t == 0) bulk_wait_all();
     // ---- block reduction of the tallies
     for (int o = 16; o > 0; o >>= 1) {
         acc_ind += __shfl_xor_sync(0xffffffffu, acc_ind, o);
         acc_es += __shfl_xor_sync(0xffffffffu, acc_es, o);
     }
-    unsigned cs[9] = {c_push, c_abs, c_el, c_ex, c_iz, c_cx, c_iso, c_viol, c_abs1};
-    for (int q = 0; q < 9; ++q) cs[q] = __reduce_add_sync(0xffffffffu, cs[q]);
+    for (int q = 0; q < 10; ++q) cnt[q] = __reduce_add_sync(0xffffffffu, cnt[q]);
     if (lane == 0) {
         s_f[warp][0] = acc_ind;
         s_f[warp][1] = acc_es;
-        for (int q = 0; q < 9; ++q) s_c[warp][q] = cs[q];
+        for (int q = 0; q < 10; ++q) s_c[warp][q] = cnt[q];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         double si = 0, se = 0;
-        unsigned long long tot[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned long long tot[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < kPushThreads / 32; ++w) {
             si += s_f[w][0];
             se += s_f[w][1];
-            for (int q = 0; q < 9; ++q) tot[q] += s_c[w][q];
+            for (int q = 0; q < 10; ++q) tot[q] += s_c[w][q];
         }
         DevState* st = a.st;
         atomicAdd(&st->p_ind_step, si);
         atomicAdd(&st->p_es_step, se);
-        const int map[8] = {C_PSTEPS, C_ABSORBED, C_E_EL, C_E_EX, C_E_IZ, C_I_CX, C_I_ISO, C_NUVIOL};
-        for (int q = 0; q < 8; ++q)
+        // electron processes in 0..2, ion processes in 3..4
+        const int map[7] = {C_E_EL, C_E_EX, C_E_IZ, C_I_CX, C_I_ISO, C_NUVIOL, C_PSTEPS};
+        for (int q = 0; q < 7; ++q)
             if (tot[q]) {
                 atomicAdd(&st->cnt[map[q]], tot[q]);
                 atomicAdd(&st->per[map[q]], tot[q]);
             }
-        unsigned long long a1 = tot[8], a0 = tot[1] - tot[8];
-        if (a0) atomicAdd(&st->live[0], (unsigned long long)(-(long long)a0));
-        if (a1) atomicAdd(&st->live[1], (unsigned long long)(-(long long)a1));
+        unsigned long long ab = tot[7] + tot[8];
+        if (ab) {
+            atomicAdd(&st->cnt[C_ABSORBED], ab);
+            atomicAdd(&st->per[C_ABSORBED], ab);
+        }
+        if (tot[7]) atomicAdd(&st->live[0], (unsigned long long)(-(long long)tot[7]));
+        if (tot[8]) atomicAdd(&st->live[1], (unsigned long long)(-(long long)tot[8]));
     }
 }
 
@@ -490,15 +701,25 @@ void launch_push(Cell* c, uint32_t step, cudaStream_t st) {
     a.nr = c->nr;
     a.NR = c->NR;
     a.i_win = c->i_win;
+    a.div_magic = c->div_magic;
+    a.div_shift = c->div_shift;
     a.step = step;
     a.key0 = (uint32_t)(c->cfg.seed & 0xffffffffu);
     a.key1 = (uint32_t)(c->cfg.seed >> 32);
     a.ev = c->d_events;
     a.st = c->d_st;
-    int dev = 0, nsm = 148;
+    size_t shm = PushSmem::bytes(c->NR);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(push_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    int dev = 0, nsm = 148, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    push_kernel<<<nsm * 4, kPushThreads, 0, st>>>(a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel, kPushThreads, shm);
+    if (per < 1) per = 1;
+    push_kernel<<<nsm * per, kPushThreads, shm, st>>>(a);
     count_launch();
 }
 

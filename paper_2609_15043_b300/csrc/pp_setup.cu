@@ -272,6 +272,7 @@ int setup_cell(Cell* c) {
         }
     c->ntn = (int)tn_node.size();
     if (c->ntn > kMaxCapNodes) return fail("too many turn nodes for the capacitance correction");
+    if (NR - 1 > 512) return fail("nr exceeds the radial unknowns supported by the Poisson solver");
     std::vector<signed char> mask(c->nnodes, -1);
     for (int t = 0; t < c->ntn; ++t) mask[tn_node[t]] = (signed char)tn_k[t];
 
@@ -327,12 +328,26 @@ int setup_cell(Cell* c) {
         arm[j] = (j == 0) ? 0.0 : (j * dr - dr / 2) * dz / dr;
     }
 
-    // ---- allocations
+    // ---- cell / nr by multiply-high and shift, verified for every plasma cell
+    {
+        uint32_t d = (uint32_t)f.nr, s = 0;
+        while ((2u << s) <= d) ++s;                       // s = floor(log2 d)
+        if ((d & (d - 1)) == 0) --s;                      // powers of two: m = 2^31
+        uint64_t m = (((uint64_t)1 << (32 + s)) + d - 1) / d;
+        if (m >> 32) return fail("no 32-bit division multiplier for nr");
+        uint32_t ncell = (uint32_t)(c->i_win * f.nr);
+        for (uint32_t q = 0; q < ncell; ++q)
+            if ((uint32_t)(((uint64_t)q * m) >> 32 >> s) != q / d) return fail("division multiplier check failed");
+        c->div_magic = (uint32_t)m;
+        c->div_shift = s;
+    }
+
+    // ---- allocations (particle storage padded to whole staging chunks)
     for (int sp = 0; sp < 2; ++sp) {
         c->cap[sp] = f.capacity[sp];
         for (int b = 0; b < 2; ++b) {
             ParticleBuf& p = c->pb[sp][b];
-            size_t n = (size_t)c->cap[sp];
+            size_t n = (size_t)((c->cap[sp] + kChunk - 1) / kChunk) * kChunk;
             p.cell = c->alloc<uint32_t>(n);
             p.dr = c->alloc<float>(n);
             p.dz = c->alloc<float>(n);
@@ -595,7 +610,7 @@ int setup_cell(Cell* c) {
             std::fill(e.begin(), e.end(), 0.0f);
             e[tn_int[t]] = 1.0f;
             cudaMemcpy(c->d_r32, e.data(), sizeof(float) * nint, cudaMemcpyHostToDevice);
-            sep_solve<float>(c->ps, c->d_r32, c->d_Z + (size_t)t * nint, 0, nullptr);
+            poisson_fast_solve(c, c->d_r32, c->d_Z + (size_t)t * nint, 0);
         }
         std::vector<float> Zh((size_t)K * nint);
         cudaMemcpy(Zh.data(), c->d_Z, sizeof(float) * K * nint, cudaMemcpyDeviceToHost);

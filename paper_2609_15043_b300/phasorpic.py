@@ -15,7 +15,7 @@ import numpy as np
 from . import workloads
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libphasorpic.so")
+LIB_PATH = os.environ.get("PHASORPIC_LIB") or os.path.join(_HERE, "libphasorpic.so")
 
 MAX_TURNS = 8
 NSPECIES = 2
@@ -23,7 +23,7 @@ NSPECIES = 2
 PP_OK = 0
 ERRORS = {-1: "PP_E_CONFIG", -2: "PP_E_NOCONV", -3: "PP_E_SAMPLES", -4: "PP_E_NAN", -5: "PP_E_TIMEOUT",
           -6: "PP_E_CUDA", -7: "PP_E_ARG", -8: "PP_E_CAPACITY"}
-ST_NOCONV, ST_EVENTS, ST_CAPACITY, ST_SAMPLES = 1, 2, 4, 8
+ST_NOCONV, ST_EVENTS, ST_CAPACITY, ST_SAMPLES, ST_TIMEOUT = 1, 2, 4, 8, 16
 
 GRID_PHI, GRID_EC, GRID_ESS, GRID_JC, GRID_JS, GRID_WINDOW, GRID_CHARGE, GRID_JMOM = range(8)
 GRID_U0 = 16
