@@ -254,6 +254,32 @@ int pp_poisson_solve(pp_cell* cell, const double* q, const double* turn_phi, dou
  */
 int pp_helmholtz_solve(pp_cell* cell, const double* rhs, double* e);
 
+/*
+ * pp_poisson_solve_noalloc -- the same Poisson solve as pp_poisson_solve for
+ * callers that must not allocate device memory: code that runs while a CUDA
+ * graph is being captured (cudaMalloc cannot be captured), or a host program
+ * whose memory manager owns the device and forbids allocations from
+ * libraries.  The paper has no counterpart; this is a library facility.
+ *
+ * Arguments are DEVICE pointers: d_q node charges (C, (nz+1)*(nr+1) doubles),
+ * d_turn_phi the N turn potentials (doubles), d_phi the output potential
+ * (node grid, fully overwritten), d_info (may be NULL) receives two ints:
+ * refinement sweeps used + 1, and 1 if the relative FP64 residual reached the
+ * cell's tolerance (0 otherwise).  Work is enqueued on `stream`; the call does
+ * not wait for it.  The cell's operator data is read, never changed.
+ *
+ * Scratch: a fixed 4 MiB device array inside the library (held by every GPU
+ * that loads the library until the process exits).  Grids needing more
+ * (interior points x 12 B + nodes x 4 B + ~4 KB) are rejected with PP_E_ARG.
+ * The first call on each device resolves the array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  No cudaMalloc or cudaFree is called.
+ */
+int pp_poisson_solve_noalloc(pp_cell* cell, const double* d_q, const double* d_turn_phi, double* d_phi,
+                             int* d_info, void* stream);
+
 /* pp_get_status -- device status bits (PP_ST_*) accumulated since init;
  * synchronises `stream`. */
 int pp_get_status(pp_cell* cell, uint32_t* status, void* stream);

@@ -5,6 +5,7 @@
 #include "pp_internal.h"
 
 #include <cmath>
+#include <string>
 
 namespace pp {
 
@@ -487,6 +488,139 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     }
     return 0;
 }
+
+// ---------------------------------------------------------------- allocation-free Poisson solve
+// Scratch of pp_poisson_solve_noalloc: a fixed device array that lives as long
+// as the library is loaded on each device that uses it, so the entry point
+// itself never allocates.  Layout per call (bytes, each part 256-aligned):
+// solver state | sigma (64 doubles) | zero charge (nnodes floats) |
+// residual, transform and sweep buffers (3 x interior floats).
+constexpr size_t kNoAllocBytes = (size_t)4 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__global__ void noalloc_report(const DevState* s, int* info) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        info[0] = s->piters + 1;
+        info[1] = (s->status & PP_ST_NOCONV) ? 0 : 1;
+    }
+}
+
+}  // namespace pp
+
+#include <mutex>
+
+namespace pp {
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+}  // namespace
+}  // namespace pp
+
+extern "C" int pp_poisson_solve_noalloc(pp_cell* h, const double* d_q, const double* d_turn_phi, double* d_phi,
+                                        int* d_info, void* stream) {
+    using namespace pp;
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !d_q || !d_turn_phi || !d_phi) {
+        set_error("bad argument to pp_poisson_solve_noalloc");
+        return PP_E_ARG;
+    }
+    const int rows = c->ps.rows, M = c->ps.M, nint = rows * M;
+    const size_t off_sig = align256(sizeof(DevState));
+    const size_t off_rho = off_sig + align256(sizeof(double) * kMaxCapNodes);
+    const size_t off_r32 = off_rho + align256(sizeof(float) * (size_t)c->nnodes);
+    const size_t off_t0 = off_r32 + align256(sizeof(float) * (size_t)nint);
+    const size_t off_t1 = off_t0 + align256(sizeof(float) * (size_t)nint);
+    const size_t need = off_t1 + align256(sizeof(float) * (size_t)nint);
+    if (need > kNoAllocBytes) {
+        set_error("pp_poisson_solve_noalloc: grid needs " + std::to_string(need) + " bytes of scratch, the fixed "
+                  "array holds " + std::to_string(kNoAllocBytes));
+        return PP_E_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        set_error("pp_poisson_solve_noalloc: no usable current device");
+        return PP_E_CUDA;
+    }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                set_error(std::string("pp_poisson_solve_noalloc: cudaGetSymbolAddress failed: ") +
+                          cudaGetErrorString(e));
+                return PP_E_CUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState* sst = reinterpret_cast<DevState*>(base);
+    double* sigma = reinterpret_cast<double*>(base + off_sig);
+    float* rho0 = reinterpret_cast<float*>(base + off_rho);
+    SepSolver<float> ps = c->ps;
+    float* r32 = reinterpret_cast<float*>(base + off_r32);
+    ps.t0 = reinterpret_cast<float*>(base + off_t0);
+    ps.t1 = reinterpret_cast<float*>(base + off_t1);
+    // what must start at zero: the solver state, the charge array the residual
+    // adds to q, and the potential (its boundary values are the grounded zeros)
+    cudaMemsetAsync(sst, 0, sizeof(DevState), st);
+    cudaMemsetAsync(rho0, 0, sizeof(float) * (size_t)c->nnodes, st);
+    cudaMemsetAsync(d_phi, 0, sizeof(double) * (size_t)c->nnodes, st);
+    const int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
+    PoisArgs a;
+    a.phi = d_phi;
+    a.rho = rho0;
+    a.win = d_q;
+    a.eps_row = c->d_eps_row;
+    a.az = c->d_az;
+    a.arp = c->d_arp;
+    a.arm = c->d_arm;
+    a.turn_mask = c->d_turn_mask;
+    a.r32 = r32;
+    a.NR = c->NR;
+    a.NZ = c->NZ;
+    a.M = M;
+    a.inv2pieps0 = 1.0 / (2.0 * kPi * kEps0);
+    a.done = &sst->pdone;
+    a.st = sst;
+    a.ext = d_turn_phi;
+    a.nt = c->nturns;
+    a.cs = 1.0;
+    a.sn = 0.0;
+    const int K = c->ntn;
+    for (int it = 0; it <= maxit; ++it) {
+        a.norm = &sst->pnorm[2 * it];
+        poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
+        poisson_check<<<1, 32, 0, st>>>(sst, it, c->cfg.poisson_tol, &sst->pdone, it == maxit ? 1 : 0);
+        count_launch(2);
+        if (it == maxit) break;
+        sep_solve<float>(ps, r32, ps.t0, st, &sst->pdone);
+        poisson_cap<<<1, kMaxCapNodes, 0, st>>>(sst, d_turn_phi, d_phi, ps.t0, c->d_tn_node, c->d_tn_int, c->d_tn_k,
+                                                c->d_Ginv, sigma, K, c->nturns, 1.0, 0.0, &sst->pdone);
+        poisson_update<<<(nint + 255) / 256, 256, 0, st>>>(d_phi, ps.t0, c->d_Z, sigma, K, rows, M, c->NR,
+                                                            c->d_turn_mask, sst, d_turn_phi, c->nturns, 1.0, 0.0,
+                                                            &sst->pdone);
+        count_launch(2);
+    }
+    if (d_info) {
+        noalloc_report<<<1, 32, 0, st>>>(sst, d_info);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("pp_poisson_solve_noalloc: ") + cudaGetErrorString(e));
+        return PP_E_CUDA;
+    }
+    return PP_OK;
+}
+
+namespace pp {
 
 // FP32 inner solve alone (used at initialisation for the capacitance columns)
 void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st) {

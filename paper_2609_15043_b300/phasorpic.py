@@ -33,7 +33,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_set_circuit_state", "pp_get_circuit_state", "pp_get_turn_phasors",
            "pp_get_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
            "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
-           "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index"]
+           "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
+           "pp_poisson_solve_noalloc"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -117,6 +118,7 @@ def _load():
         "pp_set_profiling": (I, [V, I]),
         "pp_get_phase_times": (I, [V, V, V]),
         "pp_launch_count": (C.c_int64, []),
+        "pp_poisson_solve_noalloc": (I, [V, V, V, V, V, V]),
         "pp_n_rf": (I, [V]),
         "pp_step_index": (C.c_int64, [V]),
     }
@@ -324,6 +326,17 @@ def _phase_times(self):
 
 
 Cell.set_profiling = _set_profiling
+
+
+def _poisson_solve_noalloc(self, d_q, d_turn_phi, d_phi, d_info=0, stream=0):
+    """Device-pointer Poisson solve that allocates no device memory (see the
+    header): pointers are integers (e.g. torch tensor data_ptr())."""
+    _check(lib.pp_poisson_solve_noalloc(self.h, C.c_void_p(d_q), C.c_void_p(d_turn_phi), C.c_void_p(d_phi),
+                                        C.c_void_p(d_info) if d_info else None, C.c_void_p(stream)),
+           "pp_poisson_solve_noalloc")
+
+
+Cell.poisson_solve_noalloc = _poisson_solve_noalloc
 Cell.phase_times = _phase_times
 
 
