@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s and time-to-stationary-state vs plain FP64 PIC, 1 B300"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 52      # read cell,dr,dz,vr,vt,vz,uid (28 B) + write 6 x 4 B
+BYTES_PER_PARTICLE_STEP_FP64 = 92  # read cell,uid + 5 x 8 B (48 B) + write cell + 5 x 8 B
 
 
 def parse():
@@ -46,6 +47,14 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=1, help="PIC steps of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="fused", choices=["fused", "fp64"],
+                    help="particle form: the fused FP32 kernel or the plain FP64 form")
+    ap.add_argument("--time-to-stationary", action="store_true",
+                    help="run each form from the same initial state until the stationarity test passes")
+    ap.add_argument("--max-periods", type=int, default=600, help="cap of the time-to-stationary runs")
+    ap.add_argument("--trace-out", default=None, help="write the per-period records of those runs (JSON)")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only prime the cell and run this many PIC steps, untimed (a short target for ncu)")
     return ap.parse_args()
 
 
@@ -228,13 +237,22 @@ def run_ours(args, cfg, ws, rank, local):
         # timing reductions run on CPU tensors: gloo for them, no data-path collective
         dist.init_process_group("gloo")
     from paper_2609_15043_b300 import phasorpic as pp, workloads
-    cfg = cfg.replace(seed=cfg.seed + rank)
+    cfg = cfg.replace(seed=cfg.seed + rank, plain_fp64=1 if args.form == "fp64" else 0)
     cell = pp.Cell(cfg)
     for sp in (0, 1):
         cell.set_particles(sp, workloads.population(cfg, sp))
     stream = torch.cuda.default_stream()
     sh = stream.cuda_stream
     cell.prime(sh)
+    if args.profile_steps:
+        cell.advance_steps(args.profile_steps, sh)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile_steps, "counters": cell.counters()}), flush=True)
+        cell.close()
+        return
+    # the timed region records events around the particle kernel; the period
+    # graph is captured with them during warm-up
+    cell.set_profiling(True, level=1)
     for _ in range(args.warmup):
         cell.advance_period(1, sh)
     torch.cuda.synchronize()
@@ -245,9 +263,9 @@ def run_ours(args, cfg, ws, rank, local):
         torch.cuda.synchronize()
 
     # ---- device-timed region: K periods, inputs resident in HBM
+    cell.phase_times()                           # drop the warm-up intervals
     c0 = cell.counters()
     l0 = pp.launch_count()
-    cell.set_profiling(True)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -271,6 +289,7 @@ def run_ours(args, cfg, ws, rank, local):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        cell.advance_period(1, sh)               # re-capture without events, untimed
         barrier()
         c2 = cell.counters()
         x, vg = cell.circuit_state()
@@ -288,6 +307,12 @@ def run_ours(args, cfg, ws, rank, local):
                "h2d_bytes_per_step": 16 * (2 * n + 1) + 8,
                "d2h_bytes_per_step": pp.C.sizeof(pp.PPRecord) + 4}
 
+    # per-phase breakdown from one extra, separately profiled period (not timed)
+    cell.set_profiling(True, level=2)
+    cell.advance_period(1, sh)
+    breakdown = cell.phase_times()
+    cell.set_profiling(False)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -296,25 +321,29 @@ def run_ours(args, cfg, ws, rank, local):
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     push_ms, push_n = phases["push"]
     per_launch_particles = psteps / max(push_n, 1)
-    achieved = BYTES_PER_PARTICLE_STEP * per_launch_particles / (push_ms / push_n / 1e3) / 1e9
-    traffic = profiled_traffic(args.workload)
+    bpp = BYTES_PER_PARTICLE_STEP if args.form == "fused" else BYTES_PER_PARTICLE_STEP_FP64
+    achieved = bpp * per_launch_particles / (push_ms / push_n / 1e3) / 1e9
+    traffic = profiled_traffic(args.workload) if args.form == "fused" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 particles, f64 fields/circuit",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 particles, f64 fields/circuit" if args.form == "fused" else "f64",
         "data": "synthetic",
         "config": {"workload": workload_desc(cfg, args.workload),
                    "step": "one RF period: %d PIC steps + period end" % cell.n_rf,
                    "l2": "inputs larger than L2 (%.0f MB of particle state)" % (
                        2 * cfg.n_init * 28 / 1e6),
                    "parallelism": "independent cell per GPU" if ws > 1 else "1 cell",
+                   "form": args.form,
                    "time_to_stationary": None},
-        "roofline": {"bound": "hbm", "kernel": "push_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "push_kernel" if args.form == "fused" else "push_plain",
+                     "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "measured" if peaks else "fallback",
-                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
+                     "bytes_per_particle_step": bpp,
                      "avg_launch_ms": push_ms / max(push_n, 1)},
-        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "phase_ms_per_period": {k: v[0] for k, v in breakdown.items()},
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
@@ -327,13 +356,160 @@ def run_ours(args, cfg, ws, rank, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batch of cells
+def run_batch(args, ws, rank, local):
+    """A step is one RF period of every cell of the mixed-size batch (one
+    pp_batch_advance_period); ranks take disjoint slices of the cell list."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_2609_15043_b300 import phasorpic as pp, workloads
+    cfgs_all = workloads.batch_cells()
+    cfgs = cfgs_all[rank::ws]
+    batch = pp.Batch(cfgs)
+    for c, cfg in zip(batch.cells, cfgs):
+        for sp in (0, 1):
+            c.set_particles(sp, workloads.population(cfg, sp))
+    stream = torch.cuda.default_stream()
+    sh = stream.cuda_stream
+    for _ in range(args.warmup):
+        batch.advance_period(1, sh)
+    torch.cuda.synchronize()
+    c0 = [c.counters()["particle_steps"] for c in batch.cells]
+    l0 = pp.launch_count()
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.advance_period(1, sh)
+    e1.record(stream)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = pp.launch_count() - l0
+    psteps = sum(c.counters()["particle_steps"] for c in batch.cells) - sum(c0)
+    ms_all, ps_all = reduce_over_ranks(ms, psteps, dist)
+    value = ps_all / (ms_all / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        states = [c.circuit_state() for c in batch.cells]
+        torch.cuda.synchronize()
+        p0 = sum(c.counters()["particle_steps"] for c in batch.cells)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for c, (x, vg) in zip(batch.cells, states):
+                c.set_circuit_state(x, vg)
+            batch.advance_period(1, sh)
+            recs = [c.turn_phasors(sh) for c in batch.cells]
+            states = [(r["x_next"], r["vg_next"]) for r in recs]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        p1 = sum(c.counters()["particle_steps"] for c in batch.cells)
+        e2e = {"value": (p1 - p0) / dt, "unit": UNIT,
+               "h2d_bytes_per_step": sum(16 * (2 * len(c.turn_r) + 1) + 8 for c in cfgs),
+               "d2h_bytes_per_step": len(cfgs) * (pp.C.sizeof(pp.PPRecord) + 4)}
+    if rank == 0:
+        peaks = measured_peaks()
+        peak = peaks["hbm_gbs"] if peaks else 6400.0
+        achieved = BYTES_PER_PARTICLE_STEP * ps_all / (ms_all / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak" if ws > 1 else "strong", "vs_baseline": None,
+            "dtype": "f32 particles, f64 fields/circuit", "data": "synthetic",
+            "config": {"workload": "batch32: %d independent cells, nr in 64..192 (nz = 1.5 nr), %.3g "
+                                   "macroparticles/species in total, 3-5 turns, 5-50 mTorr, 20-150 W targets"
+                                   % (len(cfgs_all), sum(c.n_init for c in cfgs_all)),
+                       "step": "one RF period of every cell (400 PIC steps + period end each)",
+                       "l2": "inputs larger than L2",
+                       "parallelism": "cells split over ranks" if ws > 1 else "32 cells on per-cell streams"},
+            "roofline": {"bound": "hbm", "kernel": "whole step (52 B per particle-step over the step time)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": "measured" if peaks else "fallback"},
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- time to stationarity
+def run_stationary(args, cfg, local):
+    """Wall time from the initial populations to the first stationary period
+    (paper_2609_15043_b300.stationarity), for the fused FP32 form and the
+    plain FP64 form from the same seeded state; each period's record is read
+    back for the test, as a user would."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2609_15043_b300 import phasorpic as pp, workloads
+    from paper_2609_15043_b300.stationarity import StationarityMonitor
+    out, traces = {}, {}
+    for form in ("fused", "fp64"):
+        c = cfg.replace(plain_fp64=1 if form == "fp64" else 0)
+        cell = pp.Cell(c)
+        for sp in (0, 1):
+            cell.set_particles(sp, workloads.population(c, sp))
+        sh = torch.cuda.current_stream().cuda_stream
+        mon = StationarityMonitor(len(c.turn_r), c.p_target if c.power_control else None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cell.prime(sh)
+        trace = []
+        periods = 0
+        for periods in range(1, args.max_periods + 1):
+            cell.advance_period(1, sh)
+            rec = cell.turn_phasors(sh)
+            trace.append({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in rec.items()
+                          if k in ("p_port", "p_ind", "p_cap", "p_cu", "eps_bal", "vg", "n_live", "accepted")})
+            if mon.update(rec):
+                break
+        wall = time.perf_counter() - t0
+        stationary = mon.stationary_at is not None
+        out[form] = {"stationary": stationary, "periods": periods, "wall_s": wall,
+                     "ms_per_period": 1e3 * wall / periods, "last_window": mon.last,
+                     "status": cell.status()}
+        traces[form] = trace
+        cell.close()
+        del cell
+        torch.cuda.empty_cache()
+    f, d = out["fused"], out["fp64"]
+    ratio = (d["wall_s"] / f["wall_s"]) if f["stationary"] and d["stationary"] else None
+    line = {"metric": "time to a stationary state, fused FP32 vs plain FP64 PIC, 1 B300",
+            "config": {"workload": workload_desc(cfg, args.workload), "max_periods": args.max_periods,
+                       "criteria": "trailing 100 periods: |P_port-P_target|<=1%, balance<=0.5%, "
+                                   "half-window drift<=0.5%"},
+            "time_to_stationary": out, "fp64_over_fused_wall": ratio}
+    if args.trace_out:
+        with open(args.trace_out, "w") as fh:
+            json.dump(traces, fh)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     from paper_2609_15043_b300 import workloads
-    cfg = workloads.WORKLOADS[args.workload]()
+    if args.workload == "batch32" and args.impl != "reference":
+        run_batch(args, ws, rank, local)
+        return
+    cfg = workloads.WORKLOADS[args.workload if args.workload != "batch32" else "cell60"]()
     if args.impl == "reference":
         run_reference(args, cfg, ws, rank)
+    elif args.time_to_stationary:
+        if rank == 0:
+            run_stationary(args, cfg, local)
     else:
         run_ours(args, cfg, ws, rank, local)
 

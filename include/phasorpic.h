@@ -97,6 +97,11 @@ typedef struct pp_config {
     int32_t sort_every[PP_NSPECIES]; /* steps between counting sorts (>= 1) */
     int32_t poisson_max_iter;        /* FP64 refinement sweeps per step (>= 1) */
     double poisson_tol;              /* relative FP64 residual target */
+    int32_t plain_fp64;              /* 1: plain FP64 particle form (one thread per particle, FP64
+                                        state, global atomics), the comparison baseline of the
+                                        default fused FP32 kernel; fields and circuit are FP64 in
+                                        both forms */
+    int32_t reserved0;               /* must be 0 */
 } pp_config;
 
 /* Completed-period record (Sec. 2.4 diagnostics; Eqs. vpind, icap, pport,
@@ -164,6 +169,54 @@ int pp_set_particles(pp_cell* cell, int species, int64_t n, const uint32_t* cell
 int pp_get_particles(pp_cell* cell, int species, int64_t cap, int64_t* n, uint32_t* cell_idx,
                      float* dr, float* dz, float* vr, float* vt, float* vz, uint32_t* uid,
                      void* stream);
+
+/*
+ * Batches of independent cells (different grids, populations, gases and
+ * circuits).  pp_init_batch builds n_cells cells from cfgs[0..n_cells-1] as
+ * pp_init_cell does; pp_batch_cell(i) returns cell i's handle for every
+ * per-cell call (particles, circuit state, records, grids, checkpoints) but
+ * the handle belongs to the batch: pp_destroy refuses it and
+ * pp_batch_destroy frees every cell.  pp_batch_advance_period advances every
+ * cell by n_periods of its own RF periods: each cell runs on its own stream
+ * (forked from and joined back into `stream`), so the work of all cells
+ * shares the GPU.  PP_E_ARG unless every cell sits on a period boundary.
+ * The cells of a batch share no device memory.
+ */
+typedef struct pp_batch pp_batch;
+int pp_init_batch(const pp_config* cfgs, int n_cells, pp_batch** out);
+int pp_batch_size(pp_batch* batch);
+pp_cell* pp_batch_cell(pp_batch* batch, int i);     /* NULL if i is out of range */
+int pp_batch_advance_period(pp_batch* batch, int n_periods, void* stream);
+int pp_batch_destroy(pp_batch* batch);
+
+/* pp_get_particles64 -- as pp_get_particles with the state in double (exact
+ * for the plain FP64 form, widened from float otherwise). */
+int pp_get_particles64(pp_cell* cell, int species, int64_t cap, int64_t* n, uint32_t* cell_idx,
+                       double* dr, double* dz, double* vr, double* vt, double* vz, uint32_t* uid,
+                       void* stream);
+
+/*
+ * pp_checkpoint -- snapshot of everything a cell carries from one PIC step to
+ * the next: the configuration, the step index and sort phase, the device
+ * state (circuit state, controller, period accumulators, counters, last
+ * record), the potential, window charge, field phasors, harmonic current
+ * accumulators with their compensation terms, and every particle slot of both
+ * species.  The snapshot is a self-describing byte image; restoring it into a
+ * cell built from the same pp_config continues the run bit for bit.
+ * With host_buf == NULL only *bytes is set (the size needed).  Otherwise
+ * *bytes is the buffer's size on entry and the bytes written on return;
+ * PP_E_ARG (with *bytes set to the size needed) if it is too small.
+ * Synchronises the device; the buffer is owned by the caller.
+ */
+int pp_checkpoint(pp_cell* cell, void* host_buf, uint64_t* bytes);
+
+/*
+ * pp_restore -- loads a pp_checkpoint image into `cell`.  PP_E_ARG if the
+ * image is truncated, of another format version, or was taken from a cell
+ * whose pp_config differs byte for byte; PP_E_CAPACITY if its populations
+ * exceed the cell's capacity.  Synchronises the device.
+ */
+int pp_restore(pp_cell* cell, const void* host_buf, uint64_t bytes);
 
 /*
  * pp_prime -- deposits the charge of the current populations and solves the
@@ -300,10 +353,12 @@ int pp_get_counters(pp_cell* cell, int64_t* out, void* stream);
 int pp_get_poisson_stats(pp_cell* cell, int* sweeps, double* rel, void* stream);
 
 /*
- * pp_set_profiling -- when enable != 0 every later step records CUDA events on
- * its stream around five phases: [0] the fused particle kernel, [1] the
- * Poisson refinement, [2] counting sorts, [3] the other per-step kernels,
- * [4] the period end.  pp_get_phase_times sums the recorded intervals (ms,
+ * pp_set_profiling -- enable = 1: every later step records CUDA events on its
+ * stream around the fused particle kernel; enable = 2: around five phases,
+ * [0] the particle kernel, [1] the Poisson refinement, [2] counting sorts,
+ * [3] the other per-step kernels, [4] the period end; 0 switches it off.
+ * Inside a replayed period graph the events are graph nodes and the library
+ * waits for each replay to read them.  pp_get_phase_times sums the recorded intervals (ms,
  * 5 entries; counts: intervals per phase, may be NULL) and clears them; it
  * waits for the recorded events.
  */

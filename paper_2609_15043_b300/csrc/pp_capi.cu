@@ -12,24 +12,45 @@ static thread_local std::string g_err;
 void set_error(const std::string& s) { g_err = s; }
 unsigned long long g_launches = 0;
 
-// records an event on st for phase `ph` (start when open, stop otherwise)
+// records an event on st for phase `ph` (start when open, stop otherwise);
+// during a graph capture the pairs are recorded into the graph and kept in a
+// pool of their own
+static thread_local bool g_capturing = false;
+static std::vector<cudaEvent_t>* pool_of(Cell* c);
 static void phase_mark(Cell* c, int ph, bool start, cudaStream_t st) {
     if (!c->profiling) return;
-    size_t k = c->ev_used;
+    if (c->profile_level < 2 && ph != PH_PUSH) return;
+    std::vector<cudaEvent_t>& pool = *pool_of(c);
+    std::vector<int>& phase = g_capturing ? c->gev_phase : c->ev_phase;
+    size_t& used = g_capturing ? c->gev_used : c->ev_used;
+    size_t k = used;
     if (start) {
-        if (2 * k + 2 > c->ev_pool.size()) {
+        if (2 * k + 2 > pool.size()) {
             for (int q = 0; q < 256; ++q) {
                 cudaEvent_t e;
                 cudaEventCreate(&e);
-                c->ev_pool.push_back(e);
+                pool.push_back(e);
             }
         }
-        c->ev_phase.resize(k + 1);
-        c->ev_phase[k] = ph;
-        cudaEventRecord(c->ev_pool[2 * k], st);
+        phase.resize(k + 1);
+        phase[k] = ph;
+        // inside a capture the record must be external to become a timestamp
+        cudaEventRecordWithFlags(pool[2 * k], st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     } else {
-        cudaEventRecord(c->ev_pool[2 * k + 1], st);
-        c->ev_used = k + 1;
+        cudaEventRecordWithFlags(pool[2 * k + 1], st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        used = k + 1;
+    }
+}
+static std::vector<cudaEvent_t>* pool_of(Cell* c) { return g_capturing ? &c->gev_pool : &c->ev_pool; }
+
+// adds the elapsed times of recorded pairs into the running sums
+static void collect_pairs(Cell* c, std::vector<cudaEvent_t>& pool, std::vector<int>& phase, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        cudaEventSynchronize(pool[2 * k + 1]);
+        float t = 0;
+        cudaEventElapsedTime(&t, pool[2 * k], pool[2 * k + 1]);
+        c->prof_ms[phase[k]] += t;
+        c->prof_n[phase[k]] += 1;
     }
 }
 
@@ -42,6 +63,9 @@ static int cuda_check(cudaError_t e, const char* what) {
 static void free_cell(Cell* c) {
     if (!c) return;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->gev_pool) cudaEventDestroy(e);
+    if (c->period_exec) cudaGraphExecDestroy(c->period_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_st) cudaFreeHost(c->h_st);
     delete c;
@@ -61,12 +85,20 @@ static void one_step(Cell* c, cudaStream_t st) {
     int64_t s = c->s;
     double th = theta(c, s), th1 = theta(c, s + 1);
     phase_mark(c, PH_OTHER, true, st);
-    cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
-    cudaMemsetAsync(c->d_jm, 0, sizeof(float) * c->nnodes, st);
+    if (c->fp64) {
+        cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * c->nnodes, st);
+        cudaMemsetAsync(c->d_jm64, 0, sizeof(double) * c->nnodes, st);
+    } else {
+        cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
+        cudaMemsetAsync(c->d_jm, 0, sizeof(float) * c->nnodes, st);
+    }
     launch_field_prep(c, std::cos(th), std::sin(th), st);
     phase_mark(c, PH_OTHER, false, st);
     phase_mark(c, PH_PUSH, true, st);
-    launch_push(c, (uint32_t)s, st);
+    if (c->fp64)
+        launch_push_plain(c, st);
+    else
+        launch_push(c, st);
     phase_mark(c, PH_PUSH, false, st);
     phase_mark(c, PH_OTHER, true, st);
     launch_append(c, st);
@@ -98,9 +130,193 @@ static void one_step(Cell* c, cudaStream_t st) {
     }
 }
 
+// A whole RF period can be replayed from one captured graph when the step
+// sequence repeats exactly: the cell sits on a period boundary, every sort
+// cadence divides N_RF an even number of times (so the buffer parity returns)
+// and the sort counters are aligned.  Per-step phases and the device step
+// counter make the captured kernels valid for every period.
+static bool graph_eligible(const Cell* c) {
+    if (!c->use_graphs || c->s % c->n_rf != 0) return false;
+    for (int sp = 0; sp < 2; ++sp) {
+        int e = c->cfg.sort_every[sp];
+        if (c->sort_count[sp] != 0 || c->n_rf % e != 0 || (c->n_rf / e) % 2 != 0) return false;
+    }
+    return true;
+}
+
+static int capture_period(Cell* c) {
+    if (c->period_exec) {
+        cudaGraphExecDestroy(c->period_exec);
+        c->period_exec = nullptr;
+    }
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("could not create the capture stream");
+        return PP_E_CUDA;
+    }
+    push_prepare(c);
+    const int64_t s0 = c->s;
+    const int cur0[2] = {c->cur[0], c->cur[1]};
+    const unsigned long long l0 = g_launches;
+    c->gev_used = 0;
+    g_capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < c->n_rf; ++k) one_step(c, c->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    g_capturing = false;
+    c->s = s0;                                   // nothing ran yet
+    c->graph_launches = g_launches - l0;
+    g_launches = l0;
+    if (e != cudaSuccess || e2 != cudaSuccess || !g || c->cur[0] != cur0[0] || c->cur[1] != cur0[1] ||
+        c->sort_count[0] != 0 || c->sort_count[1] != 0) {
+        if (g) cudaGraphDestroy(g);
+        c->cur[0] = cur0[0];
+        c->cur[1] = cur0[1];
+        c->use_graphs = false;                   // fall back to the step loop for this cell
+        cudaGetLastError();
+        return PP_OK;
+    }
+    e = cudaGraphInstantiate(&c->period_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->period_exec = nullptr;
+        c->use_graphs = false;
+        cudaGetLastError();
+        return PP_OK;
+    }
+    c->graph_cur[0] = cur0[0];
+    c->graph_cur[1] = cur0[1];
+    c->graph_prof = c->profile_level;
+    c->graph_pairs = c->gev_used;
+    return PP_OK;
+}
+
+static int run_period_graph(Cell* c, cudaStream_t st) {
+    if (!c->period_exec || c->graph_cur[0] != c->cur[0] || c->graph_cur[1] != c->cur[1] ||
+        c->graph_prof != c->profile_level) {
+        int rc = capture_period(c);
+        if (rc) return rc;
+        if (!c->period_exec) return 1;           // not capturable: caller steps instead
+    }
+    cudaError_t e = cudaGraphLaunch(c->period_exec, st);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+        return PP_E_CUDA;
+    }
+    g_launches += c->graph_launches;
+    c->s += c->n_rf;
+    if (c->profiling) collect_pairs(c, c->gev_pool, c->gev_phase, c->graph_pairs);
+    return PP_OK;
+}
+
+
+// A batch of independent cells (possibly of different grids and
+// populations).  Each cell keeps its own stream and period graph; a batch
+// period forks the caller's stream into the cells' streams, replays every
+// cell's period there and joins, so the blocks of all cells' kernels share
+// the GPU and the small latency-bound solves of one cell overlap the particle
+// kernels of the others.
+struct Batch {
+    std::vector<Cell*> cells;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+};
+
+static void free_batch(Batch* b) {
+    if (!b) return;
+    for (Cell* c : b->cells) free_cell(c);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+static int pp_prime_on(Cell* c, cudaStream_t st);
+
+static int advance_cell_periods(Cell* c, int n_periods, cudaStream_t st) {
+    if (!c->primed) {
+        int rc = pp_prime_on(c, st);
+        if (rc) return rc;
+    }
+    for (int p = 0; p < n_periods; ++p) {
+        int rc = graph_eligible(c) ? run_period_graph(c, st) : 1;
+        if (rc < 0) return rc;
+        if (rc == 1)
+            for (int k = 0; k < c->n_rf; ++k) one_step(c, st);
+    }
+    return cuda_check(cudaGetLastError(), "advancing RF periods");
+}
+
 }  // namespace pp
 
 using namespace pp;
+
+// live particles of one species in slot order, state widened to double
+static int gather_live(Cell* c, int sp, cudaStream_t st, std::vector<uint32_t>& cl, std::vector<uint32_t>& u,
+                       std::vector<double> (&v)[5]) {
+    int ns = 0;
+    cudaMemcpyAsync(&ns, c->d_nslot + sp, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int rc = cuda_check(cudaStreamSynchronize(st), "reading the particle count");
+    if (rc) return rc;
+    cl.resize(ns);
+    u.resize(ns);
+    for (auto& x : v) x.resize(ns);
+    size_t b4 = sizeof(float) * (size_t)ns;
+    if (c->fp64) {
+        PBuf<double>& p = c->pd[sp][c->cur[sp]];
+        cudaMemcpy(cl.data(), p.cell, b4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(u.data(), p.uid, b4, cudaMemcpyDeviceToHost);
+        double* srcs[5] = {p.dr, p.dz, p.vr, p.vt, p.vz};
+        for (int f = 0; f < 5; ++f) cudaMemcpy(v[f].data(), srcs[f], sizeof(double) * (size_t)ns, cudaMemcpyDeviceToHost);
+    } else {
+        ParticleBuf& p = c->pb[sp][c->cur[sp]];
+        cudaMemcpy(cl.data(), p.cell, b4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(u.data(), p.uid, b4, cudaMemcpyDeviceToHost);
+        float* srcs[5] = {p.dr, p.dz, p.vr, p.vt, p.vz};
+        std::vector<float> tmp(ns);
+        for (int f = 0; f < 5; ++f) {
+            cudaMemcpy(tmp.data(), srcs[f], b4, cudaMemcpyDeviceToHost);
+            for (int q = 0; q < ns; ++q) v[f][q] = tmp[q];
+        }
+    }
+    return cuda_check(cudaGetLastError(), "reading particles");
+}
+
+template <typename T>
+static int get_particles_t(pp_cell* h, int sp, int64_t cap, int64_t* n, uint32_t* cell_idx, T* dr, T* dz, T* vr,
+                           T* vt, T* vz, uint32_t* uid, void* stream) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || sp < 0 || sp > 1 || !n) {
+        set_error("bad argument to pp_get_particles");
+        return PP_E_ARG;
+    }
+    std::vector<uint32_t> cl, u;
+    std::vector<double> v[5];
+    int rc = gather_live(c, sp, (cudaStream_t)stream, cl, u, v);
+    if (rc) return rc;
+    int64_t m = 0;
+    for (uint32_t x : cl)
+        if (x != kDead) ++m;
+    *n = m;
+    if (m > cap) {
+        set_error("output arrays too small");
+        return PP_E_CAPACITY;
+    }
+    T* outs[5] = {dr, dz, vr, vt, vz};
+    int64_t o = 0;
+    for (size_t q = 0; q < cl.size(); ++q) {
+        if (cl[q] == kDead) continue;
+        if (cell_idx) cell_idx[o] = cl[q];
+        if (uid) uid[o] = u[q];
+        for (int f = 0; f < 5; ++f)
+            if (outs[f]) outs[f][o] = (T)v[f][q];
+        ++o;
+    }
+    return PP_OK;
+}
 
 extern "C" {
 
@@ -128,6 +344,10 @@ int pp_init_cell(const pp_config* cfg, pp_cell** out) {
 int pp_destroy(pp_cell* h) {
     Cell* c = reinterpret_cast<Cell*>(h);
     if (!c) return PP_OK;
+    if (c->in_batch) {
+        set_error("a cell of a batch is destroyed with its batch (pp_batch_destroy)");
+        return PP_E_ARG;
+    }
     cudaDeviceSynchronize();
     free_cell(c);
     return PP_OK;
@@ -162,15 +382,28 @@ int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, co
         umax = std::max(umax, uid[q] + 1u);
     }
     cudaDeviceSynchronize();
-    ParticleBuf& p = c->pb[sp][c->cur[sp]];
     size_t b4 = sizeof(float) * (size_t)n;
-    cudaMemcpy(p.cell, cell_idx, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.dr, dr, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.dz, dz, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.vr, vr, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.vt, vt, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.vz, vz, b4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p.uid, uid, b4, cudaMemcpyHostToDevice);
+    if (c->fp64) {
+        PBuf<double>& p = c->pd[sp][c->cur[sp]];
+        std::vector<double> tmp((size_t)n);
+        const float* srcs[5] = {dr, dz, vr, vt, vz};
+        double* dsts[5] = {p.dr, p.dz, p.vr, p.vt, p.vz};
+        for (int f = 0; f < 5; ++f) {
+            for (int64_t q = 0; q < n; ++q) tmp[q] = (double)srcs[f][q];
+            cudaMemcpy(dsts[f], tmp.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+        }
+        cudaMemcpy(p.cell, cell_idx, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.uid, uid, b4, cudaMemcpyHostToDevice);
+    } else {
+        ParticleBuf& p = c->pb[sp][c->cur[sp]];
+        cudaMemcpy(p.cell, cell_idx, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.dr, dr, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.dz, dz, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.vr, vr, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.vt, vt, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.vz, vz, b4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p.uid, uid, b4, cudaMemcpyHostToDevice);
+    }
     int ni = (int)n;
     cudaMemcpy(c->d_nslot + sp, &ni, sizeof(int), cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_next_uid + sp, &umax, sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -184,48 +417,178 @@ int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, co
 
 int pp_get_particles(pp_cell* h, int sp, int64_t cap, int64_t* n, uint32_t* cell_idx, float* dr, float* dz,
                      float* vr, float* vt, float* vz, uint32_t* uid, void* stream) {
+    return get_particles_t<float>(h, sp, cap, n, cell_idx, dr, dz, vr, vt, vz, uid, stream);
+}
+
+int pp_get_particles64(pp_cell* h, int sp, int64_t cap, int64_t* n, uint32_t* cell_idx, double* dr, double* dz,
+                       double* vr, double* vt, double* vz, uint32_t* uid, void* stream) {
+    return get_particles_t<double>(h, sp, cap, n, cell_idx, dr, dz, vr, vt, vz, uid, stream);
+}
+
+// ---------------------------------------------------------------- checkpoint
+// image: CkHeader, pp_config, DevState, next uids, node grids, particle slots
+struct CkHeader {
+    uint32_t magic, version, cfg_bytes, state_bytes;
+    int32_t nnodes, nslot[2], sort_count[2], primed;
+    int64_t s;
+};
+static const uint32_t kCkMagic = 0x4b435050u;   // "PPCK"
+static const uint32_t kCkVersion = 1;
+
+static std::vector<std::pair<double*, size_t>> ck_grids(Cell* c) {
+    size_t n = (size_t)c->nnodes;
+    return {{c->d_phi, n},  {c->d_win, n},  {c->d_Ec, n},   {c->d_Ess, n},        {c->d_Ecp, n},
+            {c->d_Essp, n}, {c->d_Ecp_new, n}, {c->d_Essp_new, n}, {c->d_Br, 4 * n}, {c->d_Jc, n},
+            {c->d_Js, n},   {c->d_Jc_c, n}, {c->d_Js_c, n}};
+}
+
+// member-wise (the struct has padding whose bytes are unspecified)
+static bool cfg_equal(const pp_config& a, const pp_config& b) {
+#define PP_EQ(f) (std::memcmp(&a.f, &b.f, sizeof(a.f)) == 0)
+    return PP_EQ(nr) && PP_EQ(nz) && PP_EQ(r_max) && PP_EQ(z_max) && PP_EQ(z_win_lo) && PP_EQ(z_win_hi) &&
+           PP_EQ(eps_win) && PP_EQ(z_coil) && PP_EQ(n_turns) && PP_EQ(winding) && PP_EQ(turn_r) &&
+           PP_EQ(wire_radius) && PP_EQ(freq) && PP_EQ(dt) && PP_EQ(full_helmholtz) && PP_EQ(magnetic_force) &&
+           PP_EQ(pressure_pa) && PP_EQ(t_gas) && PP_EQ(r_g) && PP_EQ(r_m) && PP_EQ(l_m) && PP_EQ(c_m) &&
+           PP_EQ(c_stray) && PP_EQ(rho20) && PP_EQ(alpha_cu) && PP_EQ(t_coil_c) && PP_EQ(r_rf_override) &&
+           PP_EQ(v_g) && PP_EQ(phase_g) && PP_EQ(power_control) && PP_EQ(p_target) && PP_EQ(gamma) &&
+           PP_EQ(n_trend) && PP_EQ(eps_p) && PP_EQ(alpha_v) && PP_EQ(f_step) && PP_EQ(v_min) && PP_EQ(v_max) &&
+           PP_EQ(alpha) && PP_EQ(weight) && PP_EQ(capacity) && PP_EQ(seed) && PP_EQ(sort_every) &&
+           PP_EQ(poisson_max_iter) && PP_EQ(poisson_tol) && PP_EQ(plain_fp64);
+#undef PP_EQ
+}
+
+// the seven particle arrays of the current buffer and their element sizes
+static void ck_arrays(Cell* c, int sp, void** arr, size_t* es) {
+    if (c->fp64) {
+        PBuf<double>& p = c->pd[sp][c->cur[sp]];
+        void* a[7] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid};
+        for (int f = 0; f < 7; ++f) {
+            arr[f] = a[f];
+            es[f] = (f == 0 || f == 6) ? 4 : 8;
+        }
+    } else {
+        ParticleBuf& p = c->pb[sp][c->cur[sp]];
+        void* a[7] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid};
+        for (int f = 0; f < 7; ++f) {
+            arr[f] = a[f];
+            es[f] = 4;
+        }
+    }
+}
+
+static uint64_t ck_size(Cell* c, const int* nslot) {
+    uint64_t b = sizeof(CkHeader) + sizeof(pp_config) + sizeof(DevState) + 2 * sizeof(uint32_t);
+    for (auto& g : ck_grids(c)) b += sizeof(double) * g.second;
+    const uint64_t per = c->fp64 ? 2 * 4 + 5 * 8 : 7 * 4;
+    for (int sp = 0; sp < 2; ++sp) b += per * (uint64_t)nslot[sp];
+    return b;
+}
+
+int pp_checkpoint(pp_cell* h, void* host_buf, uint64_t* bytes) {
     Cell* c = reinterpret_cast<Cell*>(h);
-    if (!c || sp < 0 || sp > 1 || !n) {
-        set_error("bad argument to pp_get_particles");
+    if (!c || !bytes) {
+        set_error("bad argument to pp_checkpoint");
         return PP_E_ARG;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    int ns = 0;
-    cudaMemcpyAsync(&ns, c->d_nslot + sp, sizeof(int), cudaMemcpyDeviceToHost, st);
-    int rc = cuda_check(cudaStreamSynchronize(st), "pp_get_particles");
+    int rc = cuda_check(cudaDeviceSynchronize(), "pp_checkpoint");
     if (rc) return rc;
-    std::vector<uint32_t> cl(ns), u(ns);
-    std::vector<float> a(ns), b(ns), x(ns), y(ns), z(ns);
-    ParticleBuf& p = c->pb[sp][c->cur[sp]];
-    size_t b4 = sizeof(float) * (size_t)ns;
-    cudaMemcpy(cl.data(), p.cell, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(a.data(), p.dr, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(b.data(), p.dz, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(x.data(), p.vr, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(y.data(), p.vt, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(z.data(), p.vz, b4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(u.data(), p.uid, b4, cudaMemcpyDeviceToHost);
-    int64_t m = 0;
-    for (int q = 0; q < ns; ++q)
-        if (cl[q] != kDead) ++m;
-    *n = m;
-    if (m > cap) {
-        set_error("output arrays too small");
+    int nslot[2];
+    cudaMemcpy(nslot, c->d_nslot, sizeof(nslot), cudaMemcpyDeviceToHost);
+    uint64_t need = ck_size(c, nslot);
+    if (!host_buf) {
+        *bytes = need;
+        return PP_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        set_error("checkpoint buffer too small");
+        return PP_E_ARG;
+    }
+    char* o = static_cast<char*>(host_buf);
+    CkHeader hd{kCkMagic, kCkVersion, (uint32_t)sizeof(pp_config), (uint32_t)sizeof(DevState), c->nnodes,
+                {nslot[0], nslot[1]}, {c->sort_count[0], c->sort_count[1]}, c->primed ? 1 : 0, c->s};
+    std::memcpy(o, &hd, sizeof hd);
+    o += sizeof hd;
+    std::memcpy(o, &c->cfg, sizeof(pp_config));
+    o += sizeof(pp_config);
+    cudaMemcpy(o, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost);
+    o += sizeof(DevState);
+    cudaMemcpy(o, c->d_next_uid, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    o += 2 * sizeof(uint32_t);
+    for (auto& g : ck_grids(c)) {
+        cudaMemcpy(o, g.first, sizeof(double) * g.second, cudaMemcpyDeviceToHost);
+        o += sizeof(double) * g.second;
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        void* arr[7];
+        size_t es[7];
+        ck_arrays(c, sp, arr, es);
+        for (int f = 0; f < 7; ++f) {
+            size_t nb = es[f] * (size_t)nslot[sp];
+            cudaMemcpy(o, arr[f], nb, cudaMemcpyDeviceToHost);
+            o += nb;
+        }
+    }
+    *bytes = need;
+    return cuda_check(cudaDeviceSynchronize(), "pp_checkpoint copies");
+}
+
+int pp_restore(pp_cell* h, const void* host_buf, uint64_t bytes) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !host_buf || bytes < sizeof(CkHeader)) {
+        set_error("bad argument to pp_restore");
+        return PP_E_ARG;
+    }
+    CkHeader hd;
+    std::memcpy(&hd, host_buf, sizeof hd);
+    if (hd.magic != kCkMagic || hd.version != kCkVersion || hd.cfg_bytes != sizeof(pp_config) ||
+        hd.state_bytes != sizeof(DevState) || hd.nnodes != c->nnodes) {
+        set_error("not a checkpoint of this format or grid");
+        return PP_E_ARG;
+    }
+    if (hd.nslot[0] < 0 || hd.nslot[1] < 0 || bytes < ck_size(c, hd.nslot)) {
+        set_error("truncated checkpoint");
+        return PP_E_ARG;
+    }
+    const char* o = static_cast<const char*>(host_buf) + sizeof hd;
+    pp_config saved;
+    std::memcpy(&saved, o, sizeof saved);
+    if (!cfg_equal(saved, c->cfg)) {
+        set_error("checkpoint was taken from a cell with another configuration");
+        return PP_E_ARG;
+    }
+    o += sizeof(pp_config);
+    if (hd.nslot[0] > c->cap[0] || hd.nslot[1] > c->cap[1]) {
+        set_error("checkpoint populations exceed the cell's capacity");
         return PP_E_CAPACITY;
     }
-    int64_t o = 0;
-    for (int q = 0; q < ns; ++q) {
-        if (cl[q] == kDead) continue;
-        if (cell_idx) cell_idx[o] = cl[q];
-        if (dr) dr[o] = a[q];
-        if (dz) dz[o] = b[q];
-        if (vr) vr[o] = x[q];
-        if (vt) vt[o] = y[q];
-        if (vz) vz[o] = z[q];
-        if (uid) uid[o] = u[q];
-        ++o;
+    int rc = cuda_check(cudaDeviceSynchronize(), "pp_restore");
+    if (rc) return rc;
+    cudaMemcpy(c->d_st, o, sizeof(DevState), cudaMemcpyHostToDevice);
+    o += sizeof(DevState);
+    cudaMemcpy(c->d_next_uid, o, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    o += 2 * sizeof(uint32_t);
+    for (auto& g : ck_grids(c)) {
+        cudaMemcpy(g.first, o, sizeof(double) * g.second, cudaMemcpyHostToDevice);
+        o += sizeof(double) * g.second;
     }
-    return PP_OK;
+    for (int sp = 0; sp < 2; ++sp) {
+        void* arr[7];
+        size_t es[7];
+        ck_arrays(c, sp, arr, es);
+        for (int f = 0; f < 7; ++f) {
+            size_t nb = es[f] * (size_t)hd.nslot[sp];
+            cudaMemcpy(arr[f], o, nb, cudaMemcpyHostToDevice);
+            o += nb;
+        }
+    }
+    cudaMemcpy(c->d_nslot, hd.nslot, sizeof(hd.nslot), cudaMemcpyHostToDevice);
+    c->s = hd.s;
+    c->sort_count[0] = hd.sort_count[0];
+    c->sort_count[1] = hd.sort_count[1];
+    c->primed = hd.primed != 0;
+    c->graph_cur[0] = c->graph_cur[1] = -1;     // re-capture the period graph
+    return cuda_check(cudaDeviceSynchronize(), "pp_restore copies");
 }
 
 int pp_prime(pp_cell* h, void* stream) {
@@ -234,14 +597,24 @@ int pp_prime(pp_cell* h, void* stream) {
         set_error("NULL cell");
         return PP_E_ARG;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
+    return pp_prime_on(c, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+static int pp_prime_on(Cell* c, cudaStream_t st) {
+    if (c->fp64)
+        cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * c->nnodes, st);
+    else
+        cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
     launch_deposit_only(c, st);
     double th = theta(c, c->s);
     poisson_refine(c, std::cos(th), std::sin(th), st, false, nullptr);
     c->primed = true;
     return cuda_check(cudaGetLastError(), "pp_prime");
 }
+
+extern "C" {
 
 int pp_advance_steps(pp_cell* h, int n_steps, void* stream) {
     Cell* c = reinterpret_cast<Cell*>(h);
@@ -268,7 +641,88 @@ int pp_advance_period(pp_cell* h, int n_periods, void* stream) {
         set_error("the cell is not on an RF-period boundary");
         return PP_E_ARG;
     }
-    return pp_advance_steps(h, n_periods * c->n_rf, stream);
+    return advance_cell_periods(c, n_periods, (cudaStream_t)stream);
+}
+
+int pp_init_batch(const pp_config* cfgs, int n_cells, pp_batch** out) {
+    if (!cfgs || !out || n_cells < 1) {
+        set_error("bad argument to pp_init_batch");
+        return PP_E_ARG;
+    }
+    *out = nullptr;
+    Batch* b = new Batch();
+    for (int i = 0; i < n_cells; ++i) {
+        pp_cell* h = nullptr;
+        int rc = pp_init_cell(&cfgs[i], &h);
+        if (rc != PP_OK) {
+            set_error("cell " + std::to_string(i) + ": " + g_err);
+            free_batch(b);
+            return rc;
+        }
+        Cell* c = reinterpret_cast<Cell*>(h);
+        c->in_batch = true;
+        b->cells.push_back(c);
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            if (s) cudaStreamDestroy(s);
+            free_batch(b);
+            set_error("could not create the batch streams");
+            return PP_E_CUDA;
+        }
+        b->streams.push_back(s);
+        b->done.push_back(e);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        free_batch(b);
+        set_error("could not create the batch events");
+        return PP_E_CUDA;
+    }
+    *out = reinterpret_cast<pp_batch*>(b);
+    return PP_OK;
+}
+
+int pp_batch_size(pp_batch* h) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    return b ? (int)b->cells.size() : 0;
+}
+
+pp_cell* pp_batch_cell(pp_batch* h, int i) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    if (!b || i < 0 || i >= (int)b->cells.size()) return nullptr;
+    return reinterpret_cast<pp_cell*>(b->cells[i]);
+}
+
+int pp_batch_advance_period(pp_batch* h, int n_periods, void* stream) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    if (!b || n_periods < 0) {
+        set_error("bad argument to pp_batch_advance_period");
+        return PP_E_ARG;
+    }
+    for (Cell* c : b->cells)
+        if (c->s % c->n_rf != 0) {
+            set_error("a cell of the batch is not on an RF-period boundary");
+            return PP_E_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEventRecord(b->fork, st);
+    for (size_t i = 0; i < b->cells.size(); ++i) {
+        cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        int rc = advance_cell_periods(b->cells[i], n_periods, b->streams[i]);
+        if (rc) return rc;
+        cudaEventRecord(b->done[i], b->streams[i]);
+    }
+    for (size_t i = 0; i < b->cells.size(); ++i) cudaStreamWaitEvent(st, b->done[i], 0);
+    return cuda_check(cudaGetLastError(), "pp_batch_advance_period");
+}
+
+int pp_batch_destroy(pp_batch* h) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    if (!b) return PP_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return PP_OK;
 }
 
 int pp_set_circuit_state(pp_cell* h, const double* x, double vg) {
@@ -359,6 +813,10 @@ int pp_get_grid(pp_cell* h, int which, double* host, int64_t n, void* stream) {
         case PP_GRID_WINDOW: src = c->d_win; break;
         case PP_GRID_CHARGE:
         case PP_GRID_JMOM: {
+            if (c->fp64) {
+                src = which == PP_GRID_CHARGE ? c->d_rho64 : c->d_jm64;
+                break;
+            }
             std::vector<float> tmp(c->nnodes);
             cudaMemcpy(tmp.data(), which == PP_GRID_CHARGE ? c->d_rho : c->d_jm, sizeof(float) * c->nnodes,
                        cudaMemcpyDeviceToHost);
@@ -402,9 +860,12 @@ int pp_poisson_solve(pp_cell* h, const double* q, const double* turn_phi, double
     cudaMemcpy(phi_save.data(), c->d_phi, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
     cudaMemcpy(win_save.data(), c->d_win, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
     cudaMemcpy(rho_save.data(), c->d_rho, sizeof(float) * c->nnodes, cudaMemcpyDeviceToHost);
+    std::vector<double> rho64_save(c->fp64 ? c->nnodes : 0);
+    if (c->fp64) cudaMemcpy(rho64_save.data(), c->d_rho64, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
     // the charge goes in FP64 through the window array (exact), rho = 0
     cudaMemcpy(c->d_win, q, sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
     cudaMemset(c->d_rho, 0, sizeof(float) * c->nnodes);
+    if (c->fp64) cudaMemset(c->d_rho64, 0, sizeof(double) * c->nnodes);
     cudaMemset(c->d_phi, 0, sizeof(double) * c->nnodes);
     cudaMemcpy(c->d_ext_targets, turn_phi, sizeof(double) * c->nturns, cudaMemcpyHostToDevice);
     poisson_refine(c, 1.0, 0.0, 0, true, c->d_ext_targets);
@@ -432,6 +893,7 @@ int pp_poisson_solve(pp_cell* h, const double* q, const double* turn_phi, double
     cudaMemcpy(c->d_phi, phi_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_win, win_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_rho, rho_save.data(), sizeof(float) * c->nnodes, cudaMemcpyHostToDevice);
+    if (c->fp64) cudaMemcpy(c->d_rho64, rho64_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
     return rc;
 }
 
@@ -511,7 +973,12 @@ int pp_set_profiling(pp_cell* h, int enable) {
     }
     cudaDeviceSynchronize();
     c->profiling = enable != 0;
+    c->profile_level = enable;
     c->ev_used = 0;
+    for (int q = 0; q < 8; ++q) {
+        c->prof_ms[q] = 0;
+        c->prof_n[q] = 0;
+    }
     return PP_OK;
 }
 
@@ -521,18 +988,14 @@ int pp_get_phase_times(pp_cell* h, double* ms, int64_t* counts) {
         set_error("bad argument to pp_get_phase_times");
         return PP_E_ARG;
     }
-    for (int q = 0; q < PH_N; ++q) {
-        ms[q] = 0;
-        if (counts) counts[q] = 0;
-    }
-    for (size_t k = 0; k < c->ev_used; ++k) {
-        cudaEventSynchronize(c->ev_pool[2 * k + 1]);
-        float t = 0;
-        cudaEventElapsedTime(&t, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]);
-        ms[c->ev_phase[k]] += t;
-        if (counts) counts[c->ev_phase[k]] += 1;
-    }
+    collect_pairs(c, c->ev_pool, c->ev_phase, c->ev_used);
     c->ev_used = 0;
+    for (int q = 0; q < PH_N; ++q) {
+        ms[q] = c->prof_ms[q];
+        if (counts) counts[q] = c->prof_n[q];
+        c->prof_ms[q] = 0;
+        c->prof_n[q] = 0;
+    }
     return cuda_check(cudaGetLastError(), "pp_get_phase_times");
 }
 

@@ -54,6 +54,46 @@ __global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __r
     }
 }
 
+// First product of a refinement sweep, preceded by the convergence decision
+// on the residual of this sweep: every block reads the same norms and either
+// all return (converged) or all compute.
+__global__ void gemm_check(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int rows,
+                           int K, int N, DevState* st, int sweep, double tol, int* done) {
+    if (*done) return;
+    double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
+    double sn = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
+    double rel = (sn > 0) ? rn / sn : 0.0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        st->prel = rel;
+        st->piters = sweep;
+        if (rel <= tol) *done = 1;
+    }
+    if (rel <= tol) return;
+    __shared__ float As[32][33];
+    __shared__ float Bs[32][33];
+    int tx = threadIdx.x, ty = threadIdx.y;
+    int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    float acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int q = 0; q < 4; ++q) {
+            int r = ty + 8 * q;
+            As[r][tx] = (r0 + r < rows && k0 + tx < K) ? A[(size_t)(r0 + r) * K + k0 + tx] : 0.f;
+            Bs[r][tx] = (k0 + r < K && c0 + tx < N) ? B[(size_t)(k0 + r) * N + c0 + tx] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            float b = Bs[k][tx];
+            for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * b;
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        int r = r0 + ty + 8 * q, cc = c0 + tx;
+        if (r < rows && cc < N) C[(size_t)r * N + cc] = acc[q];
+    }
+}
+
 // Thomas sweep per mode with precomputed factors.  A block takes MB modes:
 // all of their rows of f, c' and 1/denominator are staged in shared memory
 // with coalesced row loads, one warp runs the two dependent recurrences out of
@@ -109,6 +149,66 @@ static int tri_modes_per_block(int rows) {
     return mb;
 }
 
+// Parallel cyclic reduction of the per-mode z systems with precomputed level
+// coefficients (mode-major: al[(m L + l) rows + i]).  One block per mode; a
+// thread owns rows i = t + k*blockDim for k < EPT and holds every level's
+// coefficients in registers, so a level is two shared loads and two FMAs.
+template <int EPT>
+__global__ void __launch_bounds__(256) pcr_solve(const float* __restrict__ f, float* __restrict__ x,
+                                                 const float* __restrict__ al, const float* __restrict__ ga,
+                                                 const float* __restrict__ ib, int rows, int M, int L, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float d[2][256 * EPT];
+    const int m = blockIdx.x;
+    float ra[kMaxPcrLevels][EPT], rg[kMaxPcrLevels][EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        int i = threadIdx.x + k * 256;
+        bool ok = i < rows;
+        d[0][threadIdx.x + k * 256] = ok ? f[(size_t)i * M + m] : 0.f;
+#pragma unroll
+        for (int l = 0; l < kMaxPcrLevels; ++l) {
+            bool lk = ok && l < L;
+            ra[l][k] = lk ? al[((size_t)m * L + l) * rows + i] : 0.f;
+            rg[l][k] = lk ? ga[((size_t)m * L + l) * rows + i] : 0.f;
+        }
+    }
+    __syncthreads();
+    int cur = 0;
+#pragma unroll
+    for (int l = 0; l < kMaxPcrLevels; ++l) {
+        if (l >= L) break;
+        const int st = 1 << l;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            int i = threadIdx.x + k * 256;
+            if (i < rows) {
+                float v = d[cur][i];
+                if (i - st >= 0) v += ra[l][k] * d[cur][i - st];
+                if (i + st < rows) v += rg[l][k] * d[cur][i + st];
+                d[cur ^ 1][i] = v;
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        int i = threadIdx.x + k * 256;
+        if (i < rows) x[(size_t)i * M + m] = d[cur][i] * ib[(size_t)m * rows + i];
+    }
+}
+
+static void launch_pcr(const Cell* c, const float* f, float* x, cudaStream_t st, const int* skip) {
+    int rows = c->ps.rows, M = c->ps.M, L = c->pcr_levels;
+    if (rows <= 256)
+        pcr_solve<1><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+    else if (rows <= 512)
+        pcr_solve<2><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+    else
+        pcr_solve<4><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+}
+
 template <typename T>
 void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, const int* skip) {
     dim3 blk(32, 8), grd((s.M + 31) / 32, (s.rows + 31) / 32);
@@ -140,6 +240,7 @@ __device__ __forceinline__ double turn_target(const DevState* st, const double* 
 struct PoisArgs {
     const double* phi;
     const float* rho;
+    const double* rho64;           // node charge of the plain FP64 form (used when set)
     const double* win;
     const double* eps_row;
     const double* az;
@@ -185,7 +286,8 @@ __global__ void poisson_residual(PoisArgs a) {
             double t2 = a.az[j] * emz * (a.phi[n - a.NR] - pc);
             double t3 = eb * a.arp[j] * (a.phi[n + 1] - pc);
             double t4 = (j > 0) ? eb * a.arm[j] * (a.phi[n - 1] - pc) : 0.0;
-            double b = -((double)a.rho[n] + a.win[n]) * a.inv2pieps0;
+            double q = a.rho64 ? a.rho64[n] : (double)a.rho[n];
+            double b = -(q + a.win[n]) * a.inv2pieps0;
             double r = b - (((t1 + t2) + t3) + t4);
             a.r32[idx] = (float)r;
             rmax = fabs(r);
@@ -234,6 +336,40 @@ __global__ void poisson_cap(const DevState* st, const double* ext, const double*
     }
 }
 
+// the turn nodes take their Dirichlet values before the sweeps, so every
+// later correction there is zero and no kernel of the solve writes them
+__global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn_k, int K, const DevState* st,
+                                  const double* ext, int nt, double cs, double sn) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < K) phi[tn_node[t]] = turn_target(st, ext, tn_k[t], nt, cs, sn);
+}
+
+// phi += d0 + Z sigma with sigma = G^-1 (-d0_T) computed by every block
+// (the turn nodes already hold their targets)
+__global__ void poisson_update_cap(double* phi, const float* d0, const float* Z, const double* Ginv,
+                                   const int* tn_int, int K, int rows, int M, int NR,
+                                   const signed char* turn_mask, const int* done) {
+    if (*done) return;
+    __shared__ double s_r[kMaxCapNodes];
+    __shared__ double s_sig[kMaxCapNodes];
+    for (int q = threadIdx.x; q < K; q += blockDim.x) s_r[q] = -(double)d0[tn_int[q]];
+    __syncthreads();
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+        double sg = 0;
+        for (int u = 0; u < K; ++u) sg += Ginv[q * K + u] * s_r[u];
+        s_sig[q] = sg;
+    }
+    __syncthreads();
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * M) return;
+    int n = (idx / M + 1) * NR + idx % M;
+    if (turn_mask[n] >= 0) return;
+    double d = (double)d0[idx];
+    size_t stride = (size_t)rows * M;
+    for (int t = 0; t < K; ++t) d += s_sig[t] * (double)Z[t * stride + idx];
+    phi[n] += d;
+}
+
 __global__ void poisson_update(double* phi, const float* d0, const float* Z, const double* sigma, int K,
                                int rows, int M, int NR, const signed char* turn_mask, const DevState* st,
                                const double* ext, int nt, double cs, double sn, const int* done) {
@@ -255,8 +391,9 @@ __global__ void poisson_update(double* phi, const float* d0, const float* Z, con
 
 // ---------------------------------------------------------------- node fields
 // per plasma cell 5 float4 (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10, 11)
+template <typename T>
 __global__ void field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
-                           const double* __restrict__ Ess, const double* __restrict__ B, float* F,
+                           const double* __restrict__ Ess, const double* __restrict__ B, T* F,
                            int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
                            double sn, int magnetic) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,7 +410,7 @@ __global__ void field_prep(const double* __restrict__ phi, const double* __restr
         Br = B[n] * cs + B[nnodes + n] * sn;
         Bz = B[2 * nnodes + n] * cs + B[3 * nnodes + n] * sn;
     }
-    float v[5] = {(float)Er, (float)Ez, (float)Et, (float)Br, (float)Bz};
+    T v[5] = {(T)Er, (T)Ez, (T)Et, (T)Br, (T)Bz};
     // node (i, j) is corner 00 of cell (i, j), 01 of (i, j-1), 10 of (i-1, j), 11 of (i-1, j-1)
     for (int corner = 0; corner < 4; ++corner) {
         int ci = i - (corner >> 1), cj = j - (corner & 1);
@@ -311,6 +448,7 @@ __global__ void turn_sample(DevState* st, const double* phi, const int* ft, cons
         st->q_prev[k] = Q;
     }
     st->n_samples += 1;
+    st->step += 1;
     kahan_add(st->p_ind, st->p_ind_c, st->p_ind_step * inv_n);
     kahan_add(st->p_es, st->p_es_c, st->p_es_step * inv_n);
     st->p_ind_step = 0;
@@ -318,7 +456,8 @@ __global__ void turn_sample(DevState* st, const double* phi, const int* ft, cons
 }
 
 // J_c += (2/N) cos(theta) J, J_s += (2/N) sin(theta) J over the plasma nodes
-__global__ void accumulate_nodes(const float* jm, const double* vol, double* Jc, double* Js, double* Jcc,
+template <typename T>
+__global__ void accumulate_nodes(const T* jm, const double* vol, double* Jc, double* Js, double* Jcc,
                                  double* Jsc, int nn, double wc, double ws) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
@@ -426,16 +565,25 @@ void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
 
 void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
     int nn = (c->i_win + 1) * c->NR;
-    accumulate_nodes<<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
-                                                       c->d_Js_c, nn, wc, ws);
+    if (c->fp64)
+        accumulate_nodes<double><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
+                                                                   c->d_Jc_c, c->d_Js_c, nn, wc, ws);
+    else
+        accumulate_nodes<float><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
+                                                                  c->d_Js_c, nn, wc, ws);
     count_launch();
 }
 
 void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
     int n = (c->i_win + 1) * c->NR;
-    field_prep<<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->NR, c->nr,
-                                                c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
-                                                c->cfg.magnetic_force);
+    if (c->fp64)
+        field_prep<double><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64, c->NR,
+                                                            c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
+                                                            c->cfg.magnetic_force);
+    else
+        field_prep<float><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->NR,
+                                                           c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
+                                                           c->cfg.magnetic_force);
     count_launch();
 }
 
@@ -447,11 +595,12 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     DevState* dst = c->d_st;
     cudaMemsetAsync(&dst->pnorm[0], 0, sizeof(dst->pnorm), st);
     cudaMemsetAsync(&dst->pdone, 0, sizeof(int), st);
-    const int* done = &dst->pdone;
+    int* done = &dst->pdone;
     const double* ext = external_targets ? d_targets : nullptr;
     PoisArgs a;
     a.phi = c->d_phi;
     a.rho = c->d_rho;
+    a.rho64 = c->fp64 ? c->d_rho64 : nullptr;
     a.win = c->d_win;
     a.eps_row = c->d_eps_row;
     a.az = c->d_az;
@@ -469,22 +618,26 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     a.nt = c->nturns;
     a.cs = cs;
     a.sn = sn;
-    int K = c->ntn;
+    const int K = c->ntn;
+    poisson_set_turns<<<(K + 63) / 64, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K, dst, ext, c->nturns, cs, sn);
+    count_launch();
+    dim3 gblk(32, 8), ggrd((M + 31) / 32, (rows + 31) / 32);
     for (int it = 0; it <= maxit; ++it) {
         a.norm = &dst->pnorm[2 * it];
         poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
-        poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, &dst->pdone, it == maxit ? 1 : 0);
-        count_launch(2);
-        if (it == maxit) break;
-        // d0 = P(r): the second GEMM writes t0 after the tridiagonal sweep has
-        // consumed it, so t0 holds d0 afterwards
-        sep_solve<float>(c->ps, c->d_r32, c->ps.t0, st, done);
-        poisson_cap<<<1, kMaxCapNodes, 0, st>>>(dst, ext, c->d_phi, c->ps.t0, c->d_tn_node, c->d_tn_int,
-                                                c->d_tn_k, c->d_Ginv, c->d_sigma, K, c->nturns, cs, sn, done);
-        poisson_update<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Z, c->d_sigma, K, rows, M,
-                                                            c->NR, c->d_turn_mask, dst, ext, c->nturns, cs,
-                                                            sn, done);
-        count_launch(2);
+        count_launch();
+        if (it == maxit) {
+            poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, done, 1);
+            count_launch();
+            break;
+        }
+        // d0 = Vb-transform of the per-mode z solves of (r Vf)
+        gemm_check<<<ggrd, gblk, 0, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, rows, M, M, dst, it, c->cfg.poisson_tol, done);
+        launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
+        gemm_rm<float><<<ggrd, gblk, 0, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, M, done);
+        poisson_update_cap<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Z, c->d_Ginv, c->d_tn_int, K,
+                                                                rows, M, c->NR, c->d_turn_mask, done);
+        count_launch(4);
     }
     return 0;
 }
@@ -576,6 +729,7 @@ extern "C" int pp_poisson_solve_noalloc(pp_cell* h, const double* d_q, const dou
     PoisArgs a;
     a.phi = d_phi;
     a.rho = rho0;
+    a.rho64 = nullptr;
     a.win = d_q;
     a.eps_row = c->d_eps_row;
     a.az = c->d_az;

@@ -21,8 +21,6 @@ constexpr double kAmu = 1.66053906660e-27;
 constexpr double kMAr = 39.948 * kAmu;
 constexpr double kKb = 1.380649e-23;
 constexpr double kPi = 3.14159265358979323846;
-constexpr float kEExc = 11.55f;   // eV
-constexpr float kEIon = 15.76f;   // eV
 constexpr uint32_t kDead = 0xFFFFFFFFu;
 
 constexpr int kPushThreads = 256;
@@ -32,27 +30,36 @@ constexpr int kTileRows = 8;                      // node rows of the shared dep
 constexpr int kMaxNR = 513;                       // node columns supported by the tile
 constexpr int kEventCap = 8192;                   // ionisation events per step
 constexpr int kMaxCapNodes = 64;                  // turn nodes handled by the capacitance matrix
+constexpr int kMaxPcrLevels = 10;                 // cyclic reduction of z systems of up to 1024 rows
 
 // ---------------------------------------------------------------- particles
-struct ParticleBuf {
+// SoA particle store of state type T (float: the fused path; double: the
+// plain FP64 form)
+template <typename T>
+struct PBuf {
     uint32_t* cell;
-    float* dr;
-    float* dz;
-    float* vr;
-    float* vt;
-    float* vz;
+    T* dr;
+    T* dz;
+    T* vr;
+    T* vt;
+    T* vz;
     uint32_t* uid;
 };
+using ParticleBuf = PBuf<float>;
 
-struct SpeciesConst {   // float constants of one species (rounded once from FP64)
-    float qmh, dtr, dtz, qw, numax, pnull, ng, ce, inv_ce, loss, vth_gas;
+template <typename T>
+struct SpecT {          // constants of one species in T (rounded once from FP64)
+    T qmh, dtr, dtz, qw, numax, pnull, ng, ce, inv_ce, loss, vth_gas;
 };
+using SpeciesConst = SpecT<float>;
 
-struct Event {          // one ionisation: new e- and Ar+ at the parent's position
+template <typename T>
+struct EventT {         // one ionisation: new e- and Ar+ at the parent's position
     uint32_t parent, cell;
-    float dr, dz;
-    float ve[3], vi[3];
+    T dr, dz;
+    T ve[3], vi[3];
 };
+using Event = EventT<float>;
 
 // cumulative counters (unsigned long long), index = pp_get_counters order
 enum {
@@ -75,6 +82,7 @@ struct DevState {
     unsigned long long cnt[C_NCOUNT];        // cumulative
     unsigned long long per[C_NCOUNT];        // this period
     unsigned long long live[2];              // live macroparticles per species
+    unsigned long long step;                 // PIC steps completed (drives the RNG counters)
     unsigned int status;
     int n_events;                            // events recorded this step
     int accepted;                            // last period end accepted
@@ -118,11 +126,19 @@ struct Cell {
     std::vector<double> r_rf;
     SpeciesConst sc[2];
 
-    // particles
+    // particles (plain FP64 form: pd, scd, d_events64, d_F64, d_rho64, d_jm64)
+    bool fp64 = false;
     ParticleBuf pb[2][2];
+    PBuf<double> pd[2][2];
+    SpecT<double> scd[2];
+    EventT<double>* d_events64 = nullptr;
+    double* d_F64 = nullptr;
+    double* d_rho64 = nullptr;
+    double* d_jm64 = nullptr;
     int cur[2] = {0, 0};
     int64_t cap[2] = {0, 0};
     uint32_t div_magic = 0, div_shift = 0;  // cell / nr by multiply-high and shift
+    int push_blocks = 0;                    // persistent grid of the particle kernel
     int* d_nslot = nullptr;                 // [2] used slots (live + absorbed since last sort)
     uint32_t* d_next_uid = nullptr;         // [2]
     uint32_t* d_hist = nullptr;             // counting-sort bins (ncell + 2)
@@ -162,6 +178,10 @@ struct Cell {
 
     // Poisson: FP32 separable inner solve + capacitance correction
     SepSolver<float> ps;
+    int pcr_levels = 0;                     // cyclic-reduction levels of the z systems
+    float* d_pcr_a = nullptr;               // levels x rows x M
+    float* d_pcr_g = nullptr;               // levels x rows x M
+    float* d_pcr_ib = nullptr;              // rows x M
     float* d_r32 = nullptr;                 // residual (interior layout)
     double* d_rT = nullptr;                 // turn-node residuals
     double* d_sigma = nullptr;
@@ -183,9 +203,26 @@ struct Cell {
 
     // phase timing (CUDA events on the launching stream), enabled on request
     bool profiling = false;
+    int profile_level = 0;                 // 1: the particle kernel only, 2: every phase
     std::vector<cudaEvent_t> ev_pool;      // pairs: [2k] start, [2k+1] stop
     std::vector<int> ev_phase;             // phase of pair k
     size_t ev_used = 0;
+    std::vector<cudaEvent_t> gev_pool;     // pairs recorded inside the period graph
+    std::vector<int> gev_phase;
+    size_t gev_used = 0;
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    // one captured RF period (valid while the sort phase and buffer parity match)
+    cudaGraphExec_t period_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int graph_cur[2] = {-1, -1};
+    int graph_prof = 0;
+    size_t graph_pairs = 0;                // event pairs recorded in the graph
+    unsigned long long graph_launches = 0; // kernels in the graph
+    bool use_graphs = true;
+
+    bool in_batch = false;                 // owned by a pp_batch (destroyed with it)
 
     std::vector<void*> allocs;
     template <typename T>
@@ -210,7 +247,9 @@ int setup_cell(Cell* c);
 
 // ---------------------------------------------------------------- launchers
 void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st);
-void launch_push(Cell* c, uint32_t step, cudaStream_t st);
+void launch_push(Cell* c, cudaStream_t st);
+void launch_push_plain(Cell* c, cudaStream_t st);
+void push_prepare(Cell* c);
 void launch_append(Cell* c, cudaStream_t st);
 void launch_sort(Cell* c, int sp, cudaStream_t st);
 void launch_deposit_only(Cell* c, cudaStream_t st);

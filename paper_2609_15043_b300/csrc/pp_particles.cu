@@ -8,95 +8,11 @@
 // float32 instantiation of the oracle, so cell crossings, absorptions and
 // collision decisions of a step are reproduced exactly.
 #include "pp_internal.h"
+#include "pp_mcc.cuh"
 
 #include <climits>
 
 namespace pp {
-
-// ---------------------------------------------------------------- Philox4x32-10
-// Salmon et al., SC'11: round (c0..c3; k0,k1) -> (hi(M1 c2)^c1^k0, lo(M1 c2),
-// hi(M0 c0)^c3^k1, lo(M0 c0)), key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
-
-// Philox2x32-10 (same paper): round (c0, c1; k) -> (hi(M c0) ^ k ^ c1, lo(M c0)),
-// M = 0xD256D193, key bumped by 0x9E3779B9; first output only
-__device__ __forceinline__ uint32_t philox2x32_10(uint32_t c0, uint32_t c1, uint32_t k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) k += 0x9E3779B9u;
-        uint32_t hi = __umulhi(0xD256D193u, c0), lo = 0xD256D193u * c0;
-        c0 = hi ^ k ^ c1;
-        c1 = lo;
-    }
-    return c0;
-}
-
-// ((x >> 9) + 0.5) * 2^-23, exact in float32, in (0, 1)
-__device__ __forceinline__ float u01(uint32_t x) {
-    return (float)(int)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
-}
-
-struct U4 {
-    float a, b, c, d;
-};
-
-__device__ __forceinline__ U4 draw4(uint32_t uid, uint32_t step, uint32_t call, uint32_t sp, uint32_t k0,
-                                    uint32_t k1) {
-    uint4 r = philox4x32_10(make_uint4(uid, step, call, sp), k0, k1);
-    return U4{u01(r.x), u01(r.y), u01(r.z), u01(r.w)};
-}
-
-// ---------------------------------------------------------------- cross sections
-// electron-Ar (units 1e-20 m^2) at energy x (eV); project-defined rational fits
-__device__ __forceinline__ void sigma_e(float x, float& el, float& ex, float& iz) {
-    float y = x - 0.23f;
-    float y2 = y * y;
-    el = (0.1f + 14.0f * y2 / (y2 + 4.0f)) / (1.0f + x / 50.0f);
-    float ye = x - kEExc;
-    ex = (x > kEExc) ? 1.2f * ye / (ye * ye / 30.0f + ye + 8.0f) : 0.0f;
-    float yi = x - kEIon;
-    iz = (x > kEIon) ? 3.0f * yi / (yi * yi / 60.0f + yi + 30.0f) : 0.0f;
-}
-
-// Ar+-Ar charge exchange and isotropic elastic (units 1e-19 m^2) at lab energy x
-__device__ __forceinline__ void sigma_i(float x, float& cx, float& iso) {
-    float sq = sqrtf(x);
-    cx = 2.0f + 3.0f / (1.0f + sq);
-    iso = 1.0f + 2.0f / (1.0f + sq);
-}
-
-__device__ __forceinline__ void iso_dir(float u2, float u3, float& dx, float& dy, float& dz) {
-    float c = 1.0f - 2.0f * u2;
-    float s = sqrtf(fmaxf(1.0f - c * c, 0.0f));
-    float sp, cp;
-    sincospif(2.0f * u3, &sp, &cp);
-    dx = s * cp;
-    dy = s * sp;
-    dz = c;
-}
-
-__device__ __forceinline__ void gauss3(float a, float b, float c, float d, float& n0, float& n1, float& n2) {
-    float ra = sqrtf(-2.0f * logf(a));
-    float rc = sqrtf(-2.0f * logf(c));
-    float sb, cb, sd, cd;
-    sincospif(2.0f * b, &sb, &cb);
-    sincospif(2.0f * d, &sd, &cd);
-    n0 = ra * cb;
-    n1 = ra * sb;
-    n2 = rc * cd;
-}
 
 // ---------------------------------------------------------------- TMA bulk copies
 // 1-D bulk copies between global and shared memory (cp.async.bulk), completed
@@ -265,7 +181,8 @@ struct PushArgs {
     double* win;
     int nr, NR, i_win;
     uint32_t div_magic, div_shift;  // cell / nr = umulhi(cell, magic) >> shift
-    uint32_t step, key0, key1;
+    const unsigned long long* step;  // device step counter (RNG counter word)
+    uint32_t key0, key1;
     Event* ev;
     DevState* st;
 };
@@ -278,102 +195,6 @@ struct PushSmem {
                256;
     }
 };
-
-__device__ __forceinline__ void electron_collision(const PushArgs& a, const SpeciesConst& S, uint32_t uid,
-                                                   float& vx, float& vy, float& vz, uint32_t cell, float drn,
-                                                   float dzn, unsigned* cnt) {
-    U4 u = draw4(uid, a.step, 0u, 0u, a.key0, a.key1);
-    float x = vx, y = vy, z = vz;
-    float v2 = x * x + y * y + z * z;
-    float g = sqrtf(v2);
-    float en = v2 * S.ce;
-    float s_el, s_ex, s_iz;
-    sigma_e(en, s_el, s_ex, s_iz);
-    float nu_el = S.ng * s_el * g;
-    float nu_ex = S.ng * s_ex * g;
-    float nu_iz = S.ng * s_iz * g;
-    float r = u.b * S.numax;
-    float c1 = nu_el, c2 = c1 + nu_ex, c3 = c2 + nu_iz;
-    if (c3 > S.numax) ++cnt[5];
-    int proc = (r < c1) ? 0 : (r < c2) ? 1 : (r < c3) ? 2 : 3;
-    if (proc == 3) return;
-    const float one = 1.0f;
-    float dx, dy, dzz;
-    iso_dir(u.c, u.d, dx, dy, dzz);
-    float gn;
-    if (proc == 0) {
-        float cosx = (g > 0.0f) ? (x * dx + y * dy + z * dzz) / g : 0.0f;
-        gn = g * sqrtf(one - S.loss * (one - cosx));
-        ++cnt[0];
-    } else if (proc == 1) {
-        gn = sqrtf(fmaxf(en - kEExc, 0.0f) * S.inv_ce);
-        ++cnt[1];
-    } else {
-        float eh = fmaxf(en - kEIon, 0.0f) * 0.5f;
-        gn = sqrtf(eh * S.inv_ce);
-        ++cnt[2];
-        U4 a1 = draw4(uid, a.step, 1u, 0u, a.key0, a.key1);
-        U4 b1 = draw4(uid, a.step, 2u, 0u, a.key0, a.key1);
-        float ex_, ey_, ez_, g0, g1, g2;
-        iso_dir(a1.a, a1.b, ex_, ey_, ez_);
-        gauss3(a1.c, a1.d, b1.a, b1.b, g0, g1, g2);
-        int slot = atomicAdd(&a.st->n_events, 1);
-        if (slot < kEventCap) {
-            Event e;
-            e.parent = uid;
-            e.cell = cell;
-            e.dr = drn;
-            e.dz = dzn;
-            e.ve[0] = gn * ex_;
-            e.ve[1] = gn * ey_;
-            e.ve[2] = gn * ez_;
-            e.vi[0] = a.sp[1].vth_gas * g0;
-            e.vi[1] = a.sp[1].vth_gas * g1;
-            e.vi[2] = a.sp[1].vth_gas * g2;
-            a.ev[slot] = e;
-        } else {
-            atomicOr(&a.st->status, (unsigned)PP_ST_EVENTS);
-        }
-    }
-    vx = gn * dx;
-    vy = gn * dy;
-    vz = gn * dzz;
-}
-
-__device__ __forceinline__ void ion_collision(const PushArgs& a, const SpeciesConst& S, uint32_t uid, float& vx,
-                                              float& vy, float& vz, unsigned* cnt) {
-    U4 u = draw4(uid, a.step, 0u, 1u, a.key0, a.key1);
-    U4 a1 = draw4(uid, a.step, 1u, 1u, a.key0, a.key1);
-    float g0, g1, g2;
-    gauss3(a1.a, a1.b, a1.c, a1.d, g0, g1, g2);
-    float vnxn = S.vth_gas * g0, vnyn = S.vth_gas * g1, vnzn = S.vth_gas * g2;
-    float x = vx, y = vy, z = vz;
-    float gx = x - vnxn, gy = y - vnyn, gz = z - vnzn;
-    float g2s = gx * gx + gy * gy + gz * gz;
-    float g = sqrtf(g2s);
-    float en = g2s * S.ce;
-    float s_cx, s_iso;
-    sigma_i(en, s_cx, s_iso);
-    float nu_cx = S.ng * s_cx * g;
-    float nu_iso = S.ng * s_iso * g;
-    float r = u.b * S.numax;
-    float c1 = nu_cx, c2 = c1 + nu_iso;
-    if (c2 > S.numax) ++cnt[5];
-    if (r < c1) {
-        vx = vnxn;
-        vy = vnyn;
-        vz = vnzn;
-        ++cnt[3];
-    } else if (r < c2) {
-        float dx, dy, dzz;
-        iso_dir(u.c, u.d, dx, dy, dzz);
-        float hg = g * 0.5f;
-        vx = (x + vnxn) * 0.5f + hg * dx;
-        vy = (y + vnyn) * 0.5f + hg * dy;
-        vz = (z + vnzn) * 0.5f + hg * dzz;
-        ++cnt[4];
-    }
-}
 
 // One block owns a chunk of kChunk consecutive particles of one species at a
 // time: TMA bulk copies bring the seven SoA slices into shared memory, each
@@ -405,6 +226,7 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
     const int nr = a.nr, NR = a.NR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x;
+    const uint32_t step = (uint32_t)(*a.step);
 
     if (t == 0) {
         mbar_init(&s_bar, 1);
@@ -594,7 +416,7 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
                 dep_home(dq, tq, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
                          S.qw * (drn * dzn));
                 // null-collision test; candidates are processed densely below
-                uint32_t r = philox2x32_10(s_uid[p], (a.step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
+                uint32_t r = philox2x32_10(s_uid[p], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
                                            a.key0 ^ a.key1);
                 if (u01(r) < S.pnull) {
                     int slot = atomicAdd(&s_ncand, 1);
@@ -615,13 +437,14 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
         __syncthreads();
         // ---- phase B: collisions of the candidates
         const int nc = s_ncand;
+        const CollCtx<float> cc{a.key0, a.key1, a.ev, a.st, a.sp[1].vth_gas};
         for (int c = t; c < nc; c += kPushThreads) {
             const int p = s_cand[c];
             float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
             if (sp == 0)
-                electron_collision(a, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], cnt);
+                electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], cnt);
             else
-                ion_collision(a, S, s_uid[p], vx, vy, vzz, cnt);
+                ion_collision(cc, step, S, s_uid[p], vx, vy, vzz, cnt);
             s_vr[p] = vx;
             s_vt[p] = vy;
             s_vz[p] = vzz;
@@ -687,7 +510,18 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
     }
 }
 
-void launch_push(Cell* c, uint32_t step, cudaStream_t st) {
+void push_prepare(Cell* c) {
+    if (c->push_blocks) return;
+    size_t shm = PushSmem::bytes(c->NR);
+    cudaFuncSetAttribute(push_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int dev = 0, nsm = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel, kPushThreads, shm);
+    c->push_blocks = nsm * (per < 1 ? 1 : per);
+}
+
+void launch_push(Cell* c, cudaStream_t st) {
     PushArgs a;
     for (int s = 0; s < 2; ++s) {
         a.p[s] = c->pb[s][c->cur[s]];
@@ -703,36 +537,28 @@ void launch_push(Cell* c, uint32_t step, cudaStream_t st) {
     a.i_win = c->i_win;
     a.div_magic = c->div_magic;
     a.div_shift = c->div_shift;
-    a.step = step;
+    a.step = &c->d_st->step;
     a.key0 = (uint32_t)(c->cfg.seed & 0xffffffffu);
     a.key1 = (uint32_t)(c->cfg.seed >> 32);
     a.ev = c->d_events;
     a.st = c->d_st;
     size_t shm = PushSmem::bytes(c->NR);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(push_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    int dev = 0, nsm = 148, per = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel, kPushThreads, shm);
-    if (per < 1) per = 1;
-    push_kernel<<<nsm * per, kPushThreads, shm, st>>>(a);
+    push_prepare(c);
+    push_kernel<<<c->push_blocks, kPushThreads, shm, st>>>(a);
     count_launch();
 }
 
 // ---------------------------------------------------------------- prime deposit
-__global__ void deposit_only(ParticleBuf P, const int* nslot, int sp, float qw, float* rho, int nr, int NR) {
+template <typename T>
+__global__ void deposit_only(PBuf<T> P, const int* nslot, int sp, T qw, T* rho, int nr, int NR) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nslot[sp]) return;
     uint32_t cell = P.cell[idx];
     if (cell == kDead) return;
     int iz = (int)(cell / (uint32_t)nr), ir = (int)(cell - (uint32_t)iz * (uint32_t)nr);
-    float dr = P.dr[idx], dz = P.dz[idx];
-    float wa = 1.0f - dr, wb = 1.0f - dz;
-    float* p = rho + iz * NR + ir;
+    T dr = P.dr[idx], dz = P.dz[idx];
+    T wa = T(1.0) - dr, wb = T(1.0) - dz;
+    T* p = rho + iz * NR + ir;
     atomicAdd(p, qw * (wa * wb));
     atomicAdd(p + 1, qw * (dr * wb));
     atomicAdd(p + NR, qw * (wa * dz));
@@ -742,8 +568,13 @@ __global__ void deposit_only(ParticleBuf P, const int* nslot, int sp, float qw, 
 void launch_deposit_only(Cell* c, cudaStream_t st) {
     for (int s = 0; s < 2; ++s) {
         int64_t n = c->cap[s];
-        deposit_only<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->pb[s][c->cur[s]], c->d_nslot, s,
-                                                                 c->sc[s].qw, c->d_rho, c->nr, c->NR);
+        unsigned nb = (unsigned)((n + 255) / 256);
+        if (c->fp64)
+            deposit_only<double><<<nb, 256, 0, st>>>(c->pd[s][c->cur[s]], c->d_nslot, s, c->scd[s].qw, c->d_rho64,
+                                                     c->nr, c->NR);
+        else
+            deposit_only<float><<<nb, 256, 0, st>>>(c->pb[s][c->cur[s]], c->d_nslot, s, c->sc[s].qw, c->d_rho,
+                                                    c->nr, c->NR);
         count_launch();
     }
 }
@@ -751,7 +582,8 @@ void launch_deposit_only(Cell* c, cudaStream_t st) {
 // ---------------------------------------------------------------- append events
 // One block: sort this step's events by parent uid (bitonic, in shared
 // memory) and append the e- / Ar+ pairs with uid = next_uid + rank.
-__global__ void append_kernel(ParticleBuf pe, ParticleBuf pi, int* nslot, uint32_t* next_uid, const Event* ev,
+template <typename T>
+__global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next_uid, const EventT<T>* ev,
                               DevState* st, int64_t cap_e, int64_t cap_i) {
     __shared__ uint32_t key[kEventCap];
     __shared__ uint16_t val[kEventCap];
@@ -790,7 +622,7 @@ __global__ void append_kernel(ParticleBuf pe, ParticleBuf pi, int* nslot, uint32
     if (n_add < 0) n_add = 0;
     uint32_t ue = next_uid[0], ui = next_uid[1];
     for (int r = threadIdx.x; r < n_add; r += blockDim.x) {
-        const Event e = ev[val[r]];
+        const EventT<T> e = ev[val[r]];
         pe.cell[ne + r] = e.cell;
         pe.dr[ne + r] = e.dr;
         pe.dz[ne + r] = e.dz;
@@ -822,8 +654,12 @@ __global__ void append_kernel(ParticleBuf pe, ParticleBuf pi, int* nslot, uint32
 }
 
 void launch_append(Cell* c, cudaStream_t st) {
-    append_kernel<<<1, 1024, 0, st>>>(c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot, c->d_next_uid,
-                                      c->d_events, c->d_st, c->cap[0], c->cap[1]);
+    if (c->fp64)
+        append_kernel<double><<<1, 1024, 0, st>>>(c->pd[0][c->cur[0]], c->pd[1][c->cur[1]], c->d_nslot,
+                                                  c->d_next_uid, c->d_events64, c->d_st, c->cap[0], c->cap[1]);
+    else
+        append_kernel<float><<<1, 1024, 0, st>>>(c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot,
+                                                 c->d_next_uid, c->d_events, c->d_st, c->cap[0], c->cap[1]);
     count_launch();
 }
 
@@ -863,7 +699,8 @@ __global__ void sort_scan(uint32_t* hist, int n) {
     if (t == blockDim.x - 1) hist[n] = part[t];
 }
 
-__global__ void sort_scatter(ParticleBuf src, ParticleBuf dst, const int* nslot, int sp, uint32_t* offs) {
+template <typename T>
+__global__ void sort_scatter(PBuf<T> src, PBuf<T> dst, const int* nslot, int sp, uint32_t* offs) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = idx < nslot[sp];
     uint32_t c = act ? src.cell[idx] : kDead;
@@ -895,11 +732,16 @@ void launch_sort(Cell* c, int sp, cudaStream_t st) {
     cudaMemsetAsync(c->d_hist, 0, sizeof(uint32_t) * (ncell + 2), st);
     int64_t n = c->cap[sp];
     unsigned nb = (unsigned)((n + 255) / 256);
-    ParticleBuf src = c->pb[sp][c->cur[sp]], dst = c->pb[sp][1 - c->cur[sp]];
-    sort_hist<<<nb, 256, 0, st>>>(src.cell, c->d_nslot, sp, c->d_hist, ncell);
+    const uint32_t* src_cell = c->fp64 ? c->pd[sp][c->cur[sp]].cell : c->pb[sp][c->cur[sp]].cell;
+    sort_hist<<<nb, 256, 0, st>>>(src_cell, c->d_nslot, sp, c->d_hist, ncell);
     // live bins only: the dead bin (index ncell) is left out of the scan
     sort_scan<<<1, 1024, 0, st>>>(c->d_hist, ncell);
-    sort_scatter<<<nb, 256, 0, st>>>(src, dst, c->d_nslot, sp, c->d_hist);
+    if (c->fp64)
+        sort_scatter<double><<<nb, 256, 0, st>>>(c->pd[sp][c->cur[sp]], c->pd[sp][1 - c->cur[sp]], c->d_nslot, sp,
+                                                 c->d_hist);
+    else
+        sort_scatter<float><<<nb, 256, 0, st>>>(c->pb[sp][c->cur[sp]], c->pb[sp][1 - c->cur[sp]], c->d_nslot, sp,
+                                                c->d_hist);
     sort_finish<<<1, 1, 0, st>>>(c->d_nslot, sp, c->d_hist, ncell);
     count_launch(4);
     c->cur[sp] = 1 - c->cur[sp];

@@ -163,18 +163,30 @@ static void species_constants(Cell* c) {
         double q = sp == 0 ? -kQe : kQe;
         double m = sp == 0 ? kMe : kMAr;
         double nu = sp == 0 ? nue : nui;
+        SpecT<double>& d = c->scd[sp];
+        d.qmh = q / m * f.dt / 2.0;
+        d.dtr = f.dt / c->dr;
+        d.dtz = f.dt / c->dz;
+        d.qw = q * f.weight[sp];
+        d.numax = nu;
+        d.pnull = -std::expm1(-nu * f.dt);
+        d.ng = n_gas * (sp == 0 ? 1e-20 : 1e-19);
+        d.ce = 0.5 * m / kQe;
+        d.inv_ce = kQe / (0.5 * m);
+        d.loss = 2.0 * kMe / kMAr;
+        d.vth_gas = std::sqrt(kKb * f.t_gas / kMAr);
         SpeciesConst& s = c->sc[sp];
-        s.qmh = (float)(q / m * f.dt / 2.0);
-        s.dtr = (float)(f.dt / c->dr);
-        s.dtz = (float)(f.dt / c->dz);
-        s.qw = (float)(q * f.weight[sp]);
-        s.numax = (float)nu;
-        s.pnull = (float)(-std::expm1(-nu * f.dt));
-        s.ng = (float)(n_gas * (sp == 0 ? 1e-20 : 1e-19));
-        s.ce = (float)(0.5 * m / kQe);
-        s.inv_ce = (float)(kQe / (0.5 * m));
-        s.loss = (float)(2.0 * kMe / kMAr);
-        s.vth_gas = (float)std::sqrt(kKb * f.t_gas / kMAr);
+        s.qmh = (float)d.qmh;
+        s.dtr = (float)d.dtr;
+        s.dtz = (float)d.dtz;
+        s.qw = (float)d.qw;
+        s.numax = (float)d.numax;
+        s.pnull = (float)d.pnull;
+        s.ng = (float)d.ng;
+        s.ce = (float)d.ce;
+        s.inv_ce = (float)d.inv_ce;
+        s.loss = (float)d.loss;
+        s.vth_gas = (float)d.vth_gas;
     }
 }
 
@@ -195,8 +207,10 @@ int setup_cell(Cell* c) {
     pp_config& f = c->cfg;
     if (f.nr < 2 || f.nz < 4 || f.r_max <= 0 || f.z_max <= 0) return fail("grid sizes must be positive");
     if (f.nr + 1 > kMaxNR) return fail("nr exceeds the supported radial node count");
+    if (f.nz - 1 > (1 << kMaxPcrLevels)) return fail("nz exceeds the supported axial node count");
     if (f.n_turns < 1 || f.n_turns > PP_MAX_TURNS) return fail("n_turns out of range");
     if (f.freq <= 0 || f.dt <= 0) return fail("freq and dt must be positive");
+    if ((f.plain_fp64 != 0 && f.plain_fp64 != 1) || f.reserved0 != 0) return fail("plain_fp64 must be 0 or 1");
     c->nr = f.nr;
     c->nz = f.nz;
     c->NR = f.nr + 1;
@@ -343,23 +357,46 @@ int setup_cell(Cell* c) {
     }
 
     // ---- allocations (particle storage padded to whole staging chunks)
+    c->fp64 = f.plain_fp64 != 0;
     for (int sp = 0; sp < 2; ++sp) {
         c->cap[sp] = f.capacity[sp];
         for (int b = 0; b < 2; ++b) {
-            ParticleBuf& p = c->pb[sp][b];
             size_t n = (size_t)((c->cap[sp] + kChunk - 1) / kChunk) * kChunk;
-            p.cell = c->alloc<uint32_t>(n);
-            p.dr = c->alloc<float>(n);
-            p.dz = c->alloc<float>(n);
-            p.vr = c->alloc<float>(n);
-            p.vt = c->alloc<float>(n);
-            p.vz = c->alloc<float>(n);
-            p.uid = c->alloc<uint32_t>(n);
-            if (!p.uid) {
+            bool ok;
+            if (c->fp64) {
+                PBuf<double>& p = c->pd[sp][b];
+                p.cell = c->alloc<uint32_t>(n);
+                p.dr = c->alloc<double>(n);
+                p.dz = c->alloc<double>(n);
+                p.vr = c->alloc<double>(n);
+                p.vt = c->alloc<double>(n);
+                p.vz = c->alloc<double>(n);
+                p.uid = c->alloc<uint32_t>(n);
+                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid;
+                c->pb[sp][b] = ParticleBuf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            } else {
+                ParticleBuf& p = c->pb[sp][b];
+                p.cell = c->alloc<uint32_t>(n);
+                p.dr = c->alloc<float>(n);
+                p.dz = c->alloc<float>(n);
+                p.vr = c->alloc<float>(n);
+                p.vt = c->alloc<float>(n);
+                p.vz = c->alloc<float>(n);
+                p.uid = c->alloc<uint32_t>(n);
+                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid;
+                c->pd[sp][b] = PBuf<double>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            }
+            if (!ok) {
                 set_error("cudaMalloc failed for the particle store");
                 return PP_E_CUDA;
             }
         }
+    }
+    if (c->fp64) {
+        c->d_events64 = c->alloc<EventT<double>>(kEventCap);
+        c->d_F64 = c->alloc<double>((size_t)c->i_win * f.nr * 20);
+        c->d_rho64 = c->alloc<double>(c->nnodes);
+        c->d_jm64 = c->alloc<double>(c->nnodes);
     }
     c->d_nslot = c->alloc<int>(2);
     c->d_next_uid = c->alloc<uint32_t>(2);
@@ -443,6 +480,44 @@ int setup_cell(Cell* c) {
             for (int m = 0; m < M; ++m) diag[(size_t)ii * M + m] = -(ep + em) / dz + (dz / dr) * eb * mu[m];
         }
         thomas_factors(lo, up, diag, rows, M, cp, invd);
+        // parallel cyclic reduction of the same per-mode systems: level l
+        // (stride 2^l) maps d_i -> d_i + alpha_i d_{i-s} + gamma_i d_{i+s};
+        // after the last level x_i = d_i / b_i.  The coefficients depend only
+        // on the operator, so they are reduced here in FP64 once.
+        {
+            int L = 0;
+            while ((1 << L) < rows) ++L;
+            std::vector<double> al((size_t)L * rows * M), ga((size_t)L * rows * M), ib((size_t)rows * M);
+            std::vector<double> a(rows), b(rows), cc(rows), a2(rows), b2(rows), c2(rows);
+            for (int m = 0; m < M; ++m) {
+                for (int i = 0; i < rows; ++i) {
+                    a[i] = lo[i];
+                    b[i] = diag[(size_t)i * M + m];
+                    cc[i] = (i + 1 < rows) ? up[i] : 0.0;
+                }
+                for (int l = 0; l < L; ++l) {
+                    int st = 1 << l;
+                    for (int i = 0; i < rows; ++i) {
+                        int im = i - st, ip = i + st;
+                        double alpha = (im >= 0) ? -a[i] / b[im] : 0.0;
+                        double gamma = (ip < rows) ? -cc[i] / b[ip] : 0.0;
+                        al[((size_t)m * L + l) * rows + i] = alpha;
+                        ga[((size_t)m * L + l) * rows + i] = gamma;
+                        a2[i] = (im >= 0) ? alpha * a[im] : 0.0;
+                        c2[i] = (ip < rows) ? gamma * cc[ip] : 0.0;
+                        b2[i] = b[i] + ((im >= 0) ? alpha * cc[im] : 0.0) + ((ip < rows) ? gamma * a[ip] : 0.0);
+                    }
+                    a.swap(a2);
+                    b.swap(b2);
+                    cc.swap(c2);
+                }
+                for (int i = 0; i < rows; ++i) ib[(size_t)m * rows + i] = 1.0 / b[i];
+            }
+            c->pcr_levels = L;
+            c->d_pcr_a = upload<float>(c, al);
+            c->d_pcr_g = upload<float>(c, ga);
+            c->d_pcr_ib = upload<float>(c, ib);
+        }
         SepSolver<float>& s = c->ps;
         s.rows = rows;
         s.M = M;

@@ -34,7 +34,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_get_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
            "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
            "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
-           "pp_poisson_solve_noalloc"]
+           "pp_poisson_solve_noalloc", "pp_checkpoint", "pp_restore", "pp_get_particles64",
+           "pp_init_batch", "pp_batch_size", "pp_batch_cell", "pp_batch_advance_period", "pp_batch_destroy"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -65,6 +66,8 @@ class PPConfig(C.Structure):
         ("sort_every", C.c_int32 * NSPECIES),
         ("poisson_max_iter", C.c_int32),
         ("poisson_tol", C.c_double),
+        ("plain_fp64", C.c_int32),
+        ("reserved0", C.c_int32),
     ]
 
 
@@ -121,6 +124,14 @@ def _load():
         "pp_poisson_solve_noalloc": (I, [V, V, V, V, V, V]),
         "pp_n_rf": (I, [V]),
         "pp_step_index": (C.c_int64, [V]),
+        "pp_checkpoint": (I, [V, V, P(C.c_uint64)]),
+        "pp_get_particles64": (I, [V, I, C.c_int64, P(C.c_int64), V, V, V, V, V, V, V, V]),
+        "pp_init_batch": (I, [V, I, P(V)]),
+        "pp_batch_size": (I, [V]),
+        "pp_batch_cell": (V, [V, I]),
+        "pp_batch_advance_period": (I, [V, I, V]),
+        "pp_batch_destroy": (I, [V]),
+        "pp_restore": (I, [V, V, C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -180,25 +191,30 @@ def make_config(cfg, capacity=None, weight=None, poisson_max_iter=4, poisson_tol
     c.sort_every[0], c.sort_every[1] = cfg.sort_every_e, cfg.sort_every_i
     c.poisson_max_iter = poisson_max_iter
     c.poisson_tol = poisson_tol
+    c.plain_fp64 = int(getattr(cfg, "plain_fp64", 0))
     return c
 
 
 class Cell:
     """One RF cell on the current CUDA device (pp_init_cell ... pp_destroy)."""
 
-    def __init__(self, cfg, **kw):
+    def __init__(self, cfg, _handle=None, **kw):
         self.cfg = cfg
         self.pcfg = make_config(cfg, **kw)
-        h = C.c_void_p()
-        _check(lib.pp_init_cell(C.byref(self.pcfg), C.byref(h)), "pp_init_cell")
+        self.owned = _handle is None
+        if _handle is None:
+            h = C.c_void_p()
+            _check(lib.pp_init_cell(C.byref(self.pcfg), C.byref(h)), "pp_init_cell")
+        else:
+            h = C.c_void_p(_handle)
         self.h = h
         self.n_turns = len(cfg.turn_r)
         self.NZ, self.NR = cfg.nz + 1, cfg.nr + 1
 
     def close(self):
-        if self.h:
+        if self.h and self.owned:
             lib.pp_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -222,15 +238,17 @@ class Cell:
                                                      ("cell", "dr", "dz", "vr", "vt", "vz", "uid")]),
                "pp_set_particles")
 
-    def get_particles(self, sp, cap=None, stream=0):
+    def get_particles(self, sp, cap=None, stream=0, dtype=np.float32):
+        """Live particles of species sp; dtype float64 reads the state through
+        pp_get_particles64 (exact for the plain FP64 form)."""
         if cap is None:
             cap = int(self.pcfg.capacity[sp])
-        out = {k: np.empty(cap, np.uint32 if k in ("cell", "uid") else np.float32)
+        out = {k: np.empty(cap, np.uint32 if k in ("cell", "uid") else dtype)
                for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")}
         n = C.c_int64()
-        _check(lib.pp_get_particles(self.h, sp, cap, C.byref(n),
-                                    *[_ptr(out[k]) for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")],
-                                    C.c_void_p(stream)), "pp_get_particles")
+        fn = lib.pp_get_particles64 if dtype == np.float64 else lib.pp_get_particles
+        _check(fn(self.h, sp, cap, C.byref(n), *[_ptr(out[k]) for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")],
+                  C.c_void_p(stream)), "pp_get_particles")
         return {k: v[:n.value] for k, v in out.items()}
 
     def prime(self, stream=0):
@@ -314,8 +332,8 @@ def _poisson_stats(self, stream=0):
 Cell.poisson_stats = _poisson_stats
 
 
-def _set_profiling(self, on=True):
-    _check(lib.pp_set_profiling(self.h, 1 if on else 0), "pp_set_profiling")
+def _set_profiling(self, on=True, level=2):
+    _check(lib.pp_set_profiling(self.h, level if on else 0), "pp_set_profiling")
 
 
 def _phase_times(self):
@@ -337,7 +355,55 @@ def _poisson_solve_noalloc(self, d_q, d_turn_phi, d_phi, d_info=0, stream=0):
 
 
 Cell.poisson_solve_noalloc = _poisson_solve_noalloc
+
+
+def _checkpoint(self):
+    """The cell's full step-to-step state as a bytes image (pp_checkpoint)."""
+    n = C.c_uint64(0)
+    _check(lib.pp_checkpoint(self.h, None, C.byref(n)), "pp_checkpoint")
+    buf = np.zeros(n.value, np.uint8)
+    _check(lib.pp_checkpoint(self.h, _ptr(buf), C.byref(n)), "pp_checkpoint")
+    return buf[:n.value].tobytes()
+
+
+def _restore(self, image):
+    buf = np.frombuffer(image, np.uint8)
+    _check(lib.pp_restore(self.h, _ptr(buf), C.c_uint64(buf.size)), "pp_restore")
+
+
+Cell.checkpoint = _checkpoint
+Cell.restore = _restore
 Cell.phase_times = _phase_times
+
+
+class Batch:
+    """Independent cells advanced together (pp_init_batch ... pp_batch_destroy);
+    batch.cells[i] is a Cell view of cell i (owned by the batch)."""
+
+    def __init__(self, cfgs, **kw):
+        self.cfgs = list(cfgs)
+        arr = (PPConfig * len(self.cfgs))(*[make_config(c, **kw) for c in self.cfgs])
+        self._arr = arr
+        h = C.c_void_p()
+        _check(lib.pp_init_batch(arr, len(self.cfgs), C.byref(h)), "pp_init_batch")
+        self.h = h
+        self.cells = [Cell(c, _handle=lib.pp_batch_cell(h, i), **kw) for i, c in enumerate(self.cfgs)]
+
+    def advance_period(self, n=1, stream=0):
+        _check(lib.pp_batch_advance_period(self.h, n, C.c_void_p(stream)), "pp_batch_advance_period")
+
+    def close(self):
+        if self.h:
+            for c in self.cells:
+                c.h = None
+            lib.pp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count():

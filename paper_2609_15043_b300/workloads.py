@@ -84,6 +84,7 @@ class CellConfig:
     te_ev: float = 3.0
     ti_ev: float = 0.026
     seed: int = 20260915
+    plain_fp64: int = 0            # 1: the plain FP64 particle form (comparison baseline)
     capacity_factor: float = 1.5
     sort_every_e: int = 4
     sort_every_i: int = 50
@@ -104,6 +105,28 @@ def cell100():
     return CellConfig(nr=256, nz=384, n_init=16_000_000, pressure_pa=10e-3 * _TORR,
                       dt=1.0 / (800 * 13.56e6), turn_r=[0.02, 0.035, 0.05, 0.065, 0.08],
                       winding=[1] * 5, power_control=1, p_target=100.0)
+
+
+def batch_cells(n_cells=32, seed=20260915):
+    """A batch of independent cells of mixed size: nr from {64, 80, ..., 192}
+    and nz = 1.5 nr (every nz is a multiple of 24, so the window and coil
+    planes lie on grid lines), macroparticles per species log-uniform in
+    [5e5, 8e6], controller target uniform in [20, 150] W, pressure uniform in
+    [5, 50] mTorr, 3 to 5 turns spread evenly over r in [0.02, 0.08] m.
+    Drawn with PCG64 from `seed`; cell i gets PIC seed `seed + i`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_cells):
+        nr = int(rng.choice(np.arange(64, 193, 16)))
+        n_init = int(round(math.exp(rng.uniform(math.log(5e5), math.log(8e6)))))
+        p_target = float(rng.uniform(20.0, 150.0))
+        p_mtorr = float(rng.uniform(5.0, 50.0))
+        nt = int(rng.integers(3, 6))
+        radii = [0.02 + 0.06 * k / (nt - 1) for k in range(nt)]
+        out.append(CellConfig(nr=nr, nz=3 * nr // 2, n_init=n_init, pressure_pa=p_mtorr * 1e-3 * _TORR,
+                              turn_r=radii, winding=[1] * nt, power_control=1, p_target=p_target,
+                              seed=seed + i))
+    return out
 
 
 WORKLOADS = {"small": small, "cell60": cell60, "cell100": cell100}

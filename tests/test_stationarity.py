@@ -1,0 +1,61 @@
+"""Host-side stationarity test over period records (no GPU)."""
+import numpy as np
+
+from paper_2609_15043_b300.stationarity import StationarityMonitor, StationarityCriteria
+
+
+def _rec(p_port, p_ind, p_cap, p_cu, x):
+    return dict(p_port=p_port, p_ind=p_ind, p_cap=p_cap, p_cu=p_cu, x_applied=np.asarray(x, complex))
+
+
+def _series(n, tau, noise, rng, target=60.0, bias=0.0):
+    out = []
+    for k in range(n):
+        a = 1.0 - np.exp(-k / tau)
+        p = target * a * (1 + noise * rng.standard_normal())
+        pc = 0.2 * (1 + noise * rng.standard_normal())
+        pcu = 0.05 * p
+        pind = p - pc - pcu + bias * p
+        x = np.array([3.0 * a + 0.1j, 2.9 * a, 2.8 * a, 2.7 * a, 100 * a, 90 * a, 80 * a]) * \
+            (1 + noise * rng.standard_normal())
+        out.append(_rec(p, pind, pc, pcu, x))
+    return out
+
+
+def test_transient_then_stationary():
+    rng = np.random.default_rng(1)
+    recs = _series(600, tau=40.0, noise=1e-3, rng=rng)
+    m = StationarityMonitor(3, p_target=60.0)
+    for r in recs:
+        m.update(r)
+    # the window must be past the transient: a(k) within 0.25 % of 1 needs k > 40 ln 400 ~ 240
+    assert m.stationary_at is not None
+    assert 200 <= m.stationary_at <= 400
+
+
+def test_never_stationary_with_power_imbalance():
+    rng = np.random.default_rng(2)
+    recs = _series(400, tau=5.0, noise=1e-4, rng=rng, bias=0.02)
+    m = StationarityMonitor(3, p_target=60.0)
+    assert not any(m.update(r) for r in recs)
+    assert m.last["bal"] > 0.005
+
+
+def test_never_stationary_off_target_or_drifting():
+    rng = np.random.default_rng(3)
+    recs = _series(300, tau=5.0, noise=1e-4, rng=rng, target=55.0)
+    m = StationarityMonitor(3, p_target=60.0)
+    assert not any(m.update(r) for r in recs)
+    # a slow ramp of 2 % over the window fails the half-window drift test
+    recs = [_rec(60 * (1 + 2e-4 * k), 60 * (1 + 2e-4 * k) * 0.95 - 0.2, 0.2, 60 * (1 + 2e-4 * k) * 0.05,
+                 np.ones(7)) for k in range(200)]
+    m = StationarityMonitor(3, p_target=None)
+    assert not any(m.update(r) for r in recs)
+    assert m.last["drift_p"] > 0.005
+
+
+def test_window_must_fill_first():
+    rec = _rec(60.0, 59.8 - 3.0, 0.2, 3.0, np.ones(7))
+    m = StationarityMonitor(3, p_target=60.0, criteria=StationarityCriteria(window=10))
+    flags = [m.update(rec) for _ in range(12)]
+    assert flags[:9] == [False] * 9 and flags[9] and m.stationary_at == 9
