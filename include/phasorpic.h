@@ -123,6 +123,12 @@ typedef struct pp_period_record {
     int64_t n_live[PP_NSPECIES];
     int64_t coll[PP_NSPECIES][3];    /* e: elastic, excitation, ionisation; i: cx, isotropic, - */
     int64_t absorbed, created, nu_violations;
+    /* learned circuit proposal (pp_ml_configure): error of the prediction made
+       for this period against its measured loads (scaled norm of Eq. t7error),
+       the acceptance threshold (twice the trailing noise), whether the
+       prediction for the next period was applied, whether a model is active */
+    double ml_err, ml_tau;
+    int32_t ml_used, ml_active;
 } pp_period_record;
 
 typedef struct pp_cell pp_cell;
@@ -188,6 +194,57 @@ int pp_batch_size(pp_batch* batch);
 pp_cell* pp_batch_cell(pp_batch* batch, int i);     /* NULL if i is out of range */
 int pp_batch_advance_period(pp_batch* batch, int n_periods, void* stream);
 int pp_batch_destroy(pp_batch* batch);
+
+/*
+ * Learned circuit proposal (a BF16 MLP on the tensor cores).  Features of a
+ * period (2(2N+1) + 192 numbers): Re and Im of the applied circuit state,
+ * then log10(max(n_e, 1e10)) in 32 radial and 32 axial bins of the plasma
+ * (electron count x weight over the bin volume), T_e = (m_e/3e)<|v|^2> (eV) in
+ * the same bins, and the current amplitude sqrt(J_c^2 + J_s^2) of the
+ * period's harmonics averaged with the node weighting volumes.  Outputs (4N):
+ * Re, Im V_p,k for every k, then Re, Im I_cap,k: the loads of the next
+ * period.  Network: inputs standardised ((f - mu_in)/sig_in) and rounded to
+ * BF16, three hidden layers of 256 (ReLU, BF16 activations), a linear layer of
+ * 32, FP32 accumulation, outputs de-standardised (y sig_out + mu_out).
+ */
+typedef struct pp_mlp {
+    int32_t n_in;                    /* features used (2(2N+1) + 192 <= 256) */
+    int32_t n_out;                   /* outputs used (4N <= 32) */
+    const uint16_t* w[4];            /* BF16 bit patterns, [out][in]: 256x256 (x3), 32x256 */
+    const float* b[4];               /* biases: 256 (x3), 32 */
+    const double* mu_in;             /* n_in */
+    const double* sig_in;            /* n_in */
+    const double* mu_out;            /* n_out */
+    const double* sig_out;           /* n_out */
+} pp_mlp;
+
+/* pp_mlp_forward -- the network on `rows` feature rows (host, rows x n_in,
+ * row-major) into out (host, rows x n_out); 128 rows per CTA.  Synchronous;
+ * PP_E_ARG on bad sizes, PP_E_TIMEOUT if a bounded wait on the tensor cores
+ * expired. */
+int pp_mlp_forward(const pp_mlp* m, const double* feats, int rows, double* out);
+
+/*
+ * pp_ml_configure -- collect != 0 computes the features at every period end
+ * (readable with pp_get_ml_features).  With m != NULL the proposal is active:
+ * at each period end the network predicts the next period's loads; the
+ * prediction made for this period is compared with the measured loads, and
+ * when its error is within twice the RMS period-to-period change of the
+ * measured loads over the last 20 periods, the next state is relaxed with
+ * factor alpha_ml toward the network solution of the predicted loads
+ * instead of the measured ones (Eq. relaxation otherwise).  The weights are
+ * copied; m == NULL deactivates.  Synchronises the device.
+ */
+int pp_ml_configure(pp_cell* cell, const pp_mlp* m, double alpha_ml, int collect);
+
+/* pp_get_ml_features -- the feature vector of the last period end (or of the
+ * last pp_ml_features_now); *n = its length; PP_E_ARG if none exists or cap
+ * is too small.  Synchronises `stream`. */
+int pp_get_ml_features(pp_cell* cell, double* out, int cap, int* n, void* stream);
+
+/* pp_ml_features_now -- computes the features from the current particles,
+ * harmonic accumulators and applied state (enqueued on `stream`). */
+int pp_ml_features_now(pp_cell* cell, void* stream);
 
 /* pp_get_particles64 -- as pp_get_particles with the state in double (exact
  * for the plain FP64 form, widened from float otherwise). */

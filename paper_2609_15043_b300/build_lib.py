@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasorpic.so")
-SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_period.cu"]
+SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu", "pp_period.cu"]
 
 
 def nvcc():
@@ -34,7 +34,8 @@ def build(force=False, verbose=False):
     if not force and not needs_build():
         return LIB
     cmd = [nvcc(), "-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-           "--fmad=false", "-Xcompiler", "-fPIC", "-shared", "-o", LIB + ".tmp"]
+           "--fmad=false", "-Xcompiler", "-fPIC", "-shared", "-Xlinker", "-z", "-Xlinker", "defs",
+           "-o", LIB + ".tmp"]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     cmd += [os.path.join(CSRC, f) for f in SOURCES] + ["-lcudart"]

@@ -602,6 +602,7 @@ int pp_prime(pp_cell* h, void* stream) {
 
 }  // extern "C"
 
+namespace pp {
 static int pp_prime_on(Cell* c, cudaStream_t st) {
     if (c->fp64)
         cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * c->nnodes, st);
@@ -613,6 +614,7 @@ static int pp_prime_on(Cell* c, cudaStream_t st) {
     c->primed = true;
     return cuda_check(cudaGetLastError(), "pp_prime");
 }
+}  // namespace pp
 
 extern "C" {
 

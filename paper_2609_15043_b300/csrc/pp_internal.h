@@ -89,6 +89,12 @@ struct DevState {
     long long period;
     int has_record;
     pp_period_record rec;
+    // learned proposal gate: prediction for this period, previous measured
+    // loads, ring of the last period-to-period changes (scaled norm)
+    double ml_pred[32];
+    double ml_prev[32];
+    double ml_ring[20];
+    int ml_has_pred, ml_has_prev, ml_n_noise, ml_ring_pos;
     // Poisson refinement bookkeeping (per sweep: max|r|, max term scale)
     unsigned long long pnorm[2 * 16];
     int pdone;
@@ -224,6 +230,20 @@ struct Cell {
 
     bool in_batch = false;                 // owned by a pp_batch (destroyed with it)
 
+    // learned proposal: features at period ends, optional model
+    bool ml_collect = false;
+    bool ml_model = false;
+    double alpha_ml = 1.0;
+    int ml_n_in = 0, ml_n_out = 0;
+    double* d_ml_feat = nullptr;           // n_in
+    double* d_ml_pred = nullptr;           // 32
+    double* d_ml_acc = nullptr;            // summary accumulators (8 x 32)
+    unsigned long long* d_ml_cnt = nullptr;// electron counts (2 x 32)
+    uint16_t* d_ml_w[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* d_ml_b[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* d_ml_norm = nullptr;           // mu_in, sig_in, mu_out, sig_out (256 + 256 + 32 + 32)
+    bool ml_have_features = false;
+
     std::vector<void*> allocs;
     template <typename T>
     T* alloc(size_t n) {
@@ -264,5 +284,8 @@ void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, con
 void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
                          cudaStream_t st);
 void launch_compose(Cell* c, bool from_new, cudaStream_t st);
+void ml_features(Cell* c, cudaStream_t st);          // summaries + feature vector
+void ml_predict(Cell* c, cudaStream_t st);           // network on the feature vector
+int ml_configure(Cell* c, const pp_mlp* m, double alpha_ml, int collect);
 
 }  // namespace pp

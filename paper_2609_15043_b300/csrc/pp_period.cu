@@ -30,7 +30,22 @@ struct PeriodArgs {
     int power_control;
     double p_target, gamma, n_trend, eps_p, alpha_v, f_step, v_min, v_max, alpha, phase_g;
     const int* nslot;
+    int ml_model;             // a proposal network is active
+    double alpha_ml;
+    const double* ml_pred;    // its prediction of the next period's loads (4N)
 };
+
+// Eq. t7error on load vectors (V_p entries over v_scale, I_cap entries over i_scale)
+__device__ double scaled_error(const double* y, const double* ref, int N, double vs, double is) {
+    double num = 0, den = 0;
+    for (int q = 0; q < 4 * N; ++q) {
+        double s = q < 2 * N ? vs : is;
+        double d = (y[q] - ref[q]) / s, r = ref[q] / s;
+        num += d * d;
+        den += r * r;
+    }
+    return sqrt(num) / fmax(sqrt(den), 1e-300);
+}
 
 __global__ void period_circuit(PeriodArgs a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -107,6 +122,43 @@ __global__ void period_circuit(PeriodArgs a) {
     rec.n_live[0] = st->live[0];
     rec.n_live[1] = st->live[1];
 
+    // learned proposal gate: the change of the measured loads since the last
+    // period joins the trailing noise ring; the prediction made for this
+    // period is judged against twice the ring's RMS
+    double meas[4 * PP_MAX_TURNS];
+    for (int k = 0; k < N; ++k) {
+        meas[2 * k] = vp[k].r;
+        meas[2 * k + 1] = vp[k].i;
+        meas[2 * N + 2 * k] = icap[k].r;
+        meas[2 * N + 2 * k + 1] = icap[k].i;
+    }
+    const double v_scale = fmax(fabs(st->vg_amp), 1e-300);
+    const double i_scale = fmax(sqrt(cabs2(x[0])), 1e-300);
+    double ml_err = nan(""), ml_tau = nan("");
+    bool use_pred = false;
+    if (st->ml_has_prev) {
+        st->ml_ring[st->ml_ring_pos] = scaled_error(meas, st->ml_prev, N, v_scale, i_scale);
+        st->ml_ring_pos = (st->ml_ring_pos + 1) % 20;
+        if (st->ml_n_noise < 20) st->ml_n_noise += 1;
+    }
+    if (a.ml_model && st->ml_has_pred && st->ml_n_noise >= 20) {
+        ml_err = scaled_error(st->ml_pred, meas, N, v_scale, i_scale);
+        double ss = 0;
+        for (int q = 0; q < 20; ++q) ss += st->ml_ring[q] * st->ml_ring[q];
+        ml_tau = 2.0 * sqrt(ss / 20.0);
+        use_pred = ml_err <= ml_tau;
+    }
+    for (int q = 0; q < 4 * N; ++q) st->ml_prev[q] = meas[q];
+    st->ml_has_prev = 1;
+    if (a.ml_model) {
+        for (int q = 0; q < 4 * N; ++q) st->ml_pred[q] = a.ml_pred[q];
+        st->ml_has_pred = 1;
+    }
+    rec.ml_err = ml_err;
+    rec.ml_tau = ml_tau;
+    rec.ml_used = (use_pred && accepted) ? 1 : 0;
+    rec.ml_active = a.ml_model;
+
     Cx vg = Cx{st->vg_amp * cos(a.phase_g), st->vg_amp * sin(a.phase_g)};
     if (accepted) {
         if (a.power_control) {   // Eqs. pfilter, ptrend, pcontrol + limiter + bounds
@@ -126,17 +178,25 @@ __global__ void period_circuit(PeriodArgs a) {
             vg = Cx{vn * cos(a.phase_g), vn * sin(a.phase_g)};
         }
         // x_target = A^-1 (V_g, I_cap, V_p) (Eqs. blockmatrix, target)
+        // with an accepted proposal the target uses the predicted loads of the
+        // next period and the relaxation factor alpha_ml
         Cx b[2 * PP_MAX_TURNS + 1];
         b[0] = vg;
         for (int k = 0; k < N; ++k) {
-            b[1 + k] = icap[k];
-            b[1 + N + k] = vp[k];
+            if (use_pred) {
+                b[1 + k] = Cx{a.ml_pred[2 * N + 2 * k], a.ml_pred[2 * N + 2 * k + 1]};
+                b[1 + N + k] = Cx{a.ml_pred[2 * k], a.ml_pred[2 * k + 1]};
+            } else {
+                b[1 + k] = icap[k];
+                b[1 + N + k] = vp[k];
+            }
         }
+        const double alpha = use_pred ? a.alpha_ml : a.alpha;
         for (int r = 0; r < NX; ++r) {
             Cx s = Cx{0, 0};
             for (int q = 0; q < NX; ++q)
                 s = cadd(s, cmul(Cx{a.Ainv[2 * (r * NX + q)], a.Ainv[2 * (r * NX + q) + 1]}, b[q]));
-            x[r] = cadd(cscale(x[r], 1.0 - a.alpha), cscale(s, a.alpha));   // Eq. relaxation
+            x[r] = cadd(cscale(x[r], 1.0 - alpha), cscale(s, alpha));   // Eq. relaxation
         }
         for (int q = 0; q < NX; ++q) {
             st->x[2 * q] = x[q].r;
@@ -191,6 +251,10 @@ __global__ void period_circuit(PeriodArgs a) {
 
 void period_end(Cell* c, cudaStream_t st) {
     double scale = kMu0 * c->omega;
+    // features of the completed period (electrons and current harmonics as
+    // they stand) and, with a model, its prediction of the next period's loads
+    if (c->ml_collect) ml_features(c, st);
+    if (c->ml_model) ml_predict(c, st);
     // Eq. helmholtz_two_real: L E_c^p = mu0 w J_s, L E_ss^p = mu0 w J_c
     helmholtz_solve_dev(c, c->d_Js, c->d_Ecp_new, scale, st);
     helmholtz_solve_dev(c, c->d_Jc, c->d_Essp_new, scale, st);
@@ -224,6 +288,9 @@ void period_end(Cell* c, cudaStream_t st) {
     a.alpha = c->cfg.alpha;
     a.phase_g = c->cfg.phase_g;
     a.nslot = c->d_nslot;
+    a.ml_model = c->ml_model ? 1 : 0;
+    a.alpha_ml = c->alpha_ml;
+    a.ml_pred = c->d_ml_pred;
     period_circuit<<<1, 32, 0, st>>>(a);
     count_launch();
     launch_compose(c, true, st);

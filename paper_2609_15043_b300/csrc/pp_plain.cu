@@ -36,7 +36,7 @@ __device__ __forceinline__ void add4(T* g, int NR, int iz, int ir, T v0, T v1, T
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) push_plain(PlainArgs<T> a) {
+__global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
     __shared__ double s_f[8][2];
     __shared__ unsigned s_c[8][10];
     const int n0 = a.nslot[0], n1 = a.nslot[1];

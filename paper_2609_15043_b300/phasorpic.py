@@ -35,7 +35,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
            "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
            "pp_poisson_solve_noalloc", "pp_checkpoint", "pp_restore", "pp_get_particles64",
-           "pp_init_batch", "pp_batch_size", "pp_batch_cell", "pp_batch_advance_period", "pp_batch_destroy"]
+           "pp_init_batch", "pp_batch_size", "pp_batch_cell", "pp_batch_advance_period", "pp_batch_destroy",
+           "pp_mlp_forward", "pp_ml_configure", "pp_get_ml_features", "pp_ml_features_now"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -87,6 +88,7 @@ class PPRecord(C.Structure):
         ("n_live", C.c_int64 * NSPECIES),
         ("coll", (C.c_int64 * 3) * NSPECIES),
         ("absorbed", C.c_int64), ("created", C.c_int64), ("nu_violations", C.c_int64),
+        ("ml_err", C.c_double), ("ml_tau", C.c_double), ("ml_used", C.c_int32), ("ml_active", C.c_int32),
     ]
 
 
@@ -127,6 +129,10 @@ def _load():
         "pp_checkpoint": (I, [V, V, P(C.c_uint64)]),
         "pp_get_particles64": (I, [V, I, C.c_int64, P(C.c_int64), V, V, V, V, V, V, V, V]),
         "pp_init_batch": (I, [V, I, P(V)]),
+        "pp_mlp_forward": (I, [V, V, I, V]),
+        "pp_ml_configure": (I, [V, V, D, I]),
+        "pp_get_ml_features": (I, [V, V, I, P(I), V]),
+        "pp_ml_features_now": (I, [V, V]),
         "pp_batch_size": (I, [V]),
         "pp_batch_cell": (V, [V, I]),
         "pp_batch_advance_period": (I, [V, I, V]),
@@ -193,6 +199,44 @@ def make_config(cfg, capacity=None, weight=None, poisson_max_iter=4, poisson_tol
     c.poisson_tol = poisson_tol
     c.plain_fp64 = int(getattr(cfg, "plain_fp64", 0))
     return c
+
+
+class PPMlp(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_out", C.c_int32), ("w", C.c_void_p * 4), ("b", C.c_void_p * 4),
+                ("mu_in", C.c_void_p), ("sig_in", C.c_void_p), ("mu_out", C.c_void_p), ("sig_out", C.c_void_p)]
+
+
+def make_mlp(params):
+    """pp_mlp view of a parameter dict (w: 4 uint16 BF16 arrays [out][in],
+    b: 4 float32 arrays, mu_in, sig_in, mu_out, sig_out); the arrays are kept
+    alive on the returned object."""
+    keep = dict(w=[np.ascontiguousarray(x, np.uint16) for x in params["w"]],
+                b=[np.ascontiguousarray(x, np.float32) for x in params["b"]],
+                **{k: np.ascontiguousarray(params[k], np.float64) for k in ("mu_in", "sig_in", "mu_out", "sig_out")})
+    shapes = [(256, 256)] * 3 + [(32, 256)]
+    for l in range(4):
+        if keep["w"][l].shape != shapes[l] or keep["b"][l].shape != (shapes[l][0],):
+            raise ValueError("MLP layer %d must be %s" % (l, shapes[l]))
+    m = PPMlp()
+    m.n_in, m.n_out = len(keep["mu_in"]), len(keep["mu_out"])
+    for l in range(4):
+        m.w[l] = keep["w"][l].ctypes.data
+        m.b[l] = keep["b"][l].ctypes.data
+    for k in ("mu_in", "sig_in", "mu_out", "sig_out"):
+        setattr(m, k, keep[k].ctypes.data)
+    m._keep = keep
+    return m
+
+
+def mlp_forward(params, feats):
+    """pp_mlp_forward: the network on rows of raw features (tensor cores)."""
+    m = make_mlp(params)
+    f = np.ascontiguousarray(feats, np.float64)
+    if f.ndim == 1:
+        f = f[None, :]
+    out = np.zeros((f.shape[0], m.n_out))
+    _check(lib.pp_mlp_forward(C.byref(m), _ptr(f), f.shape[0], _ptr(out)), "pp_mlp_forward")
+    return out
 
 
 class Cell:
@@ -371,6 +415,24 @@ def _restore(self, image):
     _check(lib.pp_restore(self.h, _ptr(buf), C.c_uint64(buf.size)), "pp_restore")
 
 
+def _ml_configure(self, params=None, alpha_ml=1.0, collect=True):
+    m = make_mlp(params) if params is not None else None
+    self._ml = m
+    _check(lib.pp_ml_configure(self.h, C.byref(m) if m is not None else None, float(alpha_ml), int(bool(collect))),
+           "pp_ml_configure")
+
+
+def _ml_features(self, now=False, stream=0):
+    if now:
+        _check(lib.pp_ml_features_now(self.h, C.c_void_p(stream)), "pp_ml_features_now")
+    out = np.zeros(256)
+    n = C.c_int()
+    _check(lib.pp_get_ml_features(self.h, _ptr(out), 256, C.byref(n), C.c_void_p(stream)), "pp_get_ml_features")
+    return out[:n.value]
+
+
+Cell.ml_configure = _ml_configure
+Cell.ml_features = _ml_features
 Cell.checkpoint = _checkpoint
 Cell.restore = _restore
 Cell.phase_times = _phase_times
@@ -419,4 +481,5 @@ def record_dict(r, n):
                 p_cap_ph=r.p_cap_ph, p_cu=r.p_cu, p_es=r.p_es, eps_bal=r.eps_bal,
                 r_kcl=r.r_kcl, r_kvl=r.r_kvl, particle_steps=r.particle_steps,
                 n_live=list(r.n_live), coll=np.array([list(r.coll[0]), list(r.coll[1])]),
-                absorbed=r.absorbed, created=r.created, nu_violations=r.nu_violations)
+                absorbed=r.absorbed, created=r.created, nu_violations=r.nu_violations,
+                ml_err=r.ml_err, ml_tau=r.ml_tau, ml_used=bool(r.ml_used), ml_active=bool(r.ml_active))
