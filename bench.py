@@ -53,6 +53,10 @@ def parse():
                     help="run each form from the same initial state until the stationarity test passes")
     ap.add_argument("--max-periods", type=int, default=600, help="cap of the time-to-stationary runs")
     ap.add_argument("--trace-out", default=None, help="write the per-period records of those runs (JSON)")
+    ap.add_argument("--ml-weights", default=None,
+                    help="proposal network (mlp_train output): adds a fused-FP32 run with the proposal active")
+    ap.add_argument("--alpha-ml", type=float, default=1.0)
+    ap.add_argument("--forms", default="fused,fp64", help="time-to-stationary runs (fused, fp64, fused_ml)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only prime the cell and run this many PIC steps, untimed (a short target for ncu)")
     return ap.parse_args()
@@ -456,11 +460,17 @@ def run_stationary(args, cfg, local):
     from paper_2609_15043_b300 import phasorpic as pp, workloads
     from paper_2609_15043_b300.stationarity import StationarityMonitor
     out, traces = {}, {}
-    for form in ("fused", "fp64"):
+    forms = [f for f in args.forms.split(",") if f]
+    if args.ml_weights and "fused_ml" not in forms:
+        forms.append("fused_ml")
+    for form in forms:
         c = cfg.replace(plain_fp64=1 if form == "fp64" else 0)
         cell = pp.Cell(c)
         for sp in (0, 1):
             cell.set_particles(sp, workloads.population(c, sp))
+        if form == "fused_ml":
+            from paper_2609_15043_b300.mlp_train import load_params
+            cell.ml_configure(load_params(args.ml_weights), alpha_ml=args.alpha_ml)
         sh = torch.cuda.current_stream().cuda_stream
         mon = StationarityMonitor(len(c.turn_r), c.p_target if c.power_control else None)
         torch.cuda.synchronize()
@@ -472,20 +482,22 @@ def run_stationary(args, cfg, local):
             cell.advance_period(1, sh)
             rec = cell.turn_phasors(sh)
             trace.append({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in rec.items()
-                          if k in ("p_port", "p_ind", "p_cap", "p_cu", "eps_bal", "vg", "n_live", "accepted")})
+                          if k in ("p_port", "p_ind", "p_cap", "p_cu", "eps_bal", "vg", "n_live", "accepted",
+                                   "ml_err", "ml_tau", "ml_used")})
             if mon.update(rec):
                 break
         wall = time.perf_counter() - t0
         stationary = mon.stationary_at is not None
         out[form] = {"stationary": stationary, "periods": periods, "wall_s": wall,
                      "ms_per_period": 1e3 * wall / periods, "last_window": mon.last,
-                     "status": cell.status()}
+                     "status": cell.status(),
+                     "proposals_used": sum(1 for r in trace if r.get("ml_used"))}
         traces[form] = trace
         cell.close()
         del cell
         torch.cuda.empty_cache()
-    f, d = out["fused"], out["fp64"]
-    ratio = (d["wall_s"] / f["wall_s"]) if f["stationary"] and d["stationary"] else None
+    f, d = out.get("fused"), out.get("fp64")
+    ratio = (d["wall_s"] / f["wall_s"]) if f and d and f["stationary"] and d["stationary"] else None
     line = {"metric": "time to a stationary state, fused FP32 vs plain FP64 PIC, 1 B300",
             "config": {"workload": workload_desc(cfg, args.workload), "max_periods": args.max_periods,
                        "criteria": "trailing 100 periods: |P_port-P_target|<=1%, balance<=0.5%, "

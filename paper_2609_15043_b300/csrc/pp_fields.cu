@@ -54,6 +54,45 @@ __global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __r
     }
 }
 
+// Row-parallel product C = A V of a rows x M matrix with an M x M matrix: one
+// block per row of A (staged in shared memory), each thread a set of output
+// columns with four partial sums; V is read coalesced along its rows from L2.
+// With `check`, the block first takes the convergence decision of the sweep
+// from the residual norms (identical in every block).
+template <bool check>
+__global__ void __launch_bounds__(128) gemm_rows(const float* __restrict__ A, const float* __restrict__ V,
+                                                 float* __restrict__ C, int M, DevState* st, int sweep, double tol,
+                                                 int* done) {
+    if (*done) return;
+    if (check) {
+        double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
+        double sn = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
+        double rel = (sn > 0) ? rn / sn : 0.0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->prel = rel;
+            st->piters = sweep;
+            if (rel <= tol) *done = 1;
+        }
+        if (rel <= tol) return;
+    }
+    extern __shared__ float arow[];
+    const float* a = A + (size_t)blockIdx.x * M;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) arow[k] = a[k];
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int k = 0;
+        for (; k + 3 < M; k += 4) {
+            s0 += arow[k] * V[(size_t)k * M + m];
+            s1 += arow[k + 1] * V[(size_t)(k + 1) * M + m];
+            s2 += arow[k + 2] * V[(size_t)(k + 2) * M + m];
+            s3 += arow[k + 3] * V[(size_t)(k + 3) * M + m];
+        }
+        for (; k < M; ++k) s0 += arow[k] * V[(size_t)k * M + m];
+        C[(size_t)blockIdx.x * M + m] = (s0 + s1) + (s2 + s3);
+    }
+}
+
 // First product of a refinement sweep, preceded by the convergence decision
 // on the residual of this sweep: every block reads the same norms and either
 // all return (converged) or all compute.
@@ -344,6 +383,37 @@ __global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn
     if (t < K) phi[tn_node[t]] = turn_target(st, ext, tn_k[t], nt, cs, sn);
 }
 
+// phi += d0 + Z sigma as poisson_update_cap, with the K corrections of an
+// unknown read as contiguous float4s (Zt: unknown-major, K padded to Kp)
+__global__ void poisson_update_zt(double* phi, const float* d0, const float* __restrict__ Zt, const double* Ginv,
+                                  const int* tn_int, int K, int Kp, int rows, int M, int NR,
+                                  const signed char* turn_mask, const int* done) {
+    if (*done) return;
+    __shared__ double s_r[kMaxCapNodes];
+    __shared__ double s_sig[kMaxCapNodes + 4];
+    for (int q = threadIdx.x; q < K; q += blockDim.x) s_r[q] = -(double)d0[tn_int[q]];
+    __syncthreads();
+    for (int q = threadIdx.x; q < Kp; q += blockDim.x) {
+        double sg = 0;
+        if (q < K)
+            for (int u = 0; u < K; ++u) sg += Ginv[q * K + u] * s_r[u];
+        s_sig[q] = sg;
+    }
+    __syncthreads();
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * M) return;
+    int n = (idx / M + 1) * NR + idx % M;
+    if (turn_mask[n] >= 0) return;
+    double d = (double)d0[idx];
+    const float4* z = reinterpret_cast<const float4*>(Zt + (size_t)idx * Kp);
+    for (int t = 0; t < Kp / 4; ++t) {
+        float4 v = z[t];
+        d += s_sig[4 * t] * (double)v.x + s_sig[4 * t + 1] * (double)v.y + s_sig[4 * t + 2] * (double)v.z +
+             s_sig[4 * t + 3] * (double)v.w;
+    }
+    phi[n] += d;
+}
+
 // phi += d0 + Z sigma with sigma = G^-1 (-d0_T) computed by every block
 // (the turn nodes already hold their targets)
 __global__ void poisson_update_cap(double* phi, const float* d0, const float* Z, const double* Ginv,
@@ -621,7 +691,6 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     const int K = c->ntn;
     poisson_set_turns<<<(K + 63) / 64, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K, dst, ext, c->nturns, cs, sn);
     count_launch();
-    dim3 gblk(32, 8), ggrd((M + 31) / 32, (rows + 31) / 32);
     for (int it = 0; it <= maxit; ++it) {
         a.norm = &dst->pnorm[2 * it];
         poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
@@ -632,11 +701,12 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)
-        gemm_check<<<ggrd, gblk, 0, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, rows, M, M, dst, it, c->cfg.poisson_tol, done);
+        gemm_rows<true><<<rows, 128, sizeof(float) * M, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, M, dst, it,
+                                                                 c->cfg.poisson_tol, done);
         launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
-        gemm_rm<float><<<ggrd, gblk, 0, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, M, done);
-        poisson_update_cap<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Z, c->d_Ginv, c->d_tn_int, K,
-                                                                rows, M, c->NR, c->d_turn_mask, done);
+        gemm_rows<false><<<rows, 128, sizeof(float) * M, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, M, dst, it, 0.0, done);
+        poisson_update_zt<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
+                                                               c->ntn_pad, rows, M, c->NR, c->d_turn_mask, done);
         count_launch(4);
     }
     return 0;

@@ -193,6 +193,8 @@ struct Cell {
     double* d_sigma = nullptr;
     double* d_Ginv = nullptr;               // ntn x ntn
     float* d_Z = nullptr;                   // ntn x (rows*M)
+    float* d_Zt = nullptr;                  // (rows*M) x ntn_pad: the same columns interleaved per unknown
+    int ntn_pad = 0;                        // ntn rounded up to a multiple of 4
     // Helmholtz FP64
     SepSolver<double> hs;
     double* d_hstage = nullptr;             // 2 x interior Helmholtz staging

@@ -694,6 +694,13 @@ int setup_cell(Cell* c) {
             for (int u = 0; u < K; ++u) G[(size_t)t * K + u] = Zh[(size_t)u * nint + tn_int[t]];
         if (!invert(G, K)) return fail("capacitance matrix is singular");
         c->d_Ginv = upload<double>(c, G);
+        // interleaved copy: the K corrections of one unknown are contiguous
+        int Kp = (K + 3) / 4 * 4;
+        std::vector<double> Zt(nint * (size_t)Kp, 0.0);
+        for (size_t q = 0; q < nint; ++q)
+            for (int t = 0; t < K; ++t) Zt[q * Kp + t] = Zh[(size_t)t * nint + q];
+        c->ntn_pad = Kp;
+        c->d_Zt = upload<float>(c, Zt);
     }
     cudaError_t err = cudaDeviceSynchronize();
     if (err != cudaSuccess) {

@@ -1,0 +1,31 @@
+"""The offline trainer of the proposal network (numpy, CPU): it fits a
+learnable synthetic map, and its exported BF16 model evaluated by the
+oracle's forward pass reproduces the map."""
+import numpy as np
+
+from oracle import mlp
+
+
+def test_trainer_fits_a_smooth_map(tmp_path):
+    from paper_2609_15043_b300 import mlp_train
+    rng = np.random.default_rng(0)
+    n_in, n_out, n = 206, 12, 3000
+    X = rng.standard_normal((n, n_in)) * rng.uniform(0.5, 3.0, n_in) + rng.uniform(-5, 5, n_in)
+    A = rng.standard_normal((n_in, n_out)) / np.sqrt(n_in)
+    Y = np.tanh(((X - X.mean(0)) / X.std(0)) @ A) * 40.0 + 7.0
+    np.savez(tmp_path / "pairs.npz", X=X, Y=Y, n_turns=3, cells=1, periods=n)
+
+    class A_:
+        pairs = str(tmp_path / "pairs.npz")
+        out = str(tmp_path / "w.npz")
+        epochs = 40
+        batch = 128
+        lr = 2e-3
+        seed = 1
+    mlp_train.train(A_)
+    p = mlp_train.load_params(A_.out)
+    assert [w.shape for w in p["w"]] == [(256, 256)] * 3 + [(32, 256)]
+    pred = np.stack([mlp.forward(p, X[i]) for i in range(0, n, 10)])
+    ref = Y[::10]
+    rel = np.sqrt(np.mean((pred - ref) ** 2) / np.var(ref))
+    assert rel < 0.2
