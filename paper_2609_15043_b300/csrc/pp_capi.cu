@@ -85,14 +85,7 @@ static void one_step(Cell* c, cudaStream_t st) {
     int64_t s = c->s;
     double th = theta(c, s), th1 = theta(c, s + 1);
     phase_mark(c, PH_OTHER, true, st);
-    if (c->fp64) {
-        cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * c->nnodes, st);
-        cudaMemsetAsync(c->d_jm64, 0, sizeof(double) * c->nnodes, st);
-    } else {
-        cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
-        cudaMemsetAsync(c->d_jm, 0, sizeof(float) * c->nnodes, st);
-    }
-    launch_field_prep(c, std::cos(th), std::sin(th), st);
+    launch_field_prep(c, std::cos(th), std::sin(th), st);     // also clears rho and jm
     phase_mark(c, PH_OTHER, false, st);
     phase_mark(c, PH_PUSH, true, st);
     if (c->fp64)

@@ -63,6 +63,7 @@ template <bool check>
 __global__ void __launch_bounds__(128) gemm_rows(const float* __restrict__ A, const float* __restrict__ V,
                                                  float* __restrict__ C, int M, DevState* st, int sweep, double tol,
                                                  int* done) {
+    pdl_wait();
     if (*done) return;
     if (check) {
         double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
@@ -196,6 +197,7 @@ template <int EPT>
 __global__ void __launch_bounds__(256) pcr_solve(const float* __restrict__ f, float* __restrict__ x,
                                                  const float* __restrict__ al, const float* __restrict__ ga,
                                                  const float* __restrict__ ib, int rows, int M, int L, const int* skip) {
+    pdl_wait();
     if (skip && *skip) return;
     __shared__ float d[2][256 * EPT];
     const int m = blockIdx.x;
@@ -241,11 +243,11 @@ __global__ void __launch_bounds__(256) pcr_solve(const float* __restrict__ f, fl
 static void launch_pcr(const Cell* c, const float* f, float* x, cudaStream_t st, const int* skip) {
     int rows = c->ps.rows, M = c->ps.M, L = c->pcr_levels;
     if (rows <= 256)
-        pcr_solve<1><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        launch_pdl(pcr_solve<1>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
     else if (rows <= 512)
-        pcr_solve<2><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        launch_pdl(pcr_solve<2>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
     else
-        pcr_solve<4><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        launch_pdl(pcr_solve<4>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
 }
 
 template <typename T>
@@ -303,6 +305,7 @@ struct PoisArgs {
 // capacitance step imposes their values).  The relative residual is
 // max|r| / max(|b| + sum |A_ij phi_j|) (a componentwise scale).
 __global__ void poisson_residual(PoisArgs a) {
+    pdl_wait();
     if (*a.done) return;
     int rows = a.NZ - 2;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,6 +348,7 @@ __global__ void poisson_residual(PoisArgs a) {
 
 // decides convergence from the norms of this sweep (runs before the solve)
 __global__ void poisson_check(DevState* st, int sweep, double tol, int* done, int final_sweep) {
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (*done) return;
     double r = __longlong_as_double((long long)st->pnorm[2 * sweep]);
@@ -377,9 +381,13 @@ __global__ void poisson_cap(const DevState* st, const double* ext, const double*
 
 // the turn nodes take their Dirichlet values before the sweeps, so every
 // later correction there is zero and no kernel of the solve writes them
-__global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn_k, int K, const DevState* st,
+__global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn_k, int K, DevState* st,
                                   const double* ext, int nt, double cs, double sn) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // fresh refinement bookkeeping for this solve
+    if (t < 2 * 16) st->pnorm[t] = 0ull;
+    if (t == 0) st->pdone = 0;
     if (t < K) phi[tn_node[t]] = turn_target(st, ext, tn_k[t], nt, cs, sn);
 }
 
@@ -388,6 +396,7 @@ __global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn
 __global__ void poisson_update_zt(double* phi, const float* d0, const float* __restrict__ Zt, const double* Ginv,
                                   const int* tn_int, int K, int Kp, int rows, int M, int NR,
                                   const signed char* turn_mask, const int* done) {
+    pdl_wait();
     if (*done) return;
     __shared__ double s_r[kMaxCapNodes];
     __shared__ double s_sig[kMaxCapNodes + 4];
@@ -463,11 +472,15 @@ __global__ void poisson_update(double* phi, const float* d0, const float* Z, con
 // per plasma cell 5 float4 (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10, 11)
 template <typename T>
 __global__ void field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
-                           const double* __restrict__ Ess, const double* __restrict__ B, T* F,
+                           const double* __restrict__ Ess, const double* __restrict__ B, T* F, T* rho, T* jm,
                            int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
                            double sn, int magnetic) {
+    pdl_wait();
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (i_win + 1) * NR) return;
+    // the step's deposits land on node rows 0..i_win only: clear them here
+    rho[n] = T(0);
+    jm[n] = T(0);
     int i = n / NR, j = n % NR;
     double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
     double Er;
@@ -496,6 +509,7 @@ __global__ void field_prep(const double* __restrict__ phi, const double* __restr
 __global__ void turn_sample(DevState* st, const double* phi, const int* ft, const int* fnb, const int* fk,
                             const double* fc, int nfaces, int nt, double cs, double sn, double two_over_n,
                             double inv_n, int n_rf) {
+    pdl_wait();
     __shared__ double q[PP_MAX_TURNS];
     if (threadIdx.x < PP_MAX_TURNS) q[threadIdx.x] = 0;
     __syncthreads();
@@ -529,6 +543,7 @@ __global__ void turn_sample(DevState* st, const double* phi, const int* ft, cons
 template <typename T>
 __global__ void accumulate_nodes(const T* jm, const double* vol, double* Jc, double* Js, double* Jcc,
                                  double* Jsc, int nn, double wc, double ws) {
+    pdl_wait();
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     double J = (double)jm[n] / vol[n];
@@ -628,7 +643,7 @@ void launch_compose(Cell* c, bool from_new, cudaStream_t st) {
 
 // ---------------------------------------------------------------- launchers
 void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
-    turn_sample<<<1, 256, 0, st>>>(c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
+    launch_pdl(turn_sample, 1, 256, 0, st, c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
                                    c->nfaces, c->nturns, cs, sn, 2.0 / c->n_rf, 1.0 / c->n_rf, c->n_rf);
     count_launch();
 }
@@ -636,10 +651,10 @@ void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
 void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
     int nn = (c->i_win + 1) * c->NR;
     if (c->fp64)
-        accumulate_nodes<double><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
+        launch_pdl(accumulate_nodes<double>, (nn + 255) / 256, 256, 0, st, c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
                                                                    c->d_Jc_c, c->d_Js_c, nn, wc, ws);
     else
-        accumulate_nodes<float><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
+        launch_pdl(accumulate_nodes<float>, (nn + 255) / 256, 256, 0, st, c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
                                                                   c->d_Js_c, nn, wc, ws);
     count_launch();
 }
@@ -647,11 +662,13 @@ void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
 void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
     int n = (c->i_win + 1) * c->NR;
     if (c->fp64)
-        field_prep<double><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64, c->NR,
+        launch_pdl(field_prep<double>, (n + 255) / 256, 256, 0, st, c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64,
+                   c->d_rho64, c->d_jm64, c->NR,
                                                             c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                             c->cfg.magnetic_force);
     else
-        field_prep<float><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->NR,
+        launch_pdl(field_prep<float>, (n + 255) / 256, 256, 0, st, c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F,
+                   c->d_rho, c->d_jm, c->NR,
                                                            c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                            c->cfg.magnetic_force);
     count_launch();
@@ -663,8 +680,6 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     int nint = rows * M;
     int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
     DevState* dst = c->d_st;
-    cudaMemsetAsync(&dst->pnorm[0], 0, sizeof(dst->pnorm), st);
-    cudaMemsetAsync(&dst->pdone, 0, sizeof(int), st);
     int* done = &dst->pdone;
     const double* ext = external_targets ? d_targets : nullptr;
     PoisArgs a;
@@ -689,23 +704,23 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     a.cs = cs;
     a.sn = sn;
     const int K = c->ntn;
-    poisson_set_turns<<<(K + 63) / 64, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K, dst, ext, c->nturns, cs, sn);
+    launch_pdl(poisson_set_turns, (K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st, c->d_phi, c->d_tn_node, c->d_tn_k, K, dst, ext, c->nturns, cs, sn);
     count_launch();
     for (int it = 0; it <= maxit; ++it) {
         a.norm = &dst->pnorm[2 * it];
-        poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
+        launch_pdl(poisson_residual, (nint + 255) / 256, 256, 0, st, a);
         count_launch();
         if (it == maxit) {
-            poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, done, 1);
+            launch_pdl(poisson_check, 1, 32, 0, st, dst, it, c->cfg.poisson_tol, done, 1);
             count_launch();
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)
-        gemm_rows<true><<<rows, 128, sizeof(float) * M, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, M, dst, it,
+        launch_pdl(gemm_rows<true>, rows, 128, sizeof(float) * M, st, c->d_r32, c->ps.Vf, c->ps.t0, M, dst, it,
                                                                  c->cfg.poisson_tol, done);
         launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
-        gemm_rows<false><<<rows, 128, sizeof(float) * M, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, M, dst, it, 0.0, done);
-        poisson_update_zt<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
+        launch_pdl(gemm_rows<false>, rows, 128, sizeof(float) * M, st, c->ps.t1, c->ps.Vb, c->ps.t0, M, dst, it, 0.0, done);
+        launch_pdl(poisson_update_zt, (nint + 255) / 256, 256, 0, st, c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
                                                                c->ntn_pad, rows, M, c->NR, c->d_turn_mask, done);
         count_launch(4);
     }
