@@ -54,15 +54,19 @@ __global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __r
     }
 }
 
-// Row-parallel product C = A V of a rows x M matrix with an M x M matrix: one
-// block per row of A (staged in shared memory), each thread a set of output
-// columns with four partial sums; V is read coalesced along its rows from L2.
-// With `check`, the block first takes the convergence decision of the sweep
-// from the residual norms (identical in every block).
+// Row-parallel product C = A V of a rows x M matrix with an M x M matrix: a
+// block takes kGemmRows rows of A (staged in shared memory) and streams V
+// through shared memory in slabs of 32 rows, each thread accumulating its
+// output columns of every row.  With `check`, the block first takes the
+// convergence decision of the sweep from the residual norms (identical in
+// every block).
+constexpr int kGemmRows = 2;
+constexpr int kGemmSlab = 32;
+
 template <bool check>
 __global__ void __launch_bounds__(128) gemm_rows(const float* __restrict__ A, const float* __restrict__ V,
-                                                 float* __restrict__ C, int M, DevState* st, int sweep, double tol,
-                                                 int* done) {
+                                                 float* __restrict__ C, int rows, int M, DevState* st, int sweep,
+                                                 double tol, int* done) {
     pdl_wait();
     if (*done) return;
     if (check) {
@@ -76,21 +80,45 @@ __global__ void __launch_bounds__(128) gemm_rows(const float* __restrict__ A, co
         }
         if (rel <= tol) return;
     }
-    extern __shared__ float arow[];
-    const float* a = A + (size_t)blockIdx.x * M;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) arow[k] = a[k];
-    __syncthreads();
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int k = 0;
-        for (; k + 3 < M; k += 4) {
-            s0 += arow[k] * V[(size_t)k * M + m];
-            s1 += arow[k + 1] * V[(size_t)(k + 1) * M + m];
-            s2 += arow[k + 2] * V[(size_t)(k + 2) * M + m];
-            s3 += arow[k + 3] * V[(size_t)(k + 3) * M + m];
+    extern __shared__ float smg[];
+    float* arow = smg;                              // kGemmRows x M
+    float* vs = smg + kGemmRows * M;                // kGemmSlab x M
+    const int r0 = blockIdx.x * kGemmRows;
+    for (int q = threadIdx.x; q < kGemmRows * M; q += blockDim.x) {
+        int r = q / M;
+        arow[q] = (r0 + r < rows) ? A[(size_t)(r0 + r) * M + q % M] : 0.f;
+    }
+    // each thread: columns m = threadIdx.x + 128 c, c < MC (M <= 512)
+    constexpr int MC = 4;
+    float acc[kGemmRows][MC];
+#pragma unroll
+    for (int r = 0; r < kGemmRows; ++r)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[r][c] = 0.f;
+    for (int k0 = 0; k0 < M; k0 += kGemmSlab) {
+        const int kn = min(kGemmSlab, M - k0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kn * M; q += blockDim.x) vs[q] = V[(size_t)k0 * M + q];
+        __syncthreads();
+        for (int k = 0; k < kn; ++k) {
+#pragma unroll
+            for (int c = 0; c < MC; ++c) {
+                int m = threadIdx.x + 128 * c;
+                if (m < M) {
+                    float v = vs[k * M + m];
+#pragma unroll
+                    for (int r = 0; r < kGemmRows; ++r) acc[r][c] += arow[r * M + k0 + k] * v;
+                }
+            }
         }
-        for (; k < M; ++k) s0 += arow[k] * V[(size_t)k * M + m];
-        C[(size_t)blockIdx.x * M + m] = (s0 + s1) + (s2 + s3);
+    }
+#pragma unroll
+    for (int c = 0; c < MC; ++c) {
+        int m = threadIdx.x + 128 * c;
+        if (m >= M) continue;
+#pragma unroll
+        for (int r = 0; r < kGemmRows; ++r)
+            if (r0 + r < rows) C[(size_t)(r0 + r) * M + m] = acc[r][c];
     }
 }
 
@@ -716,10 +744,19 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)
-        launch_pdl(gemm_rows<true>, rows, 128, sizeof(float) * M, st, c->d_r32, c->ps.Vf, c->ps.t0, M, dst, it,
+        const unsigned gb = (unsigned)((rows + kGemmRows - 1) / kGemmRows);
+        const size_t gsm = sizeof(float) * (kGemmRows + kGemmSlab) * M;
+        static bool gattr = false;
+        if (!gattr) {
+            const int mx = (int)(sizeof(float) * (kGemmRows + kGemmSlab) * 512);
+            cudaFuncSetAttribute(gemm_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(gemm_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            gattr = true;
+        }
+        launch_pdl(gemm_rows<true>, gb, 128, gsm, st, c->d_r32, c->ps.Vf, c->ps.t0, rows, M, dst, it,
                                                                  c->cfg.poisson_tol, done);
         launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
-        launch_pdl(gemm_rows<false>, rows, 128, sizeof(float) * M, st, c->ps.t1, c->ps.Vb, c->ps.t0, M, dst, it, 0.0, done);
+        launch_pdl(gemm_rows<false>, gb, 128, gsm, st, c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, dst, it, 0.0, done);
         launch_pdl(poisson_update_zt, (nint + 255) / 256, 256, 0, st, c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
                                                                c->ntn_pad, rows, M, c->NR, c->d_turn_mask, done);
         count_launch(4);

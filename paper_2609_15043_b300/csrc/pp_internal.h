@@ -25,7 +25,13 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr uint32_t kDead = 0xFFFFFFFFu;
 
 constexpr int kPushThreads = 256;
-constexpr int kPPT = 8;                           // particles per thread per chunk
+#ifndef PP_PPT
+#define PP_PPT 8
+#endif
+#ifndef PP_PUSH_MINB
+#define PP_PUSH_MINB 3
+#endif
+constexpr int kPPT = PP_PPT;                      // particles per thread per chunk (power of two)
 constexpr int kChunk = kPushThreads * kPPT;
 constexpr int kTileRows = 8;                      // node rows of the shared deposit tile
 constexpr int kMaxNR = 513;                       // node columns supported by the tile

@@ -202,7 +202,7 @@ struct PushSmem {
 // charge deposits accumulated in registers, move, boundaries, null test), the
 // few collision candidates are then processed densely, and bulk copies write
 // the six updated slices back.
-__global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
+__global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
     pdl_wait();
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t* s_cell = reinterpret_cast<uint32_t*>(smem);
@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
     __shared__ int s_ncand;
     __shared__ int s_ok;
     __shared__ float s_f[kPushThreads / 32][2];
-    __shared__ unsigned s_c[kPushThreads / 32][10];
+    __shared__ unsigned s_c[kPushThreads / 32][3];
+    __shared__ unsigned s_pc[6];            // collision-pass tallies of the block
 
     const int n0 = a.nslot[0], n1 = a.nslot[1];
     const int ce = (n0 + kChunk - 1) / kChunk, ci = (n1 + kChunk - 1) / kChunk;
@@ -233,11 +234,13 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
         mbar_init(&s_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (t < 6) s_pc[t] = 0u;
     __syncthreads();
 
     float acc_ind = 0.f, acc_es = 0.f;
-    // counters: 0 el/cx, 1 ex/iso, 2 iz, 3 cx, 4 iso, 5 nu violations, 6 pushed, 7 absorbed e, 8 absorbed i
-    unsigned cnt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // per-thread counters of the push: 0 pushed, 1 absorbed e, 2 absorbed i
+    // (the collision pass tallies into s_pc: 0 el/cx... see below)
+    unsigned cnt[3] = {0, 0, 0};
     uint32_t parity = 0;
 
     for (int chunk = blockIdx.x; chunk < ce + ci; chunk += gridDim.x) {
@@ -308,9 +311,10 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
         DepAcc dq{-1, 0, 0.f, 0.f, 0.f, 0.f};
         uint32_t fcell = kDead;
         float4 f0, f1, f2, f3, f4;
-        // thread t owns particles t*kPPT .. t*kPPT + 7 and visits them starting
-        // at offset t/4: the 32 lanes of a warp then hit 32 different banks
-        const int p0 = t * kPPT, rot = (t >> 2) & (kPPT - 1);
+        // thread t owns particles t*kPPT .. t*kPPT + kPPT-1 and visits them
+        // starting at offset t/(32/kPPT): the 32 lanes of a warp then hit 32
+        // different banks
+        const int p0 = t * kPPT, rot = (t / (32 / kPPT)) & (kPPT - 1);
 #pragma unroll 1
         for (int k = 0; k < kPPT; ++k) {
             const int p = p0 + ((k + rot) & (kPPT - 1));
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
             float jmv = S.qw * vbt;
             acc_ind += jmv * Et;
             acc_es += S.qw * (vbr * Er + vbz * Ez);
-            ++cnt[6];
+            ++cnt[0];
             dep_run(dj, tj, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
             // move (cell units): r' = |(r + a, b)| written as r + delta
             float am = vnx * S.dtr, bm = vny * S.dtr, cm = vnz * S.dtz;
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
                     s_cand[slot] = (uint16_t)p;
                 }
             } else {
-                ++cnt[7 + sp];
+                ++cnt[1 + sp];
             }
             s_cell[p] = ncell;
             s_dr[p] = alive ? drn : 0.0f;
@@ -439,16 +443,21 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
         // ---- phase B: collisions of the candidates
         const int nc = s_ncand;
         const CollCtx<float> cc{a.key0, a.key1, a.ev, a.st, a.sp[1].vth_gas};
-        for (int c = t; c < nc; c += kPushThreads) {
-            const int p = s_cand[c];
-            float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
-            if (sp == 0)
-                electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], cnt);
-            else
-                ion_collision(cc, step, S, s_uid[p], vx, vy, vzz, cnt);
-            s_vr[p] = vx;
-            s_vt[p] = vy;
-            s_vz[p] = vzz;
+        if (t < nc) {
+            unsigned pc[6] = {0, 0, 0, 0, 0, 0};
+            for (int c = t; c < nc; c += kPushThreads) {
+                const int p = s_cand[c];
+                float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
+                if (sp == 0)
+                    electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], pc);
+                else
+                    ion_collision(cc, step, S, s_uid[p], vx, vy, vzz, pc);
+                s_vr[p] = vx;
+                s_vt[p] = vy;
+                s_vz[p] = vzz;
+            }
+            for (int q = 0; q < 6; ++q)
+                if (pc[q]) atomicAdd(&s_pc[q], pc[q]);
         }
         __syncthreads();
         // ---- write back (bulk) and flush the node tiles
@@ -476,20 +485,21 @@ __global__ void __launch_bounds__(kPushThreads, 3) push_kernel(PushArgs a) {
         acc_ind += __shfl_xor_sync(0xffffffffu, acc_ind, o);
         acc_es += __shfl_xor_sync(0xffffffffu, acc_es, o);
     }
-    for (int q = 0; q < 10; ++q) cnt[q] = __reduce_add_sync(0xffffffffu, cnt[q]);
+    for (int q = 0; q < 3; ++q) cnt[q] = __reduce_add_sync(0xffffffffu, cnt[q]);
     if (lane == 0) {
         s_f[warp][0] = acc_ind;
         s_f[warp][1] = acc_es;
-        for (int q = 0; q < 10; ++q) s_c[warp][q] = cnt[q];
+        for (int q = 0; q < 3; ++q) s_c[warp][q] = cnt[q];
     }
     __syncthreads();
     if (t == 0) {
         double si = 0, se = 0;
-        unsigned long long tot[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // 0 el/cx, 1 ex/iso, 2 iz, 3 cx, 4 iso, 5 nu violations, 6 pushed, 7 absorbed e, 8 absorbed i
+        unsigned long long tot[10] = {s_pc[0], s_pc[1], s_pc[2], s_pc[3], s_pc[4], s_pc[5], 0, 0, 0, 0};
         for (int w = 0; w < kPushThreads / 32; ++w) {
             si += s_f[w][0];
             se += s_f[w][1];
-            for (int q = 0; q < 10; ++q) tot[q] += s_c[w][q];
+            for (int q = 0; q < 3; ++q) tot[6 + q] += s_c[w][q];
         }
         DevState* st = a.st;
         atomicAdd(&st->p_ind_step, si);

@@ -103,6 +103,7 @@ def train(args):
     mask = np.zeros(OUT_PAD, np.float32)
     mask[:n_out] = 1.0
     step = 0
+    best = (float("inf"), None)
     for epoch in range(args.epochs):
         order = rng.permutation(tr)
         for s0 in range(0, len(order), args.batch):
@@ -125,10 +126,17 @@ def train(args):
                     mh = m[l] / (1 - b1 ** step)
                     vh = v[l] / (1 - b2 ** step)
                     p[l] -= (lr * mh / (np.sqrt(vh) + eps)).astype(np.float32)
+                W[l] -= np.float32(lr * args.weight_decay) * W[l]
+        # keep the weights of the best validation epoch (the loads are noisy:
+        # past that point the fit learns the noise)
+        ov, _ = _forward(W, b, Xn[val])
+        mse = float(np.mean(((ov - Yn[val]) * mask)[:, :n_out] ** 2))
+        if mse < best[0]:
+            best = (mse, ([w.copy() for w in W], [x.copy() for x in b], epoch))
         if epoch % 50 == 0 or epoch == args.epochs - 1:
-            ov, _ = _forward(W, b, Xn[val])
-            mse = float(np.mean(((ov - Yn[val]) * mask)[:, :n_out] ** 2))
             print("epoch %d  validation mse (standardised) %.4g" % (epoch, mse), file=sys.stderr, flush=True)
+    W, b, best_epoch = best[1]
+    print("best epoch %d  validation mse %.4g" % (best_epoch, best[0]), file=sys.stderr, flush=True)
     wbits = [_bf16_bits(w) for w in W]
     np.savez(args.out, w0=wbits[0], w1=wbits[1], w2=wbits[2], w3=wbits[3], b0=b[0], b1=b[1], b2=b[2], b3=b[3],
              mu_in=mu_in, sig_in=sig_in, mu_out=mu_out, sig_out=sig_out)
@@ -158,6 +166,7 @@ def main():
     t.add_argument("--batch", type=int, default=256)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=7)
+    t.add_argument("--weight-decay", type=float, default=1e-2)
     a = ap.parse_args()
     collect(a) if a.cmd == "collect" else train(a)
 

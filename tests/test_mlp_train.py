@@ -22,6 +22,7 @@ def test_trainer_fits_a_smooth_map(tmp_path):
         batch = 128
         lr = 2e-3
         seed = 1
+        weight_decay = 0.0
     mlp_train.train(A_)
     p = mlp_train.load_params(A_.out)
     assert [w.shape for w in p["w"]] == [(256, 256)] * 3 + [(32, 256)]
