@@ -54,74 +54,6 @@ __global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __r
     }
 }
 
-// Row-parallel product C = A V of a rows x M matrix with an M x M matrix: a
-// block takes kGemmRows rows of A (staged in shared memory) and streams V
-// through shared memory in slabs of 32 rows, each thread accumulating its
-// output columns of every row.  With `check`, the block first takes the
-// convergence decision of the sweep from the residual norms (identical in
-// every block).
-constexpr int kGemmRows = 2;
-constexpr int kGemmSlab = 32;
-
-template <bool check>
-__global__ void __launch_bounds__(128) gemm_rows(const float* __restrict__ A, const float* __restrict__ V,
-                                                 float* __restrict__ C, int rows, int M, DevState* st, int sweep,
-                                                 double tol, int* done) {
-    pdl_wait();
-    if (*done) return;
-    if (check) {
-        double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
-        double sn = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
-        double rel = (sn > 0) ? rn / sn : 0.0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            st->prel = rel;
-            st->piters = sweep;
-            if (rel <= tol) *done = 1;
-        }
-        if (rel <= tol) return;
-    }
-    extern __shared__ float smg[];
-    float* arow = smg;                              // kGemmRows x M
-    float* vs = smg + kGemmRows * M;                // kGemmSlab x M
-    const int r0 = blockIdx.x * kGemmRows;
-    for (int q = threadIdx.x; q < kGemmRows * M; q += blockDim.x) {
-        int r = q / M;
-        arow[q] = (r0 + r < rows) ? A[(size_t)(r0 + r) * M + q % M] : 0.f;
-    }
-    // each thread: columns m = threadIdx.x + 128 c, c < MC (M <= 512)
-    constexpr int MC = 4;
-    float acc[kGemmRows][MC];
-#pragma unroll
-    for (int r = 0; r < kGemmRows; ++r)
-#pragma unroll
-        for (int c = 0; c < MC; ++c) acc[r][c] = 0.f;
-    for (int k0 = 0; k0 < M; k0 += kGemmSlab) {
-        const int kn = min(kGemmSlab, M - k0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < kn * M; q += blockDim.x) vs[q] = V[(size_t)k0 * M + q];
-        __syncthreads();
-        for (int k = 0; k < kn; ++k) {
-#pragma unroll
-            for (int c = 0; c < MC; ++c) {
-                int m = threadIdx.x + 128 * c;
-                if (m < M) {
-                    float v = vs[k * M + m];
-#pragma unroll
-                    for (int r = 0; r < kGemmRows; ++r) acc[r][c] += arow[r * M + k0 + k] * v;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < MC; ++c) {
-        int m = threadIdx.x + 128 * c;
-        if (m >= M) continue;
-#pragma unroll
-        for (int r = 0; r < kGemmRows; ++r)
-            if (r0 + r < rows) C[(size_t)(r0 + r) * M + m] = acc[r][c];
-    }
-}
-
 // First product of a refinement sweep, preceded by the convergence decision
 // on the residual of this sweep: every block reads the same norms and either
 // all return (converged) or all compute.
@@ -225,7 +157,6 @@ template <int EPT>
 __global__ void __launch_bounds__(256) pcr_solve(const float* __restrict__ f, float* __restrict__ x,
                                                  const float* __restrict__ al, const float* __restrict__ ga,
                                                  const float* __restrict__ ib, int rows, int M, int L, const int* skip) {
-    pdl_wait();
     if (skip && *skip) return;
     __shared__ float d[2][256 * EPT];
     const int m = blockIdx.x;
@@ -271,11 +202,11 @@ __global__ void __launch_bounds__(256) pcr_solve(const float* __restrict__ f, fl
 static void launch_pcr(const Cell* c, const float* f, float* x, cudaStream_t st, const int* skip) {
     int rows = c->ps.rows, M = c->ps.M, L = c->pcr_levels;
     if (rows <= 256)
-        launch_pdl(pcr_solve<1>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        pcr_solve<1><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
     else if (rows <= 512)
-        launch_pdl(pcr_solve<2>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        pcr_solve<2><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
     else
-        launch_pdl(pcr_solve<4>, M, 256, 0, st, f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
+        pcr_solve<4><<<M, 256, 0, st>>>(f, x, c->d_pcr_a, c->d_pcr_g, c->d_pcr_ib, rows, M, L, skip);
 }
 
 template <typename T>
@@ -333,7 +264,6 @@ struct PoisArgs {
 // capacitance step imposes their values).  The relative residual is
 // max|r| / max(|b| + sum |A_ij phi_j|) (a componentwise scale).
 __global__ void poisson_residual(PoisArgs a) {
-    pdl_wait();
     if (*a.done) return;
     int rows = a.NZ - 2;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -376,7 +306,6 @@ __global__ void poisson_residual(PoisArgs a) {
 
 // decides convergence from the norms of this sweep (runs before the solve)
 __global__ void poisson_check(DevState* st, int sweep, double tol, int* done, int final_sweep) {
-    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (*done) return;
     double r = __longlong_as_double((long long)st->pnorm[2 * sweep]);
@@ -411,7 +340,6 @@ __global__ void poisson_cap(const DevState* st, const double* ext, const double*
 // later correction there is zero and no kernel of the solve writes them
 __global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn_k, int K, DevState* st,
                                   const double* ext, int nt, double cs, double sn) {
-    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     // fresh refinement bookkeeping for this solve
     if (t < 2 * 16) st->pnorm[t] = 0ull;
@@ -424,7 +352,6 @@ __global__ void poisson_set_turns(double* phi, const int* tn_node, const int* tn
 __global__ void poisson_update_zt(double* phi, const float* d0, const float* __restrict__ Zt, const double* Ginv,
                                   const int* tn_int, int K, int Kp, int rows, int M, int NR,
                                   const signed char* turn_mask, const int* done) {
-    pdl_wait();
     if (*done) return;
     __shared__ double s_r[kMaxCapNodes];
     __shared__ double s_sig[kMaxCapNodes + 4];
@@ -503,7 +430,6 @@ __global__ void field_prep(const double* __restrict__ phi, const double* __restr
                            const double* __restrict__ Ess, const double* __restrict__ B, T* F, T* rho, T* jm,
                            int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
                            double sn, int magnetic) {
-    pdl_wait();
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (i_win + 1) * NR) return;
     // the step's deposits land on node rows 0..i_win only: clear them here
@@ -537,7 +463,6 @@ __global__ void field_prep(const double* __restrict__ phi, const double* __restr
 __global__ void turn_sample(DevState* st, const double* phi, const int* ft, const int* fnb, const int* fk,
                             const double* fc, int nfaces, int nt, double cs, double sn, double two_over_n,
                             double inv_n, int n_rf) {
-    pdl_wait();
     __shared__ double q[PP_MAX_TURNS];
     if (threadIdx.x < PP_MAX_TURNS) q[threadIdx.x] = 0;
     __syncthreads();
@@ -571,7 +496,6 @@ __global__ void turn_sample(DevState* st, const double* phi, const int* ft, cons
 template <typename T>
 __global__ void accumulate_nodes(const T* jm, const double* vol, double* Jc, double* Js, double* Jcc,
                                  double* Jsc, int nn, double wc, double ws) {
-    pdl_wait();
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     double J = (double)jm[n] / vol[n];
@@ -671,7 +595,7 @@ void launch_compose(Cell* c, bool from_new, cudaStream_t st) {
 
 // ---------------------------------------------------------------- launchers
 void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
-    launch_pdl(turn_sample, 1, 256, 0, st, c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
+    turn_sample<<<1, 256, 0, st>>>(c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
                                    c->nfaces, c->nturns, cs, sn, 2.0 / c->n_rf, 1.0 / c->n_rf, c->n_rf);
     count_launch();
 }
@@ -679,10 +603,10 @@ void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
 void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
     int nn = (c->i_win + 1) * c->NR;
     if (c->fp64)
-        launch_pdl(accumulate_nodes<double>, (nn + 255) / 256, 256, 0, st, c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
+        accumulate_nodes<double><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
                                                                    c->d_Jc_c, c->d_Js_c, nn, wc, ws);
     else
-        launch_pdl(accumulate_nodes<float>, (nn + 255) / 256, 256, 0, st, c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
+        accumulate_nodes<float><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
                                                                   c->d_Js_c, nn, wc, ws);
     count_launch();
 }
@@ -690,12 +614,12 @@ void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
 void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
     int n = (c->i_win + 1) * c->NR;
     if (c->fp64)
-        launch_pdl(field_prep<double>, (n + 255) / 256, 256, 0, st, c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64,
+        field_prep<double><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64,
                    c->d_rho64, c->d_jm64, c->NR,
                                                             c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                             c->cfg.magnetic_force);
     else
-        launch_pdl(field_prep<float>, (n + 255) / 256, 256, 0, st, c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F,
+        field_prep<float><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F,
                    c->d_rho, c->d_jm, c->NR,
                                                            c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                            c->cfg.magnetic_force);
@@ -732,32 +656,24 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     a.cs = cs;
     a.sn = sn;
     const int K = c->ntn;
-    launch_pdl(poisson_set_turns, (K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st, c->d_phi, c->d_tn_node, c->d_tn_k, K, dst, ext, c->nturns, cs, sn);
+    poisson_set_turns<<<(K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K, dst,
+                                                                           ext, c->nturns, cs, sn);
     count_launch();
+    dim3 gblk(32, 8), ggrd((M + 31) / 32, (rows + 31) / 32);
     for (int it = 0; it <= maxit; ++it) {
         a.norm = &dst->pnorm[2 * it];
-        launch_pdl(poisson_residual, (nint + 255) / 256, 256, 0, st, a);
+        poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
         count_launch();
         if (it == maxit) {
-            launch_pdl(poisson_check, 1, 32, 0, st, dst, it, c->cfg.poisson_tol, done, 1);
+            poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, done, 1);
             count_launch();
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)
-        const unsigned gb = (unsigned)((rows + kGemmRows - 1) / kGemmRows);
-        const size_t gsm = sizeof(float) * (kGemmRows + kGemmSlab) * M;
-        static bool gattr = false;
-        if (!gattr) {
-            const int mx = (int)(sizeof(float) * (kGemmRows + kGemmSlab) * 512);
-            cudaFuncSetAttribute(gemm_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            cudaFuncSetAttribute(gemm_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            gattr = true;
-        }
-        launch_pdl(gemm_rows<true>, gb, 128, gsm, st, c->d_r32, c->ps.Vf, c->ps.t0, rows, M, dst, it,
-                                                                 c->cfg.poisson_tol, done);
+        gemm_check<<<ggrd, gblk, 0, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, rows, M, M, dst, it, c->cfg.poisson_tol, done);
         launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
-        launch_pdl(gemm_rows<false>, gb, 128, gsm, st, c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, dst, it, 0.0, done);
-        launch_pdl(poisson_update_zt, (nint + 255) / 256, 256, 0, st, c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
+        gemm_rm<float><<<ggrd, gblk, 0, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, M, done);
+        poisson_update_zt<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
                                                                c->ntn_pad, rows, M, c->NR, c->d_turn_mask, done);
         count_launch(4);
     }

@@ -265,33 +265,6 @@ struct Cell {
     }
 };
 
-// Programmatic dependent launch: kernels of the step chain are launched with
-// programmatic stream serialization and open with pdl_wait(), which lets the
-// next kernel of the stream be scheduled as soon as every block of this one
-// has started, and holds this one until its predecessor has completed and its
-// writes are visible.  A kernel launched without the attribute passes both
-// instructions at once.
-__device__ __forceinline__ void pdl_wait() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
 void set_error(const std::string& s);
 extern unsigned long long g_launches;     // kernels launched by this library (host count)
 inline void count_launch(int n = 1) { g_launches += (unsigned long long)n; }

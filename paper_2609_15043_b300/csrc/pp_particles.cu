@@ -203,7 +203,6 @@ struct PushSmem {
 // few collision candidates are then processed densely, and bulk copies write
 // the six updated slices back.
 __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
-    pdl_wait();
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t* s_cell = reinterpret_cast<uint32_t*>(smem);
     float* s_dr = reinterpret_cast<float*>(s_cell + kChunk);
@@ -555,7 +554,7 @@ void launch_push(Cell* c, cudaStream_t st) {
     a.st = c->d_st;
     size_t shm = PushSmem::bytes(c->NR);
     push_prepare(c);
-    launch_pdl(push_kernel, c->push_blocks, kPushThreads, shm, st, a);
+    push_kernel<<<c->push_blocks, kPushThreads, shm, st>>>(a);
     count_launch();
 }
 
@@ -596,7 +595,6 @@ void launch_deposit_only(Cell* c, cudaStream_t st) {
 template <typename T>
 __global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next_uid, const EventT<T>* ev,
                               DevState* st, int64_t cap_e, int64_t cap_i) {
-    pdl_wait();
     __shared__ uint32_t key[kEventCap];
     __shared__ uint16_t val[kEventCap];
     int n_ev = min(st->n_events, kEventCap);
@@ -667,17 +665,16 @@ __global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next
 
 void launch_append(Cell* c, cudaStream_t st) {
     if (c->fp64)
-        launch_pdl(append_kernel<double>, 1, 1024, 0, st, c->pd[0][c->cur[0]], c->pd[1][c->cur[1]], c->d_nslot,
+        append_kernel<double><<<1, 1024, 0, st>>>(c->pd[0][c->cur[0]], c->pd[1][c->cur[1]], c->d_nslot,
                                                   c->d_next_uid, c->d_events64, c->d_st, c->cap[0], c->cap[1]);
     else
-        launch_pdl(append_kernel<float>, 1, 1024, 0, st, c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot,
+        append_kernel<float><<<1, 1024, 0, st>>>(c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot,
                                                  c->d_next_uid, c->d_events, c->d_st, c->cap[0], c->cap[1]);
     count_launch();
 }
 
 // ---------------------------------------------------------------- counting sort
 __global__ void sort_hist(const uint32_t* cell, const int* nslot, int sp, uint32_t* hist, int ncell) {
-    pdl_wait();
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = idx < nslot[sp];
     uint32_t c = act ? cell[idx] : kDead;
@@ -689,7 +686,6 @@ __global__ void sort_hist(const uint32_t* cell, const int* nslot, int sp, uint32
 
 // exclusive scan of n bins in one block; hist[n] receives the total
 __global__ void sort_scan(uint32_t* hist, int n) {
-    pdl_wait();
     __shared__ uint32_t part[1024];
     int t = threadIdx.x;
     int per = (n + blockDim.x - 1) / blockDim.x;
@@ -715,7 +711,6 @@ __global__ void sort_scan(uint32_t* hist, int n) {
 
 template <typename T>
 __global__ void sort_scatter(PBuf<T> src, PBuf<T> dst, const int* nslot, int sp, uint32_t* offs) {
-    pdl_wait();
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = idx < nslot[sp];
     uint32_t c = act ? src.cell[idx] : kDead;
@@ -740,7 +735,6 @@ __global__ void sort_scatter(PBuf<T> src, PBuf<T> dst, const int* nslot, int sp,
 
 // the new slot count, then the bins are cleared for the next sort
 __global__ void sort_finish(int* nslot, int sp, uint32_t* hist, int ncell) {
-    pdl_wait();
     __shared__ uint32_t total;
     if (threadIdx.x == 0) total = hist[ncell];
     __syncthreads();
@@ -753,16 +747,16 @@ void launch_sort(Cell* c, int sp, cudaStream_t st) {
     int64_t n = c->cap[sp];
     unsigned nb = (unsigned)((n + 255) / 256);
     const uint32_t* src_cell = c->fp64 ? c->pd[sp][c->cur[sp]].cell : c->pb[sp][c->cur[sp]].cell;
-    launch_pdl(sort_hist, nb, 256, 0, st, src_cell, c->d_nslot, sp, c->d_hist, ncell);
+    sort_hist<<<nb, 256, 0, st>>>(src_cell, c->d_nslot, sp, c->d_hist, ncell);
     // live bins only: the dead bin (index ncell) is left out of the scan
-    launch_pdl(sort_scan, 1, 1024, 0, st, c->d_hist, ncell);
+    sort_scan<<<1, 1024, 0, st>>>(c->d_hist, ncell);
     if (c->fp64)
-        launch_pdl(sort_scatter<double>, nb, 256, 0, st, c->pd[sp][c->cur[sp]], c->pd[sp][1 - c->cur[sp]], c->d_nslot, sp,
+        sort_scatter<double><<<nb, 256, 0, st>>>(c->pd[sp][c->cur[sp]], c->pd[sp][1 - c->cur[sp]], c->d_nslot, sp,
                                                  c->d_hist);
     else
-        launch_pdl(sort_scatter<float>, nb, 256, 0, st, c->pb[sp][c->cur[sp]], c->pb[sp][1 - c->cur[sp]], c->d_nslot, sp,
+        sort_scatter<float><<<nb, 256, 0, st>>>(c->pb[sp][c->cur[sp]], c->pb[sp][1 - c->cur[sp]], c->d_nslot, sp,
                                                 c->d_hist);
-    launch_pdl(sort_finish, 1, 1024, 0, st, c->d_nslot, sp, c->d_hist, ncell);
+    sort_finish<<<1, 1024, 0, st>>>(c->d_nslot, sp, c->d_hist, ncell);
     count_launch(4);
     c->cur[sp] = 1 - c->cur[sp];
 }

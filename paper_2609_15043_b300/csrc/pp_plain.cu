@@ -37,7 +37,6 @@ __device__ __forceinline__ void add4(T* g, int NR, int iz, int ir, T v0, T v1, T
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
-    pdl_wait();
     __shared__ double s_f[8][2];
     __shared__ unsigned s_c[8][10];
     const int n0 = a.nslot[0], n1 = a.nslot[1];
@@ -227,7 +226,7 @@ void launch_push_plain(Cell* c, cudaStream_t st) {
     int64_t want = (slots + 255) / 256;
     int64_t blocks = (int64_t)nsm * 8;
     if (want < blocks) blocks = want < 1 ? 1 : want;
-    launch_pdl(push_plain<double>, (unsigned)blocks, 256, 0, st, a);
+    push_plain<double><<<(unsigned)blocks, 256, 0, st>>>(a);
     count_launch();
 }
 
