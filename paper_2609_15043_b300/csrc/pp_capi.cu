@@ -100,9 +100,8 @@ static void one_step(Cell* c, cudaStream_t st) {
     poisson_refine(c, std::cos(th1), std::sin(th1), st, false, nullptr);
     phase_mark(c, PH_POISSON, false, st);
     phase_mark(c, PH_OTHER, true, st);
-    launch_turn_sample(c, std::cos(th1), std::sin(th1), st);
     double two_n = 2.0 / c->n_rf;
-    launch_accumulate(c, two_n * std::cos(th), two_n * std::sin(th), st);
+    launch_sample_accumulate(c, std::cos(th1), std::sin(th1), two_n * std::cos(th), two_n * std::sin(th), st);
     phase_mark(c, PH_OTHER, false, st);
     c->s = s + 1;
     for (int sp = 0; sp < 2; ++sp) {

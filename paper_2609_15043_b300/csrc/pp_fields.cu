@@ -54,40 +54,61 @@ __global__ void gemm_rm(const T* __restrict__ A, const T* __restrict__ B, T* __r
     }
 }
 
-// First product of a refinement sweep, preceded by the convergence decision
-// on the residual of this sweep: every block reads the same norms and either
-// all return (converged) or all compute.
-__global__ void gemm_check(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int rows,
-                           int K, int N, DevState* st, int sweep, double tol, int* done) {
+// The two products of a Poisson sweep, C = A B with 32 x 32 output tiles:
+// K is taken in slabs of 128 whose 32 loads per thread are all issued before
+// any of them is stored to shared memory, so a slab costs one memory latency.
+// With `check` the block first takes the sweep's convergence decision from
+// the residual norms (identical in every block; all return when converged).
+template <bool check>
+__global__ void __launch_bounds__(256) gemm_sweep(const float* __restrict__ A, const float* __restrict__ B,
+                                                  float* __restrict__ C, int rows, int K, int N, DevState* st,
+                                                  int sweep, double tol, int* done) {
     if (*done) return;
-    double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
-    double sn = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
-    double rel = (sn > 0) ? rn / sn : 0.0;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-        st->prel = rel;
-        st->piters = sweep;
-        if (rel <= tol) *done = 1;
-    }
-    if (rel <= tol) return;
-    __shared__ float As[32][33];
-    __shared__ float Bs[32][33];
-    int tx = threadIdx.x, ty = threadIdx.y;
-    int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    float acc[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        for (int q = 0; q < 4; ++q) {
-            int r = ty + 8 * q;
-            As[r][tx] = (r0 + r < rows && k0 + tx < K) ? A[(size_t)(r0 + r) * K + k0 + tx] : 0.f;
-            Bs[r][tx] = (k0 + r < K && c0 + tx < N) ? B[(size_t)(k0 + r) * N + c0 + tx] : 0.f;
+    if (check) {
+        double rn = __longlong_as_double((long long)st->pnorm[2 * sweep]);
+        double sn = __longlong_as_double((long long)st->pnorm[2 * sweep + 1]);
+        double rel = (sn > 0) ? rn / sn : 0.0;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+            st->prel = rel;
+            st->piters = sweep;
+            if (rel <= tol) *done = 1;
         }
+        if (rel <= tol) return;
+    }
+    constexpr int KS = 128;
+    __shared__ float As[32][KS + 1];
+    __shared__ float Bs[KS][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;          // 32 x 8
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += KS) {
+        float ra[4][4], rb[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = ty + 8 * q, k = k0 + 32 * j + tx, kr = k0 + 32 * j + r;
+                ra[j][q] = (r0 + r < rows && k < K) ? A[(size_t)(r0 + r) * K + k] : 0.f;
+                rb[j][q] = (kr < K && c0 + tx < N) ? B[(size_t)kr * N + c0 + tx] : 0.f;
+            }
+        if (k0) __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                As[ty + 8 * q][32 * j + tx] = ra[j][q];
+                Bs[32 * j + ty + 8 * q][tx] = rb[j][q];
+            }
         __syncthreads();
+        const int kn = min(KS, K - k0);
 #pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < kn; ++k) {
             float b = Bs[k][tx];
+#pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * b;
         }
-        __syncthreads();
     }
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
         int r = r0 + ty + 8 * q, cc = c0 + tx;
         if (r < rows && cc < N) C[(size_t)r * N + cc] = acc[q];
@@ -458,23 +479,48 @@ __global__ void field_prep(const double* __restrict__ phi, const double* __restr
 }
 
 // ---------------------------------------------------------------- turn charge and accumulation
-// One block: Q_k (Eq. facecharge) from the current phi, the sample's
-// harmonics (Eq. fourier), the trapezoid of Eq. pcap and the power sums.
-__global__ void turn_sample(DevState* st, const double* phi, const int* ft, const int* fnb, const int* fk,
-                            const double* fc, int nfaces, int nt, double cs, double sn, double two_over_n,
-                            double inv_n, int n_rf) {
+// Per step, one kernel: every thread adds its node's current harmonics
+// (J_c += (2/N) cos(theta) J, J_s += (2/N) sin(theta) J, Eq. fourier, Kahan
+// FP64), and block 0 also takes the turn-charge sample: Q_k (Eq. facecharge)
+// from the current phi, its harmonics, the trapezoid of Eq. pcap and the
+// power sums, and advances the device step counter.
+struct SampleArgs {
+    DevState* st;
+    const double* phi;
+    const int* ft;
+    const int* fnb;
+    const int* fk;
+    const double* fc;
+    int nfaces, nt, n_rf;
+    double cs, sn, two_over_n, inv_n;   // phase of the sample (after the step)
+    const double* vol;
+    double *Jc, *Js, *Jcc, *Jsc;
+    int nn;
+    double wc, ws;                      // (2/N) cos, (2/N) sin of the step's phase
+};
+
+template <typename T>
+__global__ void sample_accumulate(SampleArgs a, const T* jm) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < a.nn) {
+        double J = (double)jm[n] / a.vol[n];
+        kahan_add(a.Jc[n], a.Jcc[n], a.wc * J);
+        kahan_add(a.Js[n], a.Jsc[n], a.ws * J);
+    }
+    if (blockIdx.x != 0) return;
     __shared__ double q[PP_MAX_TURNS];
     if (threadIdx.x < PP_MAX_TURNS) q[threadIdx.x] = 0;
     __syncthreads();
-    for (int f = threadIdx.x; f < nfaces; f += blockDim.x)
-        atomicAdd(&q[fk[f]], fc[f] * (phi[ft[f]] - phi[fnb[f]]));
+    for (int f = threadIdx.x; f < a.nfaces; f += blockDim.x)
+        atomicAdd(&q[a.fk[f]], a.fc[f] * (a.phi[a.ft[f]] - a.phi[a.fnb[f]]));
     __syncthreads();
     if (threadIdx.x != 0) return;
-    for (int k = 0; k < nt; ++k) {
-        double V = turn_target(st, nullptr, k, nt, cs, sn);
+    DevState* st = a.st;
+    for (int k = 0; k < a.nt; ++k) {
+        double V = turn_target(st, nullptr, k, a.nt, a.cs, a.sn);
         double Q = q[k];
-        kahan_add(st->qc[k], st->qc_c[k], two_over_n * Q * cs);
-        kahan_add(st->qs[k], st->qs_c[k], two_over_n * Q * sn);
+        kahan_add(st->qc[k], st->qc_c[k], a.two_over_n * Q * a.cs);
+        kahan_add(st->qs[k], st->qs_c[k], a.two_over_n * Q * a.sn);
         if (st->n_samples == 0) {
             st->v_first[k] = V;
             st->q_first[k] = Q;
@@ -486,21 +532,10 @@ __global__ void turn_sample(DevState* st, const double* phi, const int* ft, cons
     }
     st->n_samples += 1;
     st->step += 1;
-    kahan_add(st->p_ind, st->p_ind_c, st->p_ind_step * inv_n);
-    kahan_add(st->p_es, st->p_es_c, st->p_es_step * inv_n);
+    kahan_add(st->p_ind, st->p_ind_c, st->p_ind_step * a.inv_n);
+    kahan_add(st->p_es, st->p_es_c, st->p_es_step * a.inv_n);
     st->p_ind_step = 0;
     st->p_es_step = 0;
-}
-
-// J_c += (2/N) cos(theta) J, J_s += (2/N) sin(theta) J over the plasma nodes
-template <typename T>
-__global__ void accumulate_nodes(const T* jm, const double* vol, double* Jc, double* Js, double* Jcc,
-                                 double* Jsc, int nn, double wc, double ws) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
-    double J = (double)jm[n] / vol[n];
-    kahan_add(Jc[n], Jcc[n], wc * J);
-    kahan_add(Js[n], Jsc[n], ws * J);
 }
 
 // ---------------------------------------------------------------- Helmholtz glue
@@ -594,20 +629,34 @@ void launch_compose(Cell* c, bool from_new, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- launchers
-void launch_turn_sample(Cell* c, double cs, double sn, cudaStream_t st) {
-    turn_sample<<<1, 256, 0, st>>>(c->d_st, c->d_phi, c->d_face_t, c->d_face_nb, c->d_face_k, c->d_face_c,
-                                   c->nfaces, c->nturns, cs, sn, 2.0 / c->n_rf, 1.0 / c->n_rf, c->n_rf);
-    count_launch();
-}
-
-void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st) {
-    int nn = (c->i_win + 1) * c->NR;
+void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, double ws, cudaStream_t st) {
+    SampleArgs a;
+    a.st = c->d_st;
+    a.phi = c->d_phi;
+    a.ft = c->d_face_t;
+    a.fnb = c->d_face_nb;
+    a.fk = c->d_face_k;
+    a.fc = c->d_face_c;
+    a.nfaces = c->nfaces;
+    a.nt = c->nturns;
+    a.n_rf = c->n_rf;
+    a.cs = cs_new;
+    a.sn = sn_new;
+    a.two_over_n = 2.0 / c->n_rf;
+    a.inv_n = 1.0 / c->n_rf;
+    a.vol = c->d_vol;
+    a.Jc = c->d_Jc;
+    a.Js = c->d_Js;
+    a.Jcc = c->d_Jc_c;
+    a.Jsc = c->d_Js_c;
+    a.nn = (c->i_win + 1) * c->NR;
+    a.wc = wc;
+    a.ws = ws;
+    const unsigned nb = (unsigned)((a.nn + 255) / 256);
     if (c->fp64)
-        accumulate_nodes<double><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm64, c->d_vol, c->d_Jc, c->d_Js,
-                                                                   c->d_Jc_c, c->d_Js_c, nn, wc, ws);
+        sample_accumulate<double><<<nb, 256, 0, st>>>(a, c->d_jm64);
     else
-        accumulate_nodes<float><<<(nn + 255) / 256, 256, 0, st>>>(c->d_jm, c->d_vol, c->d_Jc, c->d_Js, c->d_Jc_c,
-                                                                  c->d_Js_c, nn, wc, ws);
+        sample_accumulate<float><<<nb, 256, 0, st>>>(a, c->d_jm);
     count_launch();
 }
 
@@ -670,9 +719,10 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)
-        gemm_check<<<ggrd, gblk, 0, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, rows, M, M, dst, it, c->cfg.poisson_tol, done);
+        gemm_sweep<true><<<ggrd, gblk, 0, st>>>(c->d_r32, c->ps.Vf, c->ps.t0, rows, M, M, dst, it, c->cfg.poisson_tol,
+                                                done);
         launch_pcr(c, c->ps.t0, c->ps.t1, st, done);
-        gemm_rm<float><<<ggrd, gblk, 0, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, M, done);
+        gemm_sweep<false><<<ggrd, gblk, 0, st>>>(c->ps.t1, c->ps.Vb, c->ps.t0, rows, M, M, dst, it, 0.0, done);
         poisson_update_zt<<<(nint + 255) / 256, 256, 0, st>>>(c->d_phi, c->ps.t0, c->d_Zt, c->d_Ginv, c->d_tn_int, K,
                                                                c->ntn_pad, rows, M, c->NR, c->d_turn_mask, done);
         count_launch(4);

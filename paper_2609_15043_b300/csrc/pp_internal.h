@@ -285,8 +285,7 @@ void launch_deposit_only(Cell* c, cudaStream_t st);
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
                    const double* d_targets);
 void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st);
-void launch_turn_sample(Cell* c, double cs_new, double sn_new, cudaStream_t st);
-void launch_accumulate(Cell* c, double wc, double ws, cudaStream_t st);
+void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, double ws, cudaStream_t st);
 void period_end(Cell* c, cudaStream_t st);
 template <typename T>
 void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, const int* skip);

@@ -86,7 +86,7 @@ class CellConfig:
     seed: int = 20260915
     plain_fp64: int = 0            # 1: the plain FP64 particle form (comparison baseline)
     capacity_factor: float = 1.5
-    sort_every_e: int = 4
+    sort_every_e: int = 8
     sort_every_i: int = 50
 
     def replace(self, **kw):
