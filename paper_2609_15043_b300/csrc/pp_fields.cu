@@ -449,13 +449,16 @@ __global__ void poisson_update(double* phi, const float* d0, const float* Z, con
 template <typename T>
 __global__ void field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
                            const double* __restrict__ Ess, const double* __restrict__ B, T* F, T* rho, T* jm,
+                           int* sched,
                            int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
                            double sn, int magnetic) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (i_win + 1) * NR) return;
-    // the step's deposits land on node rows 0..i_win only: clear them here
+    // the step's deposits land on node rows 0..i_win only: clear them here;
+    // and restart the particle kernel's chunk counter
     rho[n] = T(0);
     jm[n] = T(0);
+    if (n == 0) *sched = 0;
     int i = n / NR, j = n % NR;
     double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
     double Er;
@@ -664,12 +667,12 @@ void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
     int n = (c->i_win + 1) * c->NR;
     if (c->fp64)
         field_prep<double><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64,
-                   c->d_rho64, c->d_jm64, c->NR,
+                   c->d_rho64, c->d_jm64, &c->d_st->push_chunk, c->NR,
                                                             c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                             c->cfg.magnetic_force);
     else
         field_prep<float><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F,
-                   c->d_rho, c->d_jm, c->NR,
+                   c->d_rho, c->d_jm, &c->d_st->push_chunk, c->NR,
                                                            c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
                                                            c->cfg.magnetic_force);
     count_launch();

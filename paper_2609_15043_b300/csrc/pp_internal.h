@@ -105,6 +105,7 @@ struct DevState {
     // Poisson refinement bookkeeping (per sweep: max|r|, max term scale)
     unsigned long long pnorm[2 * 16];
     int pdone;
+    int push_chunk;                          // next chunk of the particle kernel's dynamic schedule
     int piters;
     double prel;
 };

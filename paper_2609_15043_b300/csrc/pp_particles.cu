@@ -242,7 +242,15 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     unsigned cnt[3] = {0, 0, 0};
     uint32_t parity = 0;
 
-    for (int chunk = blockIdx.x; chunk < ce + ci; chunk += gridDim.x) {
+    // dynamic schedule: a block takes the next unprocessed chunk when it is
+    // done with its last (electron chunks first), which evens out the blocks'
+    // shares of cheap and expensive chunks
+    __shared__ int s_chunk;
+    for (;;) {
+        if (t == 0) s_chunk = atomicAdd(&a.st->push_chunk, 1);
+        __syncthreads();
+        const int chunk = s_chunk;
+        if (chunk >= ce + ci) break;
         const int sp = chunk < ce ? 0 : 1;
         const int base = (chunk - (sp ? ce : 0)) * kChunk;
         const int n = sp ? n1 : n0;
