@@ -445,40 +445,75 @@ __global__ void poisson_update(double* phi, const float* d0, const float* Z, con
 }
 
 // ---------------------------------------------------------------- node fields
-// per plasma cell 5 float4 (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10, 11)
+// Per plasma cell 5 x 4 values (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10,
+// 11).  A block takes a tile of 8 x 32 cells: its 9 x 33 nodes are evaluated
+// once into shared memory, then every thread writes its cell's 20 values
+// contiguously.
+constexpr int kFpRows = 8, kFpCols = 32;
+
 template <typename T>
-__global__ void field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
-                           const double* __restrict__ Ess, const double* __restrict__ B, T* F, T* rho, T* jm,
-                           int* sched,
-                           int NR, int nr, int i_win, int nnodes, double dz, double dr, double cs,
-                           double sn, int magnetic) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (i_win + 1) * NR) return;
-    // the step's deposits land on node rows 0..i_win only: clear them here;
-    // and restart the particle kernel's chunk counter
-    rho[n] = T(0);
-    jm[n] = T(0);
-    if (n == 0) *sched = 0;
-    int i = n / NR, j = n % NR;
-    double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
-    double Er;
-    if (j == 0) Er = 0.0;
-    else if (j == NR - 1) Er = -(phi[n] - phi[n - 1]) / dr;
-    else Er = -(phi[n + 1] - phi[n - 1]) / (2.0 * dr);
-    double Et = Ec[n] * cs - Ess[n] * sn;
-    double Br = 0.0, Bz = 0.0;
-    if (magnetic) {
-        Br = B[n] * cs + B[nnodes + n] * sn;
-        Bz = B[2 * nnodes + n] * cs + B[3 * nnodes + n] * sn;
+__device__ __forceinline__ void store_cell(T* dst, const T (&v)[20]) {
+#pragma unroll
+    for (int q = 0; q < 20; ++q) dst[q] = v[q];
+}
+template <>
+__device__ __forceinline__ void store_cell<float>(float* dst, const float (&v)[20]) {
+    float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
+                                                  const double* __restrict__ Ess, const double* __restrict__ B, T* F,
+                                                  T* rho, T* jm, int* sched, int NR, int nr, int i_win, int nnodes,
+                                                  double dz, double dr, double cs, double sn, int magnetic) {
+    __shared__ T s_v[(kFpRows + 1) * (kFpCols + 1)][5];
+    const int ci0 = blockIdx.y * kFpRows, cj0 = blockIdx.x * kFpCols;
+    const int t = threadIdx.x;
+    if (t == 0 && blockIdx.x == 0 && blockIdx.y == 0) *sched = 0;     // the particle kernel's chunk counter
+    for (int q = t; q < (kFpRows + 1) * (kFpCols + 1); q += blockDim.x) {
+        const int i = ci0 + q / (kFpCols + 1), j = cj0 + q % (kFpCols + 1);
+        if (i > i_win || j >= NR) continue;
+        const int n = i * NR + j;
+        // the step's deposits land on node rows 0..i_win only: clear them here
+        // (each node by the tile that holds it as a lower-left node, the last
+        // row and column by the tiles at the edge)
+        const bool own = (q / (kFpCols + 1) < kFpRows || i == i_win) && (q % (kFpCols + 1) < kFpCols || j == NR - 1);
+        if (own) {
+            rho[n] = T(0);
+            jm[n] = T(0);
+        }
+        double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
+        double Er;
+        if (j == 0) Er = 0.0;
+        else if (j == NR - 1) Er = -(phi[n] - phi[n - 1]) / dr;
+        else Er = -(phi[n + 1] - phi[n - 1]) / (2.0 * dr);
+        double Et = Ec[n] * cs - Ess[n] * sn;
+        double Br = 0.0, Bz = 0.0;
+        if (magnetic) {
+            Br = B[n] * cs + B[nnodes + n] * sn;
+            Bz = B[2 * nnodes + n] * cs + B[3 * nnodes + n] * sn;
+        }
+        s_v[q][0] = (T)Er;
+        s_v[q][1] = (T)Ez;
+        s_v[q][2] = (T)Et;
+        s_v[q][3] = (T)Br;
+        s_v[q][4] = (T)Bz;
     }
-    T v[5] = {(T)Er, (T)Ez, (T)Et, (T)Br, (T)Bz};
-    // node (i, j) is corner 00 of cell (i, j), 01 of (i, j-1), 10 of (i-1, j), 11 of (i-1, j-1)
-    for (int corner = 0; corner < 4; ++corner) {
-        int ci = i - (corner >> 1), cj = j - (corner & 1);
-        if (ci < 0 || cj < 0 || ci >= i_win || cj >= nr) continue;
-        int cell = ci * nr + cj;
-        for (int comp = 0; comp < 5; ++comp) F[((size_t)cell * 5 + comp) * 4 + corner] = v[comp];
-    }
+    __syncthreads();
+    const int li = t / kFpCols, lj = t % kFpCols;
+    const int ci = ci0 + li, cj = cj0 + lj;
+    if (li >= kFpRows || ci >= i_win || cj >= nr) return;
+    T v[20];
+    // corners 00, 01, 10, 11 = nodes (ci, cj), (ci, cj+1), (ci+1, cj), (ci+1, cj+1)
+    const int q00 = li * (kFpCols + 1) + lj;
+    const int qs[4] = {q00, q00 + 1, q00 + kFpCols + 1, q00 + kFpCols + 2};
+#pragma unroll
+    for (int comp = 0; comp < 5; ++comp)
+#pragma unroll
+        for (int corner = 0; corner < 4; ++corner) v[comp * 4 + corner] = s_v[qs[corner]][comp];
+    store_cell<T>(F + ((size_t)ci * nr + cj) * 20, v);
 }
 
 // ---------------------------------------------------------------- turn charge and accumulation
@@ -664,17 +699,15 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
 }
 
 void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
-    int n = (c->i_win + 1) * c->NR;
+    dim3 grid((c->nr + kFpCols - 1) / kFpCols, (c->i_win + kFpRows - 1) / kFpRows);
     if (c->fp64)
-        field_prep<double><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64,
-                   c->d_rho64, c->d_jm64, &c->d_st->push_chunk, c->NR,
-                                                            c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
-                                                            c->cfg.magnetic_force);
+        field_prep<double><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64, c->d_rho64, c->d_jm64,
+                                                 &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
+                                                 cs, sn, c->cfg.magnetic_force);
     else
-        field_prep<float><<<(n + 255) / 256, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F,
-                   c->d_rho, c->d_jm, &c->d_st->push_chunk, c->NR,
-                                                           c->nr, c->i_win, c->nnodes, c->dz, c->dr, cs, sn,
-                                                           c->cfg.magnetic_force);
+        field_prep<float><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->d_rho, c->d_jm,
+                                                &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
+                                                cs, sn, c->cfg.magnetic_force);
     count_launch();
 }
 

@@ -614,6 +614,22 @@ __global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next
         val[q] = (uint16_t)q;
     }
     __syncthreads();
+    if (n_ev <= 256) {
+        // few events (the usual case): a parent has at most one ionisation per
+        // step, so the keys are distinct and an event's rank is the number of
+        // smaller keys -- one pass instead of the sorting network
+        int rank = 0;
+        uint32_t kq = 0;
+        const int q = threadIdx.x;
+        if (q < n_ev) {
+            kq = key[q];
+            for (int j = 0; j < n_ev; ++j) rank += key[j] < kq ? 1 : 0;
+        }
+        __syncthreads();
+        if (q < n_ev) val[rank] = (uint16_t)q;
+        __syncthreads();
+        P2 = 0;                          // skip the network below
+    }
     for (int k = 2; k <= P2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int q = threadIdx.x; q < P2; q += blockDim.x) {
