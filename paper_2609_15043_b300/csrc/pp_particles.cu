@@ -115,24 +115,36 @@ __device__ __forceinline__ void dep_run(DepAcc& a, const Tile& t, int iz, int ir
     }
 }
 
-// charge deposit at the new positions: particles that left the accumulated
-// cell add their own values directly and leave the accumulator in place
-__device__ __forceinline__ void dep_home(DepAcc& a, const Tile& t, int iz, int ir, float v0, float v1, float v2,
-                                         float v3) {
-    if (a.iz < 0) {
+// charge deposit at the new positions: slot a holds the first cell (the
+// "home" cell most particles stay in), slot b the last other cell, so strays
+// that land in the same neighbour accumulate too; a third cell evicts b
+__device__ __forceinline__ void dep_home(DepAcc& a, DepAcc& b, const Tile& t, int iz, int ir, float v0, float v1,
+                                         float v2, float v3) {
+    if (iz == a.iz && ir == a.ir) {
+        a.v0 += v0;
+        a.v1 += v1;
+        a.v2 += v2;
+        a.v3 += v3;
+    } else if (iz == b.iz && ir == b.ir) {
+        b.v0 += v0;
+        b.v1 += v1;
+        b.v2 += v2;
+        b.v3 += v3;
+    } else if (a.iz < 0) {
         a.iz = iz;
         a.ir = ir;
         a.v0 = v0;
         a.v1 = v1;
         a.v2 = v2;
         a.v3 = v3;
-    } else if (iz == a.iz && ir == a.ir) {
-        a.v0 += v0;
-        a.v1 += v1;
-        a.v2 += v2;
-        a.v3 += v3;
     } else {
-        tile_add4(t, iz, ir, v0, v1, v2, v3);
+        if (b.iz >= 0) tile_add4(t, b.iz, b.ir, b.v0, b.v1, b.v2, b.v3);
+        b.iz = iz;
+        b.ir = ir;
+        b.v0 = v0;
+        b.v1 = v1;
+        b.v2 = v2;
+        b.v3 = v3;
     }
 }
 
@@ -316,6 +328,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         // ---- phase A: thread-contiguous push
         DepAcc dj{-1, 0, 0.f, 0.f, 0.f, 0.f};
         DepAcc dq{-1, 0, 0.f, 0.f, 0.f, 0.f};
+        DepAcc dq2{-1, 0, 0.f, 0.f, 0.f, 0.f};
         uint32_t fcell = kDead;
         float4 f0, f1, f2, f3, f4;
         // thread t owns particles t*kPPT .. t*kPPT + kPPT-1 and visits them
@@ -425,7 +438,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             if (alive) {
                 ncell = (uint32_t)(iz2 * nr + ir2);
                 float wa2 = one - drn, wb2 = one - dzn;
-                dep_home(dq, tq, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
+                dep_home(dq, dq2, tq, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
                          S.qw * (drn * dzn));
                 // null-collision test; candidates are processed densely below
                 uint32_t r = philox2x32_10(s_uid[p], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
@@ -445,6 +458,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             s_vz[p] = vnz;
         }
         dep_flush_warp(dj, tj);
+        if (dq2.iz >= 0) tile_add4(tq, dq2.iz, dq2.ir, dq2.v0, dq2.v1, dq2.v2, dq2.v3);
         dep_flush_warp(dq, tq);
         __syncthreads();
         // ---- phase B: collisions of the candidates
