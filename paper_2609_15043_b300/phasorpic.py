@@ -165,7 +165,7 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data) if a is not None else None
 
 
-def make_config(cfg, capacity=None, weight=None, poisson_max_iter=3, poisson_tol=1e-10):
+def make_config(cfg, capacity=None, weight=None, poisson_max_iter=2, poisson_tol=1e-10):
     """pp_config from a workloads.CellConfig."""
     c = PPConfig()
     c.nr, c.nz = cfg.nr, cfg.nz
