@@ -85,7 +85,8 @@ static void one_step(Cell* c, cudaStream_t st) {
     int64_t s = c->s;
     double th = theta(c, s), th1 = theta(c, s + 1);
     phase_mark(c, PH_OTHER, true, st);
-    launch_field_prep(c, std::cos(th), std::sin(th), st);     // also clears rho and jm
+    // also clears rho and jm and imposes the turn potentials of theta_{s+1}
+    launch_field_prep(c, std::cos(th), std::sin(th), std::cos(th1), std::sin(th1), st);
     phase_mark(c, PH_OTHER, false, st);
     phase_mark(c, PH_PUSH, true, st);
     if (c->fp64)
@@ -97,7 +98,7 @@ static void one_step(Cell* c, cudaStream_t st) {
     launch_append(c, st);
     phase_mark(c, PH_OTHER, false, st);
     phase_mark(c, PH_POISSON, true, st);
-    poisson_refine(c, std::cos(th1), std::sin(th1), st, false, nullptr);
+    poisson_refine(c, std::cos(th1), std::sin(th1), st, false, nullptr, true);
     phase_mark(c, PH_POISSON, false, st);
     phase_mark(c, PH_OTHER, true, st);
     double two_n = 2.0 / c->n_rf;

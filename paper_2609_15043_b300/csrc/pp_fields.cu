@@ -445,6 +445,16 @@ __global__ void poisson_update(double* phi, const float* d0, const float* Z, con
 }
 
 // ---------------------------------------------------------------- node fields
+// what the step's field preparation imposes for the following Poisson solve
+struct TurnSet {
+    double* phi;
+    const int* tn_node;
+    const int* tn_k;
+    int K, nt;
+    DevState* st;
+    double cs, sn;
+};
+
 // Per plasma cell 5 x 4 values (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10,
 // 11).  A block takes a tile of 8 x 32 cells: its 9 x 33 nodes are evaluated
 // once into shared memory, then every thread writes its cell's 20 values
@@ -467,11 +477,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi, const double* __restrict__ Ec,
                                                   const double* __restrict__ Ess, const double* __restrict__ B, T* F,
                                                   T* rho, T* jm, int* sched, int NR, int nr, int i_win, int nnodes,
-                                                  double dz, double dr, double cs, double sn, int magnetic) {
+                                                  double dz, double dr, double cs, double sn, int magnetic,
+                                                  TurnSet ts) {
     __shared__ T s_v[(kFpRows + 1) * (kFpCols + 1)][5];
     const int ci0 = blockIdx.y * kFpRows, cj0 = blockIdx.x * kFpCols;
     const int t = threadIdx.x;
-    if (t == 0 && blockIdx.x == 0 && blockIdx.y == 0) *sched = 0;     // the particle kernel's chunk counter
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        if (t == 0) *sched = 0;     // the particle kernel's chunk counter
+        // the step's Poisson solve: turn potentials at the next phase (the
+        // coil nodes lie above the rows read here; set-up checks it) and
+        // fresh refinement bookkeeping
+        for (int q = t; q < ts.K; q += blockDim.x)
+            ts.phi[ts.tn_node[q]] = turn_target(ts.st, nullptr, ts.tn_k[q], ts.nt, ts.cs, ts.sn);
+        if (t < 2 * 16) ts.st->pnorm[t] = 0ull;
+        if (t == 0) ts.st->pdone = 0;
+    }
     for (int q = t; q < (kFpRows + 1) * (kFpCols + 1); q += blockDim.x) {
         const int i = ci0 + q / (kFpCols + 1), j = cj0 + q % (kFpCols + 1);
         if (i > i_win || j >= NR) continue;
@@ -535,6 +555,9 @@ struct SampleArgs {
     double *Jc, *Js, *Jcc, *Jsc;
     int nn;
     double wc, ws;                      // (2/N) cos, (2/N) sin of the step's phase
+    int* done;                          // the step's Poisson solve: final convergence decision
+    int sweep;
+    double tol;
 };
 
 template <typename T>
@@ -546,6 +569,16 @@ __global__ void sample_accumulate(SampleArgs a, const T* jm) {
         kahan_add(a.Js[n], a.Jsc[n], a.ws * J);
     }
     if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0 && !*a.done) {
+        DevState* s0 = a.st;
+        double r = __longlong_as_double((long long)s0->pnorm[2 * a.sweep]);
+        double sc = __longlong_as_double((long long)s0->pnorm[2 * a.sweep + 1]);
+        double rel = (sc > 0) ? r / sc : 0.0;
+        s0->prel = rel;
+        s0->piters = a.sweep;
+        if (rel <= a.tol) *a.done = 1;
+        else s0->status |= PP_ST_NOCONV;
+    }
     __shared__ double q[PP_MAX_TURNS];
     if (threadIdx.x < PP_MAX_TURNS) q[threadIdx.x] = 0;
     __syncthreads();
@@ -690,6 +723,9 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
     a.nn = (c->i_win + 1) * c->NR;
     a.wc = wc;
     a.ws = ws;
+    a.done = &c->d_st->pdone;
+    a.sweep = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
+    a.tol = c->cfg.poisson_tol;
     const unsigned nb = (unsigned)((a.nn + 255) / 256);
     if (c->fp64)
         sample_accumulate<double><<<nb, 256, 0, st>>>(a, c->d_jm64);
@@ -698,21 +734,22 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
     count_launch();
 }
 
-void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st) {
+void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_next, cudaStream_t st) {
     dim3 grid((c->nr + kFpCols - 1) / kFpCols, (c->i_win + kFpRows - 1) / kFpRows);
+    TurnSet ts{c->d_phi, c->d_tn_node, c->d_tn_k, c->ntn, c->nturns, c->d_st, cs_next, sn_next};
     if (c->fp64)
         field_prep<double><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64, c->d_rho64, c->d_jm64,
                                                  &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
-                                                 cs, sn, c->cfg.magnetic_force);
+                                                 cs, sn, c->cfg.magnetic_force, ts);
     else
         field_prep<float><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->d_rho, c->d_jm,
                                                 &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
-                                                cs, sn, c->cfg.magnetic_force);
+                                                cs, sn, c->cfg.magnetic_force, ts);
     count_launch();
 }
 
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
-                   const double* d_targets) {
+                   const double* d_targets, bool in_step) {
     int rows = c->ps.rows, M = c->ps.M;
     int nint = rows * M;
     int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
@@ -741,17 +778,21 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     a.cs = cs;
     a.sn = sn;
     const int K = c->ntn;
-    poisson_set_turns<<<(K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K, dst,
-                                                                           ext, c->nturns, cs, sn);
-    count_launch();
+    if (!in_step) {
+        poisson_set_turns<<<(K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st>>>(c->d_phi, c->d_tn_node, c->d_tn_k, K,
+                                                                               dst, ext, c->nturns, cs, sn);
+        count_launch();
+    }
     dim3 gblk(32, 8), ggrd((M + 31) / 32, (rows + 31) / 32);
     for (int it = 0; it <= maxit; ++it) {
         a.norm = &dst->pnorm[2 * it];
         poisson_residual<<<(nint + 255) / 256, 256, 0, st>>>(a);
         count_launch();
         if (it == maxit) {
-            poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, done, 1);
-            count_launch();
+            if (!in_step) {
+                poisson_check<<<1, 32, 0, st>>>(dst, it, c->cfg.poisson_tol, done, 1);
+                count_launch();
+            }
             break;
         }
         // d0 = Vb-transform of the per-mode z solves of (r Vf)

@@ -276,15 +276,18 @@ enum { PH_PUSH = 0, PH_POISSON, PH_SORT, PH_OTHER, PH_PERIOD, PH_N };
 int setup_cell(Cell* c);
 
 // ---------------------------------------------------------------- launchers
-void launch_field_prep(Cell* c, double cs, double sn, cudaStream_t st);
+void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_next, cudaStream_t st);
 void launch_push(Cell* c, cudaStream_t st);
 void launch_push_plain(Cell* c, cudaStream_t st);
 void push_prepare(Cell* c);
 void launch_append(Cell* c, cudaStream_t st);
 void launch_sort(Cell* c, int sp, cudaStream_t st);
 void launch_deposit_only(Cell* c, cudaStream_t st);
+// in_step: the step's field preparation already imposed the turn potentials
+// and cleared the bookkeeping, and the step's sample kernel takes the final
+// convergence decision
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
-                   const double* d_targets);
+                   const double* d_targets, bool in_step = false);
 void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st);
 void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, double ws, cudaStream_t st);
 void period_end(Cell* c, cudaStream_t st);

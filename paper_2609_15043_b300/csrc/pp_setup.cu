@@ -286,6 +286,10 @@ int setup_cell(Cell* c) {
         }
     c->ntn = (int)tn_node.size();
     if (c->ntn > kMaxCapNodes) return fail("too many turn nodes for the capacitance correction");
+    // the step's field preparation imposes the turn potentials while it reads
+    // the potential of node rows 0..i_win+1: the coil must lie above them
+    for (int n : tn_node)
+        if (n / NR <= c->i_win + 1) return fail("coil turn nodes must lie above the first row over the window");
     if (NR - 1 > 512) return fail("nr exceeds the radial unknowns supported by the Poisson solver");
     std::vector<signed char> mask(c->nnodes, -1);
     for (int t = 0; t < c->ntn; ++t) mask[tn_node[t]] = (signed char)tn_k[t];

@@ -1,0 +1,69 @@
+"""Parity at the benchmark size (128x192 cells, 4e6 macroparticles per
+species) in the launch configuration the benchmark times: the persistent
+particle kernel with its dynamic chunk schedule over the full population, and
+the field solves on the full grid, each against the oracle on the same
+seeded inputs."""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cell60_inputs():
+    from paper_2609_15043_b300 import workloads
+    cfg = workloads.cell60()
+    return cfg, [workloads.population(cfg, sp) for sp in (0, 1)]
+
+
+def test_vacuum_impedance_at_bench_size(cell60_inputs):
+    require_gpu()
+    cfg, _ = cell60_inputs
+    from oracle.cell import OracleCell
+    from paper_2609_15043_b300 import phasorpic as pp
+    oc = OracleCell(cfg, [1.0, 1.0])
+    g = pp.Cell(cfg)
+    Z, eps_rec, _ = g.vacuum_impedance()
+    assert np.max(np.abs(Z - oc.zvac)) <= 1e-9 * np.max(np.abs(oc.zvac))
+    for k in range(len(cfg.turn_r)):
+        U = g.grid(pp.GRID_U0 + k)
+        assert np.max(np.abs(U - oc.U[k])) <= 1e-9 * np.max(np.abs(oc.U[k]))
+    g.close()
+
+
+def test_one_step_parity_at_bench_size(cell60_inputs):
+    """One PIC step of all 8e6 macroparticles from the oracle's potential:
+    cells, uids, absorptions and collision counts bit-exact, float32 state
+    within 2e-5, deposited charge and current within 1e-6 of the total."""
+    require_gpu()
+    from paper_2609_15043_b300 import phasorpic as pp
+    cfg, pops = cell60_inputs
+    oc = oracle_cell(cfg, pops)
+    oc.prime(np.float32)
+    g = gpu_cell(cfg, pops)
+    g.set_potential(oc.phi)
+    info = oc.step(np.float32)
+    g.advance_steps(1)
+    cnt = g.counters()
+    assert cnt["particle_steps"] == info["stats"]["pushed"]
+    assert cnt["absorbed"] == info["stats"]["absorbed"]
+    assert cnt["created"] == info["events"]
+    assert [cnt["e_elastic"], cnt["e_excitation"], cnt["e_ionisation"]] == list(info["stats"]["coll"][0])
+    assert [cnt["i_cx"], cnt["i_isotropic"]] == list(info["stats"]["coll"][1][:2])
+    for sp in (0, 1):
+        pg = by_uid(g.get_particles(sp))
+        po = oracle_live(oc.P[sp])
+        assert np.array_equal(pg["uid"], po["uid"].astype(np.uint32))
+        assert np.array_equal(pg["cell"], po["cell"].astype(np.uint32))
+        for k in ("dr", "dz"):
+            assert np.max(np.abs(pg[k] - po[k])) <= 2e-5
+        for k in ("vr", "vt", "vz"):
+            scale = np.maximum(np.abs(po[k]), 1e-3 * np.max(np.abs(po[k])))
+            assert np.max(np.abs(pg[k] - po[k]) / scale) <= 2e-5
+    q = g.grid(pp.GRID_CHARGE)
+    assert np.max(np.abs(q - info["Q"])) <= 1e-6 * np.sum(np.abs(info["Q"]))
+    j = g.grid(pp.GRID_JMOM)
+    assert np.max(np.abs(j - info["J"])) <= 1e-6 * np.sum(np.abs(info["J"]))
+    g.close()
