@@ -36,7 +36,7 @@ constexpr int kChunk = kPushThreads * kPPT;
 constexpr int kTileRows = 8;                      // node rows of the shared deposit tile
 constexpr int kMaxNR = 513;                       // node columns supported by the tile
 constexpr int kEventCap = 8192;                   // ionisation events per step
-constexpr int kMaxCapNodes = 64;                  // turn nodes handled by the capacitance matrix
+constexpr int kMaxCapNodes = 128;                 // turn nodes handled by the capacitance matrix
 constexpr int kMaxPcrLevels = 10;                 // cyclic reduction of z systems of up to 1024 rows
 
 // ---------------------------------------------------------------- particles
