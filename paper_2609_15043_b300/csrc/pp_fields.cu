@@ -376,21 +376,27 @@ __global__ void poisson_update_zt(double* phi, const float* d0, const float* __r
     if (*done) return;
     __shared__ double s_r[kMaxCapNodes];
     __shared__ double s_sig[kMaxCapNodes + 4];
+    // the thread's own unknown is read first, so its latency overlaps sigma's
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = idx < rows * M;
+    const int n = act ? (idx / M + 1) * NR + idx % M : 0;
+    const bool free_node = act && turn_mask[n] < 0;
+    double d = free_node ? (double)d0[idx] : 0.0;
     for (int q = threadIdx.x; q < K; q += blockDim.x) s_r[q] = -(double)d0[tn_int[q]];
+    for (int q = K + threadIdx.x; q < Kp; q += blockDim.x) s_sig[q] = 0.0;
     __syncthreads();
-    for (int q = threadIdx.x; q < Kp; q += blockDim.x) {
-        double sg = 0;
-        if (q < K)
-            for (int u = 0; u < K; ++u) sg += Ginv[q * K + u] * s_r[u];
-        s_sig[q] = sg;
+    // sigma = G^-1 s_r: one warp per row, lanes across the row (independent loads)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = warp; q < K; q += nw) {
+        double part = 0.0;
+        for (int u = lane; u < K; u += 32) part += Ginv[q * K + u] * s_r[u];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_sig[q] = part;
     }
     __syncthreads();
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * M) return;
-    int n = (idx / M + 1) * NR + idx % M;
-    if (turn_mask[n] >= 0) return;
-    double d = (double)d0[idx];
+    if (!free_node) return;
     const float4* z = reinterpret_cast<const float4*>(Zt + (size_t)idx * Kp);
+#pragma unroll 4
     for (int t = 0; t < Kp / 4; ++t) {
         float4 v = z[t];
         d += s_sig[4 * t] * (double)v.x + s_sig[4 * t + 1] * (double)v.y + s_sig[4 * t + 2] * (double)v.z +
