@@ -395,14 +395,17 @@ __global__ void poisson_update_zt(double* phi, const float* d0, const float* __r
     }
     __syncthreads();
     if (!free_node) return;
+    // Z sigma in FP32: it corrects the FP32 inner solve, whose error the FP64
+    // residual of the next sweep measures anyway (FP64 rate is low on B300)
     const float4* z = reinterpret_cast<const float4*>(Zt + (size_t)idx * Kp);
+    float zc = 0.f;
 #pragma unroll 4
     for (int t = 0; t < Kp / 4; ++t) {
         float4 v = z[t];
-        d += s_sig[4 * t] * (double)v.x + s_sig[4 * t + 1] * (double)v.y + s_sig[4 * t + 2] * (double)v.z +
-             s_sig[4 * t + 3] * (double)v.w;
+        zc += (float)s_sig[4 * t] * v.x + (float)s_sig[4 * t + 1] * v.y + (float)s_sig[4 * t + 2] * v.z +
+              (float)s_sig[4 * t + 3] * v.w;
     }
-    phi[n] += d;
+    phi[n] += d + (double)zc;
 }
 
 // phi += d0 + Z sigma with sigma = G^-1 (-d0_T) computed by every block
