@@ -69,3 +69,20 @@ def test_config_validation_phase_closure():
     cfg = workloads.small().replace(dt=1.0 / (400.5 * 13.56e6))
     with pytest.raises(pp.PhasorPICError, match="phase closure"):
         pp.Cell(cfg)
+
+
+@pytest.mark.parametrize("change, message", [
+    (dict(nr=600), "nr exceeds"),
+    (dict(nz=1200, n_init=10), "nz exceeds"),
+    (dict(plain_fp64=2), "plain_fp64"),
+    (dict(z_coil=0.128), "coil turn nodes must lie above"),
+    (dict(nr=128, nz=192, turn_r=[0.05], winding=[1], wire_radius=0.008), "too many turn nodes"),
+])
+def test_config_validation_limits(change, message):
+    """Sizes and placements the kernels do not support are refused at
+    pp_init_cell, before any device work."""
+    from paper_2609_15043_b300 import phasorpic as pp
+    from paper_2609_15043_b300 import workloads
+    cfg = workloads.small().replace(**change)
+    with pytest.raises(pp.PhasorPICError, match=message):
+        pp.Cell(cfg)

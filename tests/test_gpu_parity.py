@@ -44,7 +44,7 @@ def test_vacuum_impedance_and_unit_fields(small_inputs):
     g.close()
 
 
-@pytest.mark.parametrize("workload", ["small", "cell60"])
+@pytest.mark.parametrize("workload", ["small", "cell60", "cell100"])
 def test_poisson_solve(workload):
     """Eq. poisson (chi = 0) with the dielectric window and equipotential
     turns: FP32 separable solves inside FP64 residual refinement vs the
