@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cell60")
+    ap.add_argument("--cfg", action="append", default=[], metavar="KEY=VALUE",
+                    help="override a field of the workload's configuration (repeatable), e.g. density=1e15")
     ap.add_argument("--cpu-steps", type=int, default=1, help="PIC steps of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -84,9 +86,10 @@ def reduce_over_ranks(ms, psteps, dist):
 
 def workload_desc(cfg, name):
     return ("%s: %dx%d cells over r<=%.2f m, z<=%.2f m, %d macroparticles/species, %d turns, Ar %.0f mTorr, "
-            "dt=T/%d%s" % (name, cfg.nr, cfg.nz, cfg.r_max, cfg.z_max, cfg.n_init, len(cfg.turn_r),
-                           cfg.pressure_pa / 133.322368 * 1e3, round(1 / (cfg.freq * cfg.dt)),
-                           (", controller target %.0f W" % cfg.p_target) if cfg.power_control else ""))
+            "dt=T/%d, n0=%.0e m^-3%s" % (name, cfg.nr, cfg.nz, cfg.r_max, cfg.z_max, cfg.n_init, len(cfg.turn_r),
+                                          cfg.pressure_pa / 133.322368 * 1e3, round(1 / (cfg.freq * cfg.dt)),
+                                          cfg.density,
+                                          (", controller target %.0f W" % cfg.p_target) if cfg.power_control else ""))
 
 
 # ---------------------------------------------------------------- clocks
@@ -517,6 +520,13 @@ def main():
         run_batch(args, ws, rank, local)
         return
     cfg = workloads.WORKLOADS[args.workload if args.workload != "batch32" else "cell60"]()
+    if args.cfg:
+        over = {}
+        for kv in args.cfg:
+            k, v = kv.split("=", 1)
+            cur = getattr(cfg, k)
+            over[k] = type(cur)(float(v)) if isinstance(cur, (int, float)) else v
+        cfg = cfg.replace(**over)
     if args.impl == "reference":
         run_reference(args, cfg, ws, rank)
     elif args.time_to_stationary:
