@@ -343,7 +343,8 @@ def run_ours(args, cfg, ws, rank, local):
                        2 * cfg.n_init * 28 / 1e6),
                    "parallelism": "independent cell per GPU" if ws > 1 else "1 cell",
                    "form": args.form,
-                   "time_to_stationary": None},
+                   "time_to_stationary": None,
+                   "time_to_stationary_mode": "bench.py --time-to-stationary (minutes; not part of this run)"},
         "roofline": {"bound": "hbm", "kernel": "push_kernel" if args.form == "fused" else "push_plain",
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
