@@ -1,7 +1,8 @@
 """Training of the learned circuit proposal (offline tooling; the network runs
 on the device through pp_ml_configure / pp_mlp_forward).
 
-  python -m paper_2609_15043_b300.mlp_train collect --out pairs.npz [--cells 16 --periods 150 --n-init 250000]
+  python -m paper_2609_15043_b300.mlp_train collect --out pairs.npz [--cells 16 --periods 150 --n-init 250000
+                                                   --density 1e16 --p-min 20 --p-max 150]
   python -m paper_2609_15043_b300.mlp_train train --pairs pairs.npz --out weights.npz [--epochs 300]
 
 collect: runs a batch of cells shaped like the 128x192 workload (seeds and
@@ -36,8 +37,9 @@ def collect(args):
     import torch
     from . import phasorpic as pp, workloads
     rng = np.random.default_rng(args.seed)
-    base = workloads.cell60()
-    cfgs = [base.replace(n_init=args.n_init, seed=args.seed + 101 * i, p_target=float(rng.uniform(20.0, 150.0)))
+    base = workloads.cell60().replace(density=args.density, capacity_factor=args.capacity_factor)
+    cfgs = [base.replace(n_init=args.n_init, seed=args.seed + 101 * i,
+                         p_target=float(rng.uniform(args.p_min, args.p_max)))
             for i in range(args.cells)]
     batch = pp.Batch(cfgs)
     for c, cfg in zip(batch.cells, cfgs):
@@ -159,6 +161,10 @@ def main():
     c.add_argument("--periods", type=int, default=150)
     c.add_argument("--n-init", type=int, default=250000)
     c.add_argument("--seed", type=int, default=7)
+    c.add_argument("--density", type=float, default=1e16, help="initial plasma density (m^-3)")
+    c.add_argument("--p-min", type=float, default=20.0, help="controller targets drawn in [p-min, p-max] W")
+    c.add_argument("--p-max", type=float, default=150.0)
+    c.add_argument("--capacity-factor", type=float, default=1.5)
     t = sub.add_parser("train")
     t.add_argument("--pairs", required=True)
     t.add_argument("--out", required=True)
