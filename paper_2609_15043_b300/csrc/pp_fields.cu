@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi
 // ---------------------------------------------------------------- turn charge and accumulation
 // Per step, one kernel: every thread adds its node's current harmonics
 // (J_c += (2/N) cos(theta) J, J_s += (2/N) sin(theta) J, Eq. fourier, Kahan
-// FP64), and block 0 also takes the turn-charge sample: Q_k (Eq. facecharge)
+// FP64), and one extra block takes the turn-charge sample: Q_k (Eq. facecharge)
 // from the current phi, its harmonics, the trapezoid of Eq. pcap and the
 // power sums, and advances the device step counter.
 struct SampleArgs {
@@ -571,13 +571,17 @@ struct SampleArgs {
 
 template <typename T>
 __global__ void sample_accumulate(SampleArgs a, const T* jm) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < a.nn) {
-        double J = (double)jm[n] / a.vol[n];
-        kahan_add(a.Jc[n], a.Jcc[n], a.wc * J);
-        kahan_add(a.Js[n], a.Jsc[n], a.ws * J);
+    // the last block takes the turn-charge sample alone, so its serial part
+    // runs beside the node work of the other blocks
+    if (blockIdx.x + 1 < gridDim.x) {
+        int n = blockIdx.x * blockDim.x + threadIdx.x;
+        if (n < a.nn) {
+            double J = (double)jm[n] / a.vol[n];
+            kahan_add(a.Jc[n], a.Jcc[n], a.wc * J);
+            kahan_add(a.Js[n], a.Jsc[n], a.ws * J);
+        }
+        return;
     }
-    if (blockIdx.x != 0) return;
     if (threadIdx.x == 0 && !*a.done) {
         DevState* s0 = a.st;
         double r = __longlong_as_double((long long)s0->pnorm[2 * a.sweep]);
@@ -735,7 +739,7 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
     a.done = &c->d_st->pdone;
     a.sweep = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
     a.tol = c->cfg.poisson_tol;
-    const unsigned nb = (unsigned)((a.nn + 255) / 256);
+    const unsigned nb = (unsigned)((a.nn + 255) / 256) + 1;     // + the sample block
     if (c->fp64)
         sample_accumulate<double><<<nb, 256, 0, st>>>(a, c->d_jm64);
     else
