@@ -246,6 +246,61 @@ int pp_get_ml_features(pp_cell* cell, double* out, int cap, int* n, void* stream
  * harmonic accumulators and applied state (enqueued on `stream`). */
 int pp_ml_features_now(pp_cell* cell, void* stream);
 
+/*
+ * Training of the proposal network on the device (the network of pp_mlp):
+ * minibatch Adam on the mean squared error
+ *     L = sum over the batch rows r and used outputs o of (y_ro - t_ro)^2 / (B n_out)
+ * of standardised targets t, with FP32 master weights.  Every product runs on
+ * the tensor cores with BF16 operands and FP32 accumulation: the forward pass
+ * is that of pp_mlp_forward (BF16 weights, inputs and hidden activations), and
+ * the backward products take BF16 copies of the layer gradients; the ReLU
+ * derivative is 1 where the (BF16) activation is > 0.  Bias gradients sum the
+ * FP32 gradients.  Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), then weights (not
+ * biases) p -= lr weight_decay p.  The trainer owns its device memory and a
+ * stream of its own; every call below is synchronous.
+ */
+typedef struct pp_trainer pp_trainer;
+typedef struct pp_train_opts {
+    int32_t n_in;                    /* used input columns, 1..256 */
+    int32_t n_out;                   /* used outputs, 1..32 */
+    int32_t batch;                   /* rows per step, 1..4096 (padded to a multiple of 128 on the device) */
+    int32_t reserved0;
+    double lr, beta1, beta2, eps, weight_decay;
+} pp_train_opts;
+
+/* pp_trainer_create -- w[l]: FP32 [out][in] initial weights (256x256 x3, 32x256),
+ * b[l]: biases (256 x3, 32); copied.  PP_E_ARG on bad options. */
+int pp_trainer_create(const pp_train_opts* opts, const float* const* w, const float* const* b, pp_trainer** out);
+
+/* pp_trainer_load -- the resident training set: x (rows x n_in) standardised
+ * features, y (rows x n_out) standardised targets, host FP32 row-major; the
+ * features are stored as BF16.  Replaces the previous set. */
+int pp_trainer_load(pp_trainer* t, const float* x, const float* y, int rows);
+
+/* pp_trainer_gradients -- loss and gradients (FP32, layouts of w and b) of
+ * the n <= batch loaded rows idx[0..n); no update.  PP_E_ARG if an index is
+ * outside the loaded rows. */
+int pp_trainer_gradients(pp_trainer* t, const int32_t* idx, int n, float* const* gw, float* const* gb,
+                         double* loss);
+
+/* pp_trainer_epoch -- one Adam step per consecutive batch of order[0..n)
+ * (the last one may be short); *mean_loss = the steps' summed squared error
+ * over n n_out. */
+int pp_trainer_epoch(pp_trainer* t, const int32_t* order, int n, double* mean_loss);
+
+/* pp_trainer_evaluate -- *mse = the loss over rows idx[0..n) (any n), no update. */
+int pp_trainer_evaluate(pp_trainer* t, const int32_t* idx, int n, double* mse);
+
+/* pp_trainer_params -- current FP32 master weights, their BF16 bit patterns
+ * (the pp_mlp weights) and the biases; any array pointer may be NULL. */
+int pp_trainer_params(pp_trainer* t, float* const* w, uint16_t* const* wbits, float* const* b);
+
+/* pp_trainer_steps -- Adam steps taken (-1 for NULL). */
+int64_t pp_trainer_steps(pp_trainer* t);
+
+int pp_trainer_destroy(pp_trainer* t);
+
 /* pp_get_particles64 -- as pp_get_particles with the state in double (exact
  * for the plain FP64 form, widened from float otherwise). */
 int pp_get_particles64(pp_cell* cell, int species, int64_t cap, int64_t* n, uint32_t* cell_idx,

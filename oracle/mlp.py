@@ -28,6 +28,16 @@ FP64) accumulation, biases in FP32; a linear output layer of 32 rows of which
 the first 4N are the standardised loads (Re V_p,k, Im V_p,k for every k, then
 Re I_cap,k, Im I_cap,k).  Weights are BF16, stored [out][in].
 
+Training (the network's fit to pairs the method generates): mean squared
+error L = sum_r sum_{o < n_out} (y_ro - t_ro)^2 / (B n_out) over a batch of B
+standardised rows; its gradient by the chain rule through the layers, with
+the derivative of ReLU taken as 1 where the (BF16) activation is positive and
+each BF16 rounding passed through as the identity.  In the device's
+arithmetic the backward products take BF16 copies of the layer gradients
+(round_grad); bias gradients sum the unrounded ones.  Adam (Kingma and Ba,
+2015) with bias-corrected moments, then decoupled weight decay on the
+weights.
+
 Acceptance: the error of a prediction against the measured loads uses the
 scaled norm of Eq. t7error with voltages scaled by |V_g| and currents by
 |I_f| of the applied state.  The noise level after period n is the RMS of the
@@ -183,3 +193,56 @@ class Gate:
         self.prev = np.asarray(loads, float).copy()
         self.pred = None if pred_next is None else np.asarray(pred_next, float).copy()
         return use, err, tau
+
+
+def train_loss_grads(w, b, x_std, t_std, rounding=True, round_grad=True):
+    """Loss and gradients of one batch (module docstring).  w: 4 weight arrays
+    [out][in] (256x256 x3, 32x256, the FP32 master values), b: 4 bias arrays,
+    x_std: B x n_in standardised features, t_std: B x n_out standardised
+    targets.  rounding=True is the device's network (weights, inputs and
+    hidden activations rounded to BF16; with round_grad the backward products
+    take BF16 copies of the layer gradients); rounding=False is the plain
+    FP64 network.  Returns (loss, gw, gb) with gw[l] shaped like w[l]."""
+    x_std = np.asarray(x_std, np.float64)
+    t_std = np.asarray(t_std, np.float64)
+    B, n_in = x_std.shape
+    n_out = t_std.shape[1]
+
+    def rnd(a):
+        return bf16_round(np.asarray(a, np.float32)).astype(np.float64) if rounding else np.asarray(a, np.float64)
+
+    W = [rnd(wl) for wl in w]
+    bias = [np.asarray(bl, np.float64) for bl in b]
+    h = np.zeros((B, WIDTH))
+    h[:, :n_in] = rnd(np.asarray(x_std, np.float32)) if rounding else x_std
+    hs = [h]
+    for layer in range(3):
+        hs.append(rnd(np.maximum(hs[-1] @ W[layer].T + bias[layer], 0.0)))
+    y = hs[3] @ W[3].T + bias[3]
+    d = np.zeros((B, N_OUT_PAD))
+    d[:, :n_out] = y[:, :n_out] - t_std
+    loss = float(np.sum(d * d) / (B * n_out))
+    G = 2.0 * d / (B * n_out)
+    gw, gb = [None] * 4, [None] * 4
+    for layer in (3, 2, 1, 0):
+        Gq = rnd(G) if (rounding and round_grad) else G
+        gw[layer] = Gq.T @ hs[layer]
+        gb[layer] = G.sum(axis=0)
+        if layer > 0:
+            G = (Gq @ W[layer]) * (hs[layer] > 0)
+    return loss, gw, gb
+
+
+def adam_update(p, g, m, v, t, lr, beta1, beta2, eps, weight_decay=0.0, decay=True):
+    """One Adam step of parameter array p with gradient g and moments m, v
+    (step count t after this step); returns the new (p, m, v).  decay applies
+    the decoupled weight decay p -= lr weight_decay p after the step."""
+    p, g = np.asarray(p, np.float64), np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    p = p - lr * m_hat / (np.sqrt(v_hat) + eps)
+    if decay:
+        p = p - lr * weight_decay * p
+    return p, m, v

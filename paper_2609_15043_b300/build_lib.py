@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasorpic.so")
-SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu", "pp_period.cu"]
+SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu", "pp_mlp_train.cu", "pp_period.cu"]
 
 
 def nvcc():

@@ -11,6 +11,7 @@
 // warps then read their 32 TMEM lanes (rows) with tcgen05.ld, add the bias,
 // apply ReLU, round to BF16 and write the next layer's A operand in place.
 #include "pp_internal.h"
+#include "pp_tc.cuh"
 
 #include <cuda_bf16.h>
 
@@ -34,45 +35,11 @@ struct MlpSmem {
     uint32_t tmem_base;
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
-// offsets in 16-byte units, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// instruction descriptor of kind::f16: D f32, A and B bf16, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// byte offset of element (row, k) of a K-major no-swizzle operand whose
-// stride-dimension extent is `rows`.  Core matrices (8 rows x 16 bytes) are
-// grouped per MMA K-step (16 elements): within a step the two K-halves of a
-// row group are adjacent (leading byte offset 128) and row groups follow at
-// 256 bytes (stride byte offset); a step occupies rows * 32 bytes.
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
-    return (uint32_t)((((k >> 4) * (rows >> 3) * 2 + (row >> 3) * 2 + ((k >> 3) & 1)) << 7) + ((row & 7) << 4) +
-                      ((k & 7) << 1));
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    uint32_t a = smem_addr(bar);
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
+using tc::smem_addr;
+using tc::sdesc;
+using tc::idesc_bf16;
+using tc::kmajor_off;
+using tc::mbar_wait_bounded;
 
 // load `rows_n` rows of BF16 weights [out][in] (in = 256) into the K-major B operand
 __device__ void load_weights(MlpSmem& s, const uint16_t* w, int rows_n, const float* bias) {

@@ -3,14 +3,16 @@ on the device through pp_ml_configure / pp_mlp_forward).
 
   python -m paper_2609_15043_b300.mlp_train collect --out pairs.npz [--cells 16 --periods 150 --n-init 250000
                                                    --density 1e16 --p-min 20 --p-max 150]
-  python -m paper_2609_15043_b300.mlp_train train --pairs pairs.npz --out weights.npz [--epochs 300]
+  python -m paper_2609_15043_b300.mlp_train train --pairs pairs.npz --out weights.npz [--epochs 300 --device gpu]
 
 collect: runs a batch of cells shaped like the 128x192 workload (seeds and
 controller targets varied, fewer macroparticles per cell) with feature
 collection on, and stores the pairs (features after period n, measured loads
 of period n+1).  train: fits the 3x256 ReLU network to the standardised loads
-with Adam on mean squared error (float32 master weights, numpy), then rounds
-the weights to BF16 for the device.
+with Adam on mean squared error on the device (pp_trainer_*: FP32 master
+weights, BF16 tensor-core products), keeps the weights of the best
+validation epoch and stores their BF16 patterns; `--device cpu` runs the same
+fit in numpy (FP32 throughout) instead.
 """
 import argparse
 import math
@@ -47,20 +49,81 @@ def collect(args):
             c.set_particles(sp, workloads.population(cfg, sp))
         c.ml_configure(None, collect=True)
     sh = torch.cuda.current_stream().cuda_stream
-    feats = [[] for _ in cfgs]
-    loads = [[] for _ in cfgs]
-    for period in range(args.periods):
-        batch.advance_period(1, sh)
-        for i, c in enumerate(batch.cells):
-            feats[i].append(c.ml_features())
-            loads[i].append(_loads(c.turn_phasors()))
-        if period % 25 == 0:
-            print("period", period, file=sys.stderr, flush=True)
-    X = np.concatenate([np.asarray(f[:-1]) for f in feats])
-    Y = np.concatenate([np.asarray(l[1:]) for l in loads])
+    X, Y = run_and_collect(batch, args.periods, sh, log_every=25)
     np.savez(args.out, X=X, Y=Y, n_turns=len(base.turn_r), cells=args.cells, periods=args.periods)
     batch.close()
     print("pairs", X.shape, Y.shape)
+
+
+def run_and_collect(batch, periods, stream=None, log_every=0):
+    """Advances a Batch whose cells collect features (Cell.ml_configure) by
+    `periods` periods; returns the pairs X (features after period n) and Y
+    (measured loads of period n+1) of all cells."""
+    feats = [[] for _ in batch.cells]
+    loads = [[] for _ in batch.cells]
+    for period in range(periods):
+        batch.advance_period(1, stream)
+        for i, c in enumerate(batch.cells):
+            feats[i].append(c.ml_features())
+            loads[i].append(_loads(c.turn_phasors()))
+        if log_every and period % log_every == 0:
+            print("period", period, file=sys.stderr, flush=True)
+    X = np.concatenate([np.asarray(f[:-1]) for f in feats])
+    Y = np.concatenate([np.asarray(l[1:]) for l in loads])
+    return X, Y
+
+
+def standardise(X, Y):
+    """Means and scales of the features and loads and the standardised
+    float32 arrays.  A constant feature keeps scale 1 (it standardises to 0).
+    A load that never varied in the pairs gets scale 0: it is predicted by
+    its mean whatever the network outputs (its standardised target is 0).
+    With scale 1 instead, the fit's small absolute error on such an output
+    (V_p of a particle-free cell, exactly 0) would be an error in volts
+    beside the much smaller scaled currents of the acceptance norm."""
+    X, Y = np.asarray(X, np.float64), np.asarray(Y, np.float64)
+    mu_in, sig_in = X.mean(0), X.std(0)
+    sig_in[sig_in < 1e-12] = 1.0
+    mu_out, sig_out = Y.mean(0), Y.std(0)
+    const = sig_out == 0.0
+    Yn = (Y - mu_out) / np.where(const, 1.0, sig_out)
+    return (mu_in, sig_in, mu_out, np.where(const, 0.0, sig_out), ((X - mu_in) / sig_in).astype(np.float32),
+            Yn.astype(np.float32))
+
+
+def fit_device(X, Y, epochs=300, batch=256, lr=1e-3, weight_decay=1e-2, seed=7, log_every=50):
+    """Fits the network to pairs on the device (pp_trainer_*); 10 % of the
+    pairs are held out and the weights of the best validation epoch are
+    kept.  Returns (params for Cell.ml_configure / phasorpic.mlp_forward,
+    info dict with the validation history)."""
+    from . import phasorpic as pp
+    mu_in, sig_in, mu_out, sig_out, Xn, Yn = standardise(X, Y)
+    n_in, n_out = Xn.shape[1], Yn.shape[1]
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(Xn))
+    n_val = max(len(Xn) // 10, 1)
+    val, tr = perm[:n_val], perm[n_val:]
+    W, b = _init(rng, n_in, n_out)
+    T = pp.Trainer(n_in, n_out, W, b, batch=min(batch, 4096), lr=lr, weight_decay=weight_decay)
+    try:
+        T.load(Xn, Yn)
+        best = (float("inf"), None, -1)
+        hist = []
+        for epoch in range(epochs):
+            train_loss = T.epoch(rng.permutation(tr))
+            mse = T.evaluate(val)
+            hist.append((train_loss, mse))
+            if mse < best[0]:
+                best = (mse, T.params(), epoch)
+            if log_every and (epoch % log_every == 0 or epoch == epochs - 1):
+                print("epoch %d  train %.4g  validation mse (standardised) %.4g" % (epoch, train_loss, mse),
+                      file=sys.stderr, flush=True)
+        steps = T.steps
+    finally:
+        T.close()
+    p = best[1]
+    params = dict(w=p["w"], b=p["b"], mu_in=mu_in, sig_in=sig_in, mu_out=mu_out, sig_out=sig_out)
+    return params, dict(best_epoch=best[2], best_mse=best[0], history=hist, steps=steps)
 
 
 def _init(rng, n_in, n_out):
@@ -81,17 +144,33 @@ def _forward(W, b, x):
 
 
 def train(args):
+    if getattr(args, "device", "gpu") == "gpu":
+        d = np.load(args.pairs)
+        params, info = fit_device(d["X"], d["Y"], epochs=args.epochs, batch=args.batch, lr=args.lr,
+                                  weight_decay=args.weight_decay, seed=args.seed)
+        print("best epoch %d  validation mse %.4g  (%d device steps)" % (info["best_epoch"], info["best_mse"],
+                                                                        info["steps"]), file=sys.stderr, flush=True)
+        save_params(args.out, params)
+        print("saved", args.out)
+        return
+    _train_numpy(args)
+
+
+def save_params(path, p):
+    np.savez(path, w0=p["w"][0], w1=p["w"][1], w2=p["w"][2], w3=p["w"][3], b0=p["b"][0], b1=p["b"][1],
+             b2=p["b"][2], b3=p["b"][3], mu_in=p["mu_in"], sig_in=p["sig_in"], mu_out=p["mu_out"],
+             sig_out=p["sig_out"])
+
+
+def _train_numpy(args):
     d = np.load(args.pairs)
     X, Y = d["X"].astype(np.float64), d["Y"].astype(np.float64)
     n_in, n_out = X.shape[1], Y.shape[1]
-    mu_in, sig_in = X.mean(0), X.std(0)
-    sig_in[sig_in < 1e-12] = 1.0
-    mu_out, sig_out = Y.mean(0), Y.std(0)
-    sig_out[sig_out < 1e-30] = 1.0
+    mu_in, sig_in, mu_out, sig_out, xs, ys = standardise(X, Y)
     Xn = np.zeros((len(X), WIDTH), np.float32)
-    Xn[:, :n_in] = ((X - mu_in) / sig_in).astype(np.float32)
+    Xn[:, :n_in] = xs
     Yn = np.zeros((len(Y), OUT_PAD), np.float32)
-    Yn[:, :n_out] = ((Y - mu_out) / sig_out).astype(np.float32)
+    Yn[:, :n_out] = ys
     rng = np.random.default_rng(args.seed)
     perm = rng.permutation(len(X))
     n_val = max(len(X) // 10, 1)
@@ -173,6 +252,8 @@ def main():
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=7)
     t.add_argument("--weight-decay", type=float, default=1e-2)
+    t.add_argument("--device", choices=("gpu", "cpu"), default="gpu",
+                   help="gpu: pp_trainer_* on the tensor cores; cpu: the same fit in numpy")
     a = ap.parse_args()
     collect(a) if a.cmd == "collect" else train(a)
 

@@ -36,7 +36,9 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
            "pp_poisson_solve_noalloc", "pp_checkpoint", "pp_restore", "pp_get_particles64",
            "pp_init_batch", "pp_batch_size", "pp_batch_cell", "pp_batch_advance_period", "pp_batch_destroy",
-           "pp_mlp_forward", "pp_ml_configure", "pp_get_ml_features", "pp_ml_features_now"]
+           "pp_mlp_forward", "pp_ml_configure", "pp_get_ml_features", "pp_ml_features_now",
+           "pp_trainer_create", "pp_trainer_load", "pp_trainer_gradients", "pp_trainer_epoch",
+           "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -92,6 +94,12 @@ class PPRecord(C.Structure):
     ]
 
 
+class PPTrainOpts(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_out", C.c_int32), ("batch", C.c_int32), ("reserved0", C.c_int32),
+                ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("weight_decay", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libphasorpic.so is not built (run paper_2609_15043_b300/build_lib.py); "
@@ -138,6 +146,14 @@ def _load():
         "pp_batch_advance_period": (I, [V, I, V]),
         "pp_batch_destroy": (I, [V]),
         "pp_restore": (I, [V, V, C.c_uint64]),
+        "pp_trainer_create": (I, [P(PPTrainOpts), V, V, P(V)]),
+        "pp_trainer_load": (I, [V, V, V, I]),
+        "pp_trainer_gradients": (I, [V, V, I, V, V, P(D)]),
+        "pp_trainer_epoch": (I, [V, V, I, P(D)]),
+        "pp_trainer_evaluate": (I, [V, V, I, P(D)]),
+        "pp_trainer_params": (I, [V, V, V, V]),
+        "pp_trainer_steps": (C.c_int64, [V]),
+        "pp_trainer_destroy": (I, [V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +253,83 @@ def mlp_forward(params, feats):
     out = np.zeros((f.shape[0], m.n_out))
     _check(lib.pp_mlp_forward(C.byref(m), _ptr(f), f.shape[0], _ptr(out)), "pp_mlp_forward")
     return out
+
+
+_LAYER_ROWS = (256, 256, 256, 32)
+
+
+def _ptr_array(arrays):
+    return (C.c_void_p * 4)(*[a.ctypes.data for a in arrays])
+
+
+class Trainer:
+    """pp_trainer_*: training of the proposal network on the device.  w, b:
+    initial FP32 weights [out][in] (256x256 x3, 32x256) and biases."""
+
+    def __init__(self, n_in, n_out, w, b, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                 weight_decay=0.0):
+        o = PPTrainOpts(n_in=n_in, n_out=n_out, batch=batch, reserved0=0, lr=lr, beta1=beta1, beta2=beta2,
+                        eps=eps, weight_decay=weight_decay)
+        self.n_in, self.n_out, self.batch = n_in, n_out, batch
+        w = [np.ascontiguousarray(x, np.float32) for x in w]
+        b = [np.ascontiguousarray(x, np.float32) for x in b]
+        for l in range(4):
+            if w[l].shape != (_LAYER_ROWS[l], 256) or b[l].shape != (_LAYER_ROWS[l],):
+                raise ValueError("layer %d must be (%d, 256) with %d biases" % (l, _LAYER_ROWS[l], _LAYER_ROWS[l]))
+        h = C.c_void_p()
+        _check(lib.pp_trainer_create(C.byref(o), _ptr_array(w), _ptr_array(b), C.byref(h)), "pp_trainer_create")
+        self.h = h
+
+    def load(self, x, y):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        if x.ndim != 2 or x.shape[1] != self.n_in or y.shape != (x.shape[0], self.n_out):
+            raise ValueError("x must be rows x n_in and y rows x n_out")
+        _check(lib.pp_trainer_load(self.h, _ptr(x), _ptr(y), x.shape[0]), "pp_trainer_load")
+        self.rows = x.shape[0]
+
+    def gradients(self, idx):
+        idx = np.ascontiguousarray(idx, np.int32)
+        gw = [np.zeros((r, 256), np.float32) for r in _LAYER_ROWS]
+        gb = [np.zeros(r, np.float32) for r in _LAYER_ROWS]
+        loss = C.c_double()
+        _check(lib.pp_trainer_gradients(self.h, _ptr(idx), len(idx), _ptr_array(gw), _ptr_array(gb),
+                                        C.byref(loss)), "pp_trainer_gradients")
+        return loss.value, gw, gb
+
+    def epoch(self, order):
+        order = np.ascontiguousarray(order, np.int32)
+        loss = C.c_double()
+        _check(lib.pp_trainer_epoch(self.h, _ptr(order), len(order), C.byref(loss)), "pp_trainer_epoch")
+        return loss.value
+
+    def evaluate(self, idx):
+        idx = np.ascontiguousarray(idx, np.int32)
+        mse = C.c_double()
+        _check(lib.pp_trainer_evaluate(self.h, _ptr(idx), len(idx), C.byref(mse)), "pp_trainer_evaluate")
+        return mse.value
+
+    def params(self):
+        w = [np.zeros((r, 256), np.float32) for r in _LAYER_ROWS]
+        wb = [np.zeros((r, 256), np.uint16) for r in _LAYER_ROWS]
+        b = [np.zeros(r, np.float32) for r in _LAYER_ROWS]
+        _check(lib.pp_trainer_params(self.h, _ptr_array(w), _ptr_array(wb), _ptr_array(b)), "pp_trainer_params")
+        return dict(w_master=w, w=wb, b=b)
+
+    @property
+    def steps(self):
+        return int(lib.pp_trainer_steps(self.h))
+
+    def close(self):
+        if self.h:
+            _check(lib.pp_trainer_destroy(self.h), "pp_trainer_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Cell:

@@ -1,4 +1,4 @@
-"""The offline trainer of the proposal network (numpy, CPU): it fits a
+"""The numpy form of the proposal network's trainer (`--device cpu`): it fits a
 learnable synthetic map, and its exported BF16 model evaluated by the
 oracle's forward pass reproduces the map."""
 import numpy as np
@@ -23,6 +23,7 @@ def test_trainer_fits_a_smooth_map(tmp_path):
         lr = 2e-3
         seed = 1
         weight_decay = 0.0
+        device = "cpu"
     mlp_train.train(A_)
     p = mlp_train.load_params(A_.out)
     assert [w.shape for w in p["w"]] == [(256, 256)] * 3 + [(32, 256)]
