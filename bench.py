@@ -59,6 +59,10 @@ def parse():
                     help="proposal network (mlp_train output): adds a fused-FP32 run with the proposal active")
     ap.add_argument("--alpha-ml", type=float, default=1.0)
     ap.add_argument("--forms", default="fused,fp64", help="time-to-stationary runs (fused, fp64, fused_ml)")
+    ap.add_argument("--mlp-train", action="store_true",
+                    help="time the device training of the proposal network (context, not the step metric)")
+    ap.add_argument("--mlp-pairs", type=int, default=100000)
+    ap.add_argument("--mlp-batch", type=int, default=4096)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only prime the cell and run this many PIC steps, untimed (a short target for ncu)")
     return ap.parse_args()
@@ -518,10 +522,63 @@ def run_stationary(args, cfg, local):
     print(json.dumps(line), flush=True)
 
 
+# FLOPs of one training step per batch row: forward (3 x 256 x 256 + 32 x 256 MACs), the
+# weight gradients (the same), the input gradients of layers 3, 2, 1 (32 x 256 + 2 x 256 x 256)
+MLP_TRAIN_FLOP_PER_ROW = 2 * (2 * (3 * 256 * 256 + 32 * 256) + (32 * 256 + 2 * 256 * 256))
+
+
+def run_mlp_train(args):
+    """Device training of the proposal network on synthetic standardised
+    pairs shaped like the 128x192 cell's (206 features, 12 loads): epochs of
+    pp_trainer_epoch (one Adam step per batch), wall time around the
+    synchronous call."""
+    import numpy as np
+    import torch
+    from paper_2609_15043_b300 import phasorpic as pp, mlp_train
+    rng = np.random.default_rng(1)
+    n_in, n_out, n = 206, 12, args.mlp_pairs
+    x = rng.standard_normal((n, n_in)).astype(np.float32)
+    y = np.tanh(x @ (rng.standard_normal((n_in, n_out)) / np.sqrt(n_in))).astype(np.float32)
+    W, b = mlp_train._init(rng, n_in, n_out)
+    T = pp.Trainer(n_in, n_out, W, b, batch=args.mlp_batch, lr=1e-3)
+    T.load(x, y)
+    torch.cuda.synchronize()
+    order = rng.permutation(n)
+    for _ in range(args.warmup):
+        T.epoch(order)
+    l0 = pp.launch_count()
+    s0 = T.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss = T.epoch(order)
+    dt = time.perf_counter() - t0
+    steps = T.steps - s0
+    launches = pp.launch_count() - l0
+    T.close()
+    flops = MLP_TRAIN_FLOP_PER_ROW * n * args.steps
+    tf = flops / dt / 1e12
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops")
+    line = {"metric": "proposal network training (context)", "value": tf, "unit": "TFLOP/s",
+            "higher_is_better": True, "epochs": args.steps, "warmup": args.warmup, "adam_steps": steps,
+            "ms_per_adam_step": 1e3 * dt / steps, "pairs_per_s": n * args.steps / dt, "last_epoch_loss": loss,
+            "gpu_launches": launches, "dtype": "bf16 operands, f32 accumulate and master weights",
+            "data": "synthetic", "timing": "wall time around synchronous pp_trainer_epoch calls",
+            "config": {"workload": "proposal training, %d pairs x 206 features -> 12 loads, batch %d"
+                       % (n, args.mlp_batch)},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (tf / peak) if peak else None, "traffic": None}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     from paper_2609_15043_b300 import workloads
+    if args.mlp_train and args.impl != "reference":
+        if rank == 0:
+            run_mlp_train(args)
+        return
     if args.workload == "batch32" and args.impl != "reference":
         run_batch(args, ws, rank, local)
         return

@@ -3,8 +3,12 @@
 // cores and FP32 accumulation in tensor memory, and an Adam update.
 //
 // Every product of a step is one tcgen05 GEMM D[M x N] = A[M x K] B[N x K]^T
-// with both operands K-major BF16 in global memory (a 128-row tile of D per
-// CTA, K staged through shared memory 64 at a time) and a fused epilogue:
+// with both operands K-major BF16 in global memory and a fused epilogue.  A CTA
+// owns a 128 x Nt tile of D (Nt = min(N, 128)) over a range of K (the weight
+// gradients, whose K is the batch, split K across CTAs and add their partial
+// tiles); K is staged through two shared-memory buffers 64 at a time with
+// cp.async, so the next slab loads while the tensor cores work on this one.
+// Epilogues:
 //   forward, hidden layer l:  H_{l+1} = bf16(relu(H_l W_l^T + b_l)), written
 //                             row-major and transposed;
 //   forward, output layer:    Y = H_3 W_3^T + b_3 (FP32);
@@ -63,10 +67,12 @@ struct GemmArgs {
     unsigned* status;
 };
 
+constexpr int kNt = 128;         // columns of D per CTA at most
+
 struct GemmSmem {
-    uint16_t a[kTile * kSlab];   // 16 KB
-    uint16_t b[kW * kSlab];      // 32 KB
-    uint64_t bar;
+    uint16_t a[2][kTile * kSlab];   // 2 x 16 KB
+    uint16_t b[2][kNt * kSlab];     // 2 x 16 KB
+    uint64_t bar[2];
     uint32_t tmem_base;
 };
 
@@ -85,12 +91,30 @@ __device__ __forceinline__ void store_row16(uint16_t* dst, const uint32_t (&pk)[
     d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// grid: (M / 128, N / Nt, K splits); K per split a multiple of 16
 __global__ void __launch_bounds__(128, 1) tr_gemm(GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     GemmSmem& s = *reinterpret_cast<GemmSmem*>(smraw);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int m0 = blockIdx.x * kTile;
-    const uint32_t ncols = g.N <= 32 ? 32u : 256u;
+    const int Nt = g.N < kNt ? g.N : kNt;
+    const int n0 = blockIdx.y * Nt;
+    // K splits on 16-element boundaries (K is a multiple of 16, splits <= K / 16)
+    const int units = g.K / 16;
+    const int u0 = (int)((long long)units * blockIdx.z / gridDim.z);
+    const int u1 = (int)((long long)units * (blockIdx.z + 1) / gridDim.z);
+    const int kbeg = 16 * u0, kc = 16 * (u1 - u0);
+    const int nslab = (kc + kSlab - 1) / kSlab;
+    const uint32_t ncols = Nt <= 32 ? 32u : (uint32_t)kNt;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_addr(
@@ -99,92 +123,145 @@ __global__ void __launch_bounds__(128, 1) tr_gemm(GemmArgs g) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) tc::mbar_init1(&s.bar);
+    if (t == 0) {
+        tc::mbar_init1(&s.bar[0]);
+        tc::mbar_init1(&s.bar[1]);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s.tmem_base;
-    uint32_t parity = 0;
-    bool ok = true;
 
-    for (int k0 = 0; k0 < g.K; k0 += kSlab) {
-        const int kn = min(kSlab, g.K - k0);           // a multiple of 16
-        const int pieces = kn / 8;                      // 16-byte pieces of a row
+    // slab i of this CTA's K range into buffer `buf` (16-byte pieces: 8 consecutive k of a row)
+    auto load_slab = [&](int i, int buf) {
+        const int k0 = kbeg + i * kSlab;
+        const int kn = min(kSlab, kbeg + kc - k0);
+        const int pieces = kn / 8;
         for (int q = t; q < kTile * pieces; q += blockDim.x) {
             const int r = q / pieces, k8 = (q % pieces) * 8;
-            uint4 v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + k8);
-            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(s.a) + tc::kmajor_off(r, k8, kTile)) = v;
+            cp_async16(reinterpret_cast<char*>(s.a[buf]) + tc::kmajor_off(r, k8, kTile),
+                       g.A + (size_t)(m0 + r) * g.lda + k0 + k8);
         }
-        for (int q = t; q < g.N * pieces; q += blockDim.x) {
+        for (int q = t; q < Nt * pieces; q += blockDim.x) {
             const int r = q / pieces, k8 = (q % pieces) * 8;
-            uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)r * g.ldb + k0 + k8);
-            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(s.b) + tc::kmajor_off(r, k8, g.N)) = v;
+            cp_async16(reinterpret_cast<char*>(s.b[buf]) + tc::kmajor_off(r, k8, Nt),
+                       g.B + (size_t)(n0 + r) * g.ldb + k0 + k8);
+        }
+        cp_async_commit();
+    };
+
+    // commits of slab i arrive on bar[i & 1]; each is waited once, in order
+    uint32_t phase[2] = {0u, 0u};
+    int waited = 0;
+    bool ok = true;
+    auto wait_slab = [&](int i) -> bool {
+        const int b = i & 1;
+        const bool done = __syncthreads_and(tc::mbar_wait_bounded(&s.bar[b], phase[b]) ? 1 : 0) != 0;
+        if (!done) {
+            // the products may still be in flight: one more bounded wait
+            // before shared memory or tensor memory is released
+            tc::mbar_wait_bounded(&s.bar[b], phase[b]);
+            __syncthreads();
+        }
+        phase[b] ^= 1u;
+        waited = i + 1;
+        return done;
+    };
+
+    load_slab(0, 0);
+    int issued = 0;
+    for (int i = 0; i < nslab; ++i) {
+        const int buf = i & 1;
+        if (i + 1 < nslab) {
+            // the other buffer held slab i - 1: its products must be complete
+            if (i >= 1 && !wait_slab(i - 1)) {
+                ok = false;
+                break;
+            }
+            load_slab(i + 1, buf ^ 1);
+            cp_async_wait<1>();              // slab i has landed
+        } else {
+            cp_async_wait<0>();
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ab = tc::smem_addr(s.a), bb = tc::smem_addr(s.b);
-            const uint32_t idesc = tc::idesc_bf16(kTile, g.N);
+            const int kn = min(kSlab, kbeg + kc - (kbeg + i * kSlab));
+            const uint32_t ab = tc::smem_addr(s.a[buf]), bb = tc::smem_addr(s.b[buf]);
+            const uint32_t idesc = tc::idesc_bf16(kTile, Nt);
 #pragma unroll 1
             for (int ks = 0; ks < kn / 16; ++ks) {
                 const uint64_t da = tc::sdesc(ab + (uint32_t)(ks * kTile * 32), 128, 256);
-                const uint64_t db = tc::sdesc(bb + (uint32_t)(ks * g.N * 32), 128, 256);
-                tc::mma_bf16(tmem, da, db, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
+                const uint64_t db = tc::sdesc(bb + (uint32_t)(ks * Nt * 32), 128, 256);
+                tc::mma_bf16(tmem, da, db, idesc, (i > 0 || ks > 0) ? 1u : 0u);
             }
-            tc::mma_commit(&s.bar);
+            tc::mma_commit(&s.bar[buf]);
         }
         __syncwarp();
-        // the slab's products must complete before the next slab overwrites
-        // shared memory (and before the epilogue reads the accumulator)
-        const bool done = __syncthreads_and(tc::mbar_wait_bounded(&s.bar, parity) ? 1 : 0) != 0;
-        if (!done) {
-            if (t == 0 && g.status) atomicOr(g.status, (unsigned)PP_ST_TIMEOUT);
-            tc::mbar_wait_bounded(&s.bar, parity);     // copies in flight: one more bounded wait
-            __syncthreads();
-            ok = false;
-            break;
-        }
-        parity ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issued = i + 1;
     }
+    // every commit is waited before the accumulator is read or the CTA exits
+    while (waited < issued) {
+        if (!wait_slab(waited)) {
+            if (ok && t == 0 && g.status) atomicOr(g.status, (unsigned)PP_ST_TIMEOUT);
+            ok = false;
+        }
+    }
+    if (!ok && t == 0 && g.status) atomicOr(g.status, (unsigned)PP_ST_TIMEOUT);
+    cp_async_wait<0>();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (ok) {
         // warp w reads TMEM lanes (rows of D) 32w .. 32w + 31
         const int m = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < g.N; c0 += 16) {
+        for (int c0 = 0; c0 < Nt; c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+            const int n = n0 + c0;
             if (g.epi == EPI_HIDDEN) {
                 uint32_t pk[8];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    float y = __uint_as_float(v[j]) + g.bias[c0 + j];
+                    float y = __uint_as_float(v[j]) + g.bias[n + j];
                     const uint16_t hb = bf16_bits(y > 0.f ? y : 0.f);
-                    g.outt[(size_t)(c0 + j) * g.ldot + m] = hb;
+                    g.outt[(size_t)(n + j) * g.ldot + m] = hb;
                     pk[j >> 1] = (j & 1) ? (pk[j >> 1] | ((uint32_t)hb << 16)) : (uint32_t)hb;
                 }
-                store_row16(g.outb + (size_t)m * g.ldob + c0, pk);
+                store_row16(g.outb + (size_t)m * g.ldob + n, pk);
             } else if (g.epi == EPI_OUT) {
+                float4* dst = reinterpret_cast<float4*>(g.out + (size_t)m * g.ldo + n);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) g.out[(size_t)m * g.ldo + c0 + j] = __uint_as_float(v[j]) + g.bias[c0 + j];
+                for (int j = 0; j < 4; ++j)
+                    dst[j] = make_float4(__uint_as_float(v[4 * j]) + g.bias[n + 4 * j],
+                                         __uint_as_float(v[4 * j + 1]) + g.bias[n + 4 * j + 1],
+                                         __uint_as_float(v[4 * j + 2]) + g.bias[n + 4 * j + 2],
+                                         __uint_as_float(v[4 * j + 3]) + g.bias[n + 4 * j + 3]);
             } else if (g.epi == EPI_DW) {
+                // partial sums of the K splits (the output is zeroed first)
 #pragma unroll
-                for (int j = 0; j < 16; ++j) g.out[(size_t)(c0 + j) * g.ldo + m] = __uint_as_float(v[j]);
+                for (int j = 0; j < 16; ++j) atomicAdd(&g.out[(size_t)(n + j) * g.ldo + m], __uint_as_float(v[j]));
             } else {
+                // the 16 mask activations of this row segment (32 bytes)
+                const uint4* mp = reinterpret_cast<const uint4*>(g.mask + (size_t)m * g.ldm + n);
+                const uint4 m0v = mp[0], m1v = mp[1];
+                const uint32_t mw[8] = {m0v.x, m0v.y, m0v.z, m0v.w, m1v.x, m1v.y, m1v.z, m1v.w};
                 uint32_t pk[8];
+                float gv[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const uint16_t h = g.mask[(size_t)m * g.ldm + c0 + j];
+                    const uint32_t h = (mw[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
                     const bool pass = (h & 0x8000u) == 0 && (h & 0x7FFFu) != 0;   // activation > 0
-                    const float gv = pass ? __uint_as_float(v[j]) : 0.f;
-                    g.out[(size_t)m * g.ldo + c0 + j] = gv;
-                    const uint16_t gb = bf16_bits(gv);
-                    g.outt[(size_t)(c0 + j) * g.ldot + m] = gb;
+                    gv[j] = pass ? __uint_as_float(v[j]) : 0.f;
+                    const uint16_t gb = bf16_bits(gv[j]);
+                    g.outt[(size_t)(n + j) * g.ldot + m] = gb;
                     pk[j >> 1] = (j & 1) ? (pk[j >> 1] | ((uint32_t)gb << 16)) : (uint32_t)gb;
                 }
-                store_row16(g.outb + (size_t)m * g.ldob + c0, pk);
+                float4* dst = reinterpret_cast<float4*>(g.out + (size_t)m * g.ldo + n);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[j] = make_float4(gv[4 * j], gv[4 * j + 1], gv[4 * j + 2], gv[4 * j + 3]);
+                store_row16(g.outb + (size_t)m * g.ldob + n, pk);
             }
         }
     }
@@ -366,8 +443,12 @@ struct Trainer {
     }
 };
 
-static void gemm(Trainer* T, const GemmArgs& g) {
-    tr_gemm<<<g.M / kTile, 128, kGemmSmem, T->st>>>(g);
+// one product; `splits` CTAs share K (the weight gradients only: their
+// epilogue adds partial tiles)
+static void gemm(Trainer* T, const GemmArgs& g, int splits = 1) {
+    const int nt = g.N < kNt ? g.N : kNt;
+    dim3 grid((unsigned)(g.M / kTile), (unsigned)(g.N / nt), (unsigned)splits);
+    tr_gemm<<<grid, 128, kGemmSmem, T->st>>>(g);
     count_launch();
 }
 
@@ -419,6 +500,9 @@ static void run_batch(Trainer* T, const int* idx, int B, int sse_slot, bool back
         count_launch();
     }
     if (!backward) return;
+    // the weight gradients accumulate partial tiles of their K splits
+    cudaMemsetAsync(T->Gr, 0, sizeof(float) * kNW, T->st);
+    const int splits = Bp >= 256 ? Bp / 256 : 1;     // about 256 batch rows (four slabs) per CTA
     int cur = 0;
     for (int l = 3; l >= 0; --l) {
         const int nl = rows_of(l);
@@ -426,7 +510,7 @@ static void run_batch(Trainer* T, const int* idx, int B, int sse_slot, bool back
             GemmArgs g = gemm_args(T, T->HT[l], Bp, T->GT[cur], Bp, kW, nl, Bp, EPI_DW);
             g.out = T->Gr + w_off(l);
             g.ldo = kW;
-            gemm(T, g);
+            gemm(T, g, splits);
         }
         tr_bias_grad<<<nl, 256, 0, T->st>>>(T->Gf[cur], Bp, nl, T->Gr + b_off(l));
         count_launch();

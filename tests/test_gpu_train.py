@@ -32,10 +32,60 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("batch", [300, 4096])
+def _exact_case(rng, batch, n_in, n_out):
+    """A network and batch whose every value and sum is exact in BF16 and
+    FP32: inputs +-1, three weights of +-1/2 per row, zero biases (hidden
+    values are multiples of 1/8 below 4, outputs below 8, and batch x n_out
+    is a power of two, so the output gradient 2 d / (B n_out) is dyadic with
+    a few significant bits, and every weight-gradient sum stays below 2^24
+    units of its last bit).  Both sides then take every ReLU decision and
+    every rounding identically, and the results are equal bit for bit."""
+    w = []
+    for layer, r in enumerate(ROWS):
+        W = np.zeros((r, 256), np.float32)
+        for o in range(r):
+            cols = rng.choice(n_in if layer == 0 else 256, 3, replace=False)
+            W[o, cols] = rng.choice([-0.5, 0.5], 3)
+        w.append(W)
+    b = [np.zeros(r, np.float32) for r in ROWS]
+    x = rng.choice([-1.0, 1.0], (batch, n_in)).astype(np.float32)
+    t = (rng.integers(-16, 17, (batch, n_out)) / 8.0).astype(np.float32)
+    return w, b, x, t
+
+
+@pytest.mark.parametrize("batch", [64, 512, 4096])
+def test_gradients_exact_arithmetic(batch):
+    """64 rows: one 128-row tile, half of it padding; 512 rows: two K splits
+    of the weight gradients; 4096: the largest batch (sixteen splits).  Every
+    index, transpose, mask and split-K sum of the device's products is pinned
+    here: the gradients and the loss equal the oracle's bit for bit."""
+    require_gpu()
+    from oracle import mlp
+    from paper_2609_15043_b300 import phasorpic as pp
+    rng = np.random.default_rng(batch)
+    n_in, n_out = 64, 8
+    w, b, x, t = _exact_case(rng, batch, n_in, n_out)
+    T = pp.Trainer(n_in, n_out, w, b, batch=batch)
+    T.load(x, t)
+    loss, gw, gb = T.gradients(np.arange(batch, dtype=np.int32))
+    T.close()
+    lo, gwo, gbo = mlp.train_loss_grads(w, b, x, t)
+    assert loss == lo
+    for layer in range(4):
+        assert np.count_nonzero(gwo[layer]) > 0
+        assert np.array_equal(gw[layer], gwo[layer]), layer
+        assert np.array_equal(gb[layer], gbo[layer]), layer
+
+
+@pytest.mark.parametrize("batch", [300, 1000, 4096])
 def test_gradients_match_oracle(batch):
-    """300 rows: three 128-row tiles, the last ragged; 4096 rows: the largest
-    batch (the weight-gradient products run 64 K-slabs)."""
+    """Random network and data (300 rows: three 128-row tiles, the last
+    ragged; 1000: four K splits; 4096: sixteen).  Ties make the tolerance: a
+    BF16 activation one unit apart between FP32 and FP64 accumulation moves
+    the next pre-activations by up to ~1e-4 of their scale, and a ReLU
+    decision that close to 0 is either value, moving one gradient element by
+    its full size; measured up to 3e-3 (normwise) on layer 0 of such
+    batches."""
     require_gpu()
     from oracle import mlp
     from paper_2609_15043_b300 import phasorpic as pp
@@ -52,10 +102,8 @@ def test_gradients_match_oracle(batch):
     assert loss == pytest.approx(lo, rel=1e-4)
     assert T.evaluate(idx) == pytest.approx(lo, rel=1e-4)
     for layer in range(4):
-        # same rounding points as the oracle: FP32 against FP64 accumulation,
-        # and the BF16 roundings that accumulation order flips
-        assert _rel(gw[layer], gwo[layer]) <= 3e-3, layer
-        assert _rel(gb[layer], gbo[layer]) <= 3e-3, layer
+        assert _rel(gw[layer], gwo[layer]) <= 1e-2, layer
+        assert _rel(gb[layer], gbo[layer]) <= 1e-2, layer
         # the exact gradient of the BF16 network: BF16 copies of the layer
         # gradients (relative 2^-9 per element) in the backward products
         assert _rel(gw[layer], gwe[layer]) <= 2e-2, layer
