@@ -59,6 +59,8 @@ def parse():
                     help="proposal network (mlp_train output): adds a fused-FP32 run with the proposal active")
     ap.add_argument("--alpha-ml", type=float, default=1.0)
     ap.add_argument("--forms", default="fused,fp64", help="time-to-stationary runs (fused, fp64, fused_ml)")
+    ap.add_argument("--autotune", type=int, default=0, metavar="TRIAL_PERIODS",
+                    help="run pp_autotune before the warm-up (0: keep the configured tuning)")
     ap.add_argument("--mlp-train", action="store_true",
                     help="time the device training of the proposal network (context, not the step metric)")
     ap.add_argument("--mlp-pairs", type=int, default=100000)
@@ -255,6 +257,16 @@ def run_ours(args, cfg, ws, rank, local):
     stream = torch.cuda.default_stream()
     sh = stream.cuda_stream
     cell.prime(sh)
+    if args.autotune:
+        # tuned on a copy of the workload, so the measured cell starts from
+        # the same state as without tuning
+        tcell = pp.Cell(cfg)
+        for sp in (0, 1):
+            tcell.set_particles(sp, workloads.population(cfg, sp))
+        tcell.prime(sh)
+        tuned = tcell.autotune(args.autotune, sh)
+        tcell.close()
+        cell.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"])
     if args.profile_steps:
         cell.advance_steps(args.profile_steps, sh)
         torch.cuda.synchronize()
@@ -352,6 +364,7 @@ def run_ours(args, cfg, ws, rank, local):
                        2 * cfg.n_init * 28 / 1e6),
                    "parallelism": "independent cell per GPU" if ws > 1 else "1 cell",
                    "form": args.form,
+                   "tuning": cell.tuning(),
                    "time_to_stationary": None,
                    "time_to_stationary_mode": "bench.py --time-to-stationary (minutes; not part of this run)"},
         "roofline": {"bound": "hbm", "kernel": "push_kernel" if args.form == "fused" else "push_plain",
@@ -394,6 +407,15 @@ def run_batch(args, ws, rank, local):
             c.set_particles(sp, workloads.population(cfg, sp))
     stream = torch.cuda.default_stream()
     sh = stream.cuda_stream
+    if args.autotune:
+        tb = pp.Batch(cfgs)
+        for c, cfg in zip(tb.cells, cfgs):
+            for sp in (0, 1):
+                c.set_particles(sp, workloads.population(cfg, sp))
+        tuned = tb.autotune(args.autotune, sh)
+        tb.close()
+        for c in batch.cells:
+            c.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"])
     for _ in range(args.warmup):
         batch.advance_period(1, sh)
     torch.cuda.synchronize()
@@ -451,7 +473,8 @@ def run_batch(args, ws, rank, local):
                                    % (len(cfgs_all), sum(c.n_init for c in cfgs_all)),
                        "step": "one RF period of every cell (400 PIC steps + period end each)",
                        "l2": "inputs larger than L2",
-                       "parallelism": "cells split over ranks" if ws > 1 else "32 cells on per-cell streams"},
+                       "parallelism": "cells split over ranks" if ws > 1 else "32 cells on per-cell streams",
+                       "tuning": batch.cells[0].tuning()},
             "roofline": {"bound": "hbm", "kernel": "whole step (52 B per particle-step over the step time)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": "measured" if peaks else "fallback"},

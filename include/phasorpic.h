@@ -477,6 +477,44 @@ int pp_get_poisson_stats(pp_cell* cell, int* sweeps, double* rel, void* stream);
 int pp_set_profiling(pp_cell* cell, int enable);
 int pp_get_phase_times(pp_cell* cell, double* ms, int64_t* counts);
 
+/*
+ * Run-time tuning.  Two knobs change only the order of floating-point sums,
+ * never the physics: the counting-sort cadence of each species (steps between
+ * sorts; the store drifts out of cell order between sorts, which costs the
+ * particle kernel's deposits, while a sort costs a pass over the store), and
+ * the resident blocks per SM of the persistent particle kernel.  A period
+ * graph is replayed only when each cadence divides N_RF an even number of
+ * times; other cadences run the step loop.  The tuning is not part of
+ * pp_config or of a checkpoint; a new cell starts from pp_config.sort_every
+ * and as many blocks per SM as fit.
+ */
+typedef struct pp_tuning {
+    int32_t sort_every[2];           /* sort cadence (steps) of electrons, ions; >= 1 */
+    int32_t push_blocks_per_sm;      /* blocks per SM of the particle kernel; 0 = as many as fit */
+    int32_t reserved0;
+} pp_tuning;
+
+int pp_get_tuning(pp_cell* cell, pp_tuning* out);
+/* PP_E_ARG unless both cadences are >= 1 and the block count >= 0. */
+int pp_set_tuning(pp_cell* cell, const pp_tuning* t);
+
+/*
+ * pp_autotune -- coordinate descent over the blocks per SM (1 .. as many as
+ * fit; skipped for the plain FP64 form), the electron cadence (graph-capable
+ * divisors of N_RF in [2, 40]) and the ion cadence (in [10, 200]).  Each
+ * candidate runs one period, then is timed over trial_periods periods with
+ * CUDA events on `stream` and ranked by time per particle-step (time per
+ * period in a cell without particles); it replaces the incumbent only when
+ * better by more than 1 %.  The periods run are periods of the simulation (the cell
+ * advances); the cell keeps the chosen tuning, returned in *chosen with its
+ * time per period (ms; either pointer may be NULL).  PP_E_ARG unless the cell
+ * is on a period boundary and trial_periods >= 1.  Synchronises `stream`.
+ * pp_batch_autotune tunes the knobs of all cells of a batch together against
+ * the time of a whole batch period (cadences valid for every cell).
+ */
+int pp_autotune(pp_cell* cell, int trial_periods, pp_tuning* chosen, double* ms_per_period, void* stream);
+int pp_batch_autotune(pp_batch* batch, int trial_periods, pp_tuning* chosen, double* ms_per_period, void* stream);
+
 /* pp_launch_count -- kernels launched by the library in this process. */
 int64_t pp_launch_count(void);
 

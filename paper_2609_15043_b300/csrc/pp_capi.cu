@@ -2,6 +2,9 @@
 // the host-side step sequencing (every step's arithmetic runs in kernels).
 #include "pp_internal.h"
 
+#include <algorithm>
+#include <functional>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -106,7 +109,7 @@ static void one_step(Cell* c, cudaStream_t st) {
     phase_mark(c, PH_OTHER, false, st);
     c->s = s + 1;
     for (int sp = 0; sp < 2; ++sp) {
-        if (++c->sort_count[sp] >= c->cfg.sort_every[sp]) {
+        if (++c->sort_count[sp] >= c->sort_every[sp]) {
             phase_mark(c, PH_SORT, true, st);
             launch_sort(c, sp, st);
             phase_mark(c, PH_SORT, false, st);
@@ -131,7 +134,7 @@ static void one_step(Cell* c, cudaStream_t st) {
 static bool graph_eligible(const Cell* c) {
     if (!c->use_graphs || c->s % c->n_rf != 0) return false;
     for (int sp = 0; sp < 2; ++sp) {
-        int e = c->cfg.sort_every[sp];
+        int e = c->sort_every[sp];
         if (c->sort_count[sp] != 0 || c->n_rf % e != 0 || (c->n_rf / e) % 2 != 0) return false;
     }
     return true;
@@ -228,6 +231,7 @@ static void free_batch(Batch* b) {
 }
 
 static int pp_prime_on(Cell* c, cudaStream_t st);
+static int batch_advance(Batch* b, int n_periods, cudaStream_t st);
 
 static int advance_cell_periods(Cell* c, int n_periods, cudaStream_t st) {
     if (!c->primed) {
@@ -325,6 +329,8 @@ int pp_init_cell(const pp_config* cfg, pp_cell** out) {
     *out = nullptr;
     Cell* c = new Cell();
     c->cfg = *cfg;
+    c->sort_every[0] = cfg->sort_every[0];
+    c->sort_every[1] = cfg->sort_every[1];
     int rc = setup_cell(c);
     if (rc != PP_OK) {
         free_cell(c);
@@ -700,7 +706,35 @@ int pp_batch_advance_period(pp_batch* h, int n_periods, void* stream) {
             set_error("a cell of the batch is not on an RF-period boundary");
             return PP_E_ARG;
         }
-    cudaStream_t st = (cudaStream_t)stream;
+    return batch_advance(b, n_periods, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- autotuning
+}  // extern "C"
+
+namespace pp {
+
+// sort cadences the period graph can replay: divisors d of N_RF with an even
+// number of sorts per period (the buffer parity returns), within [lo, hi]
+static std::vector<int> cadences(const std::vector<Cell*>& cells, int lo, int hi) {
+    std::vector<int> v;
+    for (int d = lo; d <= hi; ++d) {
+        bool ok = true;
+        for (const Cell* c : cells) ok = ok && c->n_rf % d == 0 && (c->n_rf / d) % 2 == 0;
+        if (ok) v.push_back(d);
+    }
+    return v;
+}
+
+static void apply_tuning(Cell* c, const pp_tuning& t) {
+    c->sort_every[0] = t.sort_every[0];
+    c->sort_every[1] = t.sort_every[1];
+    c->push_per_sm = t.push_blocks_per_sm;
+    c->push_blocks = 0;                          // recomputed by push_prepare
+    c->graph_cur[0] = c->graph_cur[1] = -1;      // re-capture the period graph
+}
+
+static int batch_advance(Batch* b, int n_periods, cudaStream_t st) {
     cudaEventRecord(b->fork, st);
     for (size_t i = 0; i < b->cells.size(); ++i) {
         cudaStreamWaitEvent(b->streams[i], b->fork, 0);
@@ -709,7 +743,154 @@ int pp_batch_advance_period(pp_batch* h, int n_periods, void* stream) {
         cudaEventRecord(b->done[i], b->streams[i]);
     }
     for (size_t i = 0; i < b->cells.size(); ++i) cudaStreamWaitEvent(st, b->done[i], 0);
-    return cuda_check(cudaGetLastError(), "pp_batch_advance_period");
+    return cuda_check(cudaGetLastError(), "advancing the batch");
+}
+
+// Coordinate descent over the particle kernel's blocks per SM, the electron
+// sort cadence and the ion sort cadence.  Each candidate runs one period
+// (the graph is re-captured and the sort phase settles) and is then timed
+// over `trial` periods with CUDA events on `st`.  Candidates are ranked by
+// time per particle-step (the populations change while the tuner runs, so the
+// time per period alone would favour whichever candidate ran last), or by
+// time per period in a cell without particles; a candidate replaces the
+// incumbent only when it is better by more than 1 %.  The periods run are
+// periods of the simulation: the knobs change the order of floating-point
+// sums, not the physics.
+static int autotune(std::vector<Cell*>& cells, const std::function<int(int)>& advance, int trial, cudaStream_t st,
+                    pp_tuning* chosen, double* ms_out) {
+    for (Cell* c : cells) push_prepare(c);
+    pp_tuning best{{cells[0]->sort_every[0], cells[0]->sort_every[1]}, cells[0]->push_per_sm, 0};
+    int max_per_sm = cells[0]->push_per_sm_max;
+    bool fp64 = true;
+    for (Cell* c : cells) {
+        max_per_sm = std::min(max_per_sm, c->push_per_sm_max);
+        fp64 = fp64 && c->fp64;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        set_error("autotune: cudaEventCreate failed");
+        return PP_E_CUDA;
+    }
+    // particle-steps pushed so far by all cells (read after a synchronisation)
+    auto psteps = [&]() -> double {
+        double n = 0;
+        for (Cell* c : cells) {
+            unsigned long long v = 0;
+            cudaMemcpy(&v, &c->d_st->cnt[C_PSTEPS], sizeof(v), cudaMemcpyDeviceToHost);
+            n += (double)v;
+        }
+        return n;
+    };
+    // ms per period and the ranking cost of one candidate
+    auto measure = [&](const pp_tuning& t, double* ms, double* cost) -> int {
+        for (Cell* c : cells) apply_tuning(c, t);
+        int rc = advance(1);
+        if (rc) return rc;
+        cudaEventRecord(e0, st);
+        rc = cuda_check(cudaEventSynchronize(e0), "autotune timing");
+        if (rc) return rc;
+        const double p0 = psteps();
+        rc = advance(trial);
+        if (rc) return rc;
+        cudaEventRecord(e1, st);
+        rc = cuda_check(cudaEventSynchronize(e1), "autotune timing");
+        if (rc) return rc;
+        const double p1 = psteps();
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = (double)f / trial;
+        *cost = p1 > p0 ? (double)f / (p1 - p0) : *ms;
+        return PP_OK;
+    };
+    double best_ms = 0, best_cost = 0;
+    int rc = measure(best, &best_ms, &best_cost);
+    std::vector<std::vector<int>> cand(3);
+    if (!fp64)
+        for (int k = 1; k <= max_per_sm; ++k) cand[0].push_back(k);
+    cand[1] = cadences(cells, 2, 40);
+    cand[2] = cadences(cells, 10, 200);
+    for (int knob = 0; knob < 3 && rc == PP_OK; ++knob) {
+        const pp_tuning inc = best;
+        for (int v : cand[knob]) {
+            pp_tuning t = inc;
+            int* field = knob == 0 ? &t.push_blocks_per_sm : &t.sort_every[knob - 1];
+            const int cur = knob == 0 ? (inc.push_blocks_per_sm > 0 ? inc.push_blocks_per_sm : max_per_sm) : *field;
+            if (v == cur) continue;
+            *field = v;
+            double ms = 0, cost = 0;
+            rc = measure(t, &ms, &cost);
+            if (rc) break;
+            if (cost < 0.99 * best_cost) {
+                best = t;
+                best_ms = ms;
+                best_cost = cost;
+            }
+        }
+    }
+    for (Cell* c : cells) apply_tuning(c, best);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    if (ms_out) *ms_out = best_ms;
+    return PP_OK;
+}
+
+}  // namespace pp
+
+extern "C" {
+
+int pp_get_tuning(pp_cell* h, pp_tuning* out) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !out) {
+        set_error("bad argument to pp_get_tuning");
+        return PP_E_ARG;
+    }
+    *out = pp_tuning{{c->sort_every[0], c->sort_every[1]}, c->push_per_sm, 0};
+    return PP_OK;
+}
+
+int pp_set_tuning(pp_cell* h, const pp_tuning* t) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !t || t->sort_every[0] < 1 || t->sort_every[1] < 1 || t->push_blocks_per_sm < 0) {
+        set_error("bad argument to pp_set_tuning (sort cadences >= 1, blocks per SM >= 0)");
+        return PP_E_ARG;
+    }
+    apply_tuning(c, *t);
+    return PP_OK;
+}
+
+int pp_autotune(pp_cell* h, int trial_periods, pp_tuning* chosen, double* ms_per_period, void* stream) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || trial_periods < 1) {
+        set_error("bad argument to pp_autotune (trial_periods >= 1)");
+        return PP_E_ARG;
+    }
+    if (c->s % c->n_rf != 0) {
+        set_error("the cell is not on an RF-period boundary");
+        return PP_E_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<Cell*> cells{c};
+    return autotune(cells, [&](int n) { return advance_cell_periods(c, n, st); }, trial_periods, st, chosen,
+                    ms_per_period);
+}
+
+int pp_batch_autotune(pp_batch* h, int trial_periods, pp_tuning* chosen, double* ms_per_period, void* stream) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    if (!b || trial_periods < 1) {
+        set_error("bad argument to pp_batch_autotune (trial_periods >= 1)");
+        return PP_E_ARG;
+    }
+    for (Cell* c : b->cells)
+        if (c->s % c->n_rf != 0) {
+            set_error("a cell of the batch is not on an RF-period boundary");
+            return PP_E_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    return autotune(b->cells, [&](int n) { return batch_advance(b, n, st); }, trial_periods, st, chosen,
+                    ms_per_period);
 }
 
 int pp_batch_destroy(pp_batch* h) {

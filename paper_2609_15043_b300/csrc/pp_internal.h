@@ -131,6 +131,12 @@ struct Cell {
     int64_t s = 0;                        // steps completed
     bool primed = false;
     int sort_count[2] = {0, 0};
+    // run-time tuning (pp_set_tuning / pp_autotune): sort cadences and the
+    // particle kernel's blocks per SM (0: as many as fit); neither changes
+    // the physics, only the order of floating-point sums
+    int sort_every[2] = {1, 1};
+    int push_per_sm = 0;
+    int push_per_sm_max = 0;
 
     // host-side geometry and circuit
     std::vector<std::vector<int>> turn_nodes;     // full node indices per turn

@@ -550,7 +550,9 @@ void push_prepare(Cell* c) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel, kPushThreads, shm);
-    c->push_blocks = nsm * (per < 1 ? 1 : per);
+    per = per < 1 ? 1 : per;
+    c->push_per_sm_max = per;
+    c->push_blocks = nsm * ((c->push_per_sm > 0 && c->push_per_sm < per) ? c->push_per_sm : per);
 }
 
 void launch_push(Cell* c, cudaStream_t st) {

@@ -38,7 +38,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_init_batch", "pp_batch_size", "pp_batch_cell", "pp_batch_advance_period", "pp_batch_destroy",
            "pp_mlp_forward", "pp_ml_configure", "pp_get_ml_features", "pp_ml_features_now",
            "pp_trainer_create", "pp_trainer_load", "pp_trainer_gradients", "pp_trainer_epoch",
-           "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy"]
+           "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy",
+           "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -92,6 +93,10 @@ class PPRecord(C.Structure):
         ("absorbed", C.c_int64), ("created", C.c_int64), ("nu_violations", C.c_int64),
         ("ml_err", C.c_double), ("ml_tau", C.c_double), ("ml_used", C.c_int32), ("ml_active", C.c_int32),
     ]
+
+
+class PPTuning(C.Structure):
+    _fields_ = [("sort_every", C.c_int32 * 2), ("push_blocks_per_sm", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class PPTrainOpts(C.Structure):
@@ -154,6 +159,10 @@ def _load():
         "pp_trainer_params": (I, [V, V, V, V]),
         "pp_trainer_steps": (C.c_int64, [V]),
         "pp_trainer_destroy": (I, [V]),
+        "pp_get_tuning": (I, [V, P(PPTuning)]),
+        "pp_set_tuning": (I, [V, P(PPTuning)]),
+        "pp_autotune": (I, [V, I, P(PPTuning), P(D), V]),
+        "pp_batch_autotune": (I, [V, I, P(PPTuning), P(D), V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +262,11 @@ def mlp_forward(params, feats):
     out = np.zeros((f.shape[0], m.n_out))
     _check(lib.pp_mlp_forward(C.byref(m), _ptr(f), f.shape[0], _ptr(out)), "pp_mlp_forward")
     return out
+
+
+def _tuning_dict(t):
+    return {"sort_every": [int(t.sort_every[0]), int(t.sort_every[1])],
+            "push_blocks_per_sm": int(t.push_blocks_per_sm)}
 
 
 _LAYER_ROWS = (256, 256, 256, 32)
@@ -524,6 +538,33 @@ def _ml_features(self, now=False, stream=0):
     return out[:n.value]
 
 
+def _get_tuning(self):
+    t = PPTuning()
+    _check(lib.pp_get_tuning(self.h, C.byref(t)), "pp_get_tuning")
+    return _tuning_dict(t)
+
+
+def _set_tuning(self, sort_every=None, push_blocks_per_sm=None):
+    cur = self.tuning()
+    se = cur["sort_every"] if sort_every is None else list(sort_every)
+    pb = cur["push_blocks_per_sm"] if push_blocks_per_sm is None else push_blocks_per_sm
+    t = PPTuning((C.c_int32 * 2)(int(se[0]), int(se[1])), int(pb), 0)
+    _check(lib.pp_set_tuning(self.h, C.byref(t)), "pp_set_tuning")
+
+
+def _autotune(self, trial_periods=1, stream=0):
+    """pp_autotune: returns the chosen tuning with its ms per period (the
+    periods run are periods of the simulation)."""
+    t, ms = PPTuning(), C.c_double()
+    _check(lib.pp_autotune(self.h, trial_periods, C.byref(t), C.byref(ms), C.c_void_p(stream)), "pp_autotune")
+    d = _tuning_dict(t)
+    d["ms_per_period"] = ms.value
+    return d
+
+
+Cell.tuning = _get_tuning
+Cell.set_tuning = _set_tuning
+Cell.autotune = _autotune
 Cell.ml_configure = _ml_configure
 Cell.ml_features = _ml_features
 Cell.checkpoint = _checkpoint
@@ -546,6 +587,15 @@ class Batch:
 
     def advance_period(self, n=1, stream=0):
         _check(lib.pp_batch_advance_period(self.h, n, C.c_void_p(stream)), "pp_batch_advance_period")
+
+    def autotune(self, trial_periods=1, stream=0):
+        """pp_batch_autotune: one tuning for every cell, timed on whole batch periods."""
+        t, ms = PPTuning(), C.c_double()
+        _check(lib.pp_batch_autotune(self.h, trial_periods, C.byref(t), C.byref(ms), C.c_void_p(stream)),
+               "pp_batch_autotune")
+        d = _tuning_dict(t)
+        d["ms_per_period"] = ms.value
+        return d
 
     def close(self):
         if self.h:
