@@ -68,8 +68,9 @@ struct DepAcc {
 };
 
 struct Tile {
-    float* s;      // shared rows [lo, lo + rows)
+    float* s;      // shared nodes: rows [lo, lo + rows) x columns [clo, clo + cols), row stride cols
     int lo, rows;
+    int clo, cols;
     float* g;      // global node grid
     int NR;
 };
@@ -78,10 +79,11 @@ struct Tile {
 // the native atomic of its state space (a pointer that may be either would
 // force generic atomics)
 __device__ __forceinline__ void tile_add4(const Tile& t, int iz, int ir, float v0, float v1, float v2, float v3) {
-    int r0 = iz - t.lo;
-    if (r0 >= 0 && r0 + 1 < t.rows) {
-        uint32_t a = smem_u32(t.s + r0 * t.NR + ir);
-        uint32_t b = a + 4u * (uint32_t)t.NR;
+    const int r0 = iz - t.lo, c0 = ir - t.clo;
+    // both corner rows and both corner columns inside the tile
+    if (r0 >= 0 && r0 + 1 < t.rows && c0 >= 0 && c0 + 1 < t.cols) {
+        uint32_t a = smem_u32(t.s + r0 * t.cols + c0);
+        uint32_t b = a + 4u * (uint32_t)t.cols;
         asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v0));
         asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a + 4u), "f"(v1));
         asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b), "f"(v2));
@@ -199,6 +201,8 @@ struct PushArgs {
     DevState* st;
 };
 
+static_assert(kTileRows <= kPushThreads / 32, "one warp clears and flushes each tile row");
+
 // shared-memory layout of one block (dynamic)
 struct PushSmem {
     static constexpr int kArrays = 7;        // cell, dr, dz, vr, vt, vz, uid
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     uint16_t* s_cand = reinterpret_cast<uint16_t*>(t_jm + kTileRows * a.NR);
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_min[kPushThreads / 32], s_max[kPushThreads / 32];
+    __shared__ int s_cmin[kPushThreads / 32], s_cmax[kPushThreads / 32];
     __shared__ int s_ncand;
     __shared__ int s_ok;
     __shared__ float s_f[kPushThreads / 32][2];
@@ -291,39 +296,54 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         }
         parity ^= 1u;
         if (t == 0) s_ok = ok ? 1 : 0;
-        // ---- tile rows from the chunk's cell range
-        int lmin = INT_MAX, lmax = -1;
+        // ---- node tile from the chunk's cell rows and columns: deposits at the
+        // old positions reach one row/column beyond, at the new ones one
+        // below and two beyond; anything outside goes to global atomics
+        int lmin = INT_MAX, lmax = -1, cmin = INT_MAX, cmax = -1;
         for (int q = t; q < nact; q += kPushThreads) {
             uint32_t c = s_cell[q];
             if (c != kDead) {
                 int iz = (int)(__umulhi(c, a.div_magic) >> a.div_shift);
+                int ir = (int)c - iz * nr;
                 lmin = min(lmin, iz);
                 lmax = max(lmax, iz);
+                cmin = min(cmin, ir);
+                cmax = max(cmax, ir);
             }
         }
         lmin = __reduce_min_sync(0xffffffffu, lmin);
         lmax = __reduce_max_sync(0xffffffffu, lmax);
+        cmin = __reduce_min_sync(0xffffffffu, cmin);
+        cmax = __reduce_max_sync(0xffffffffu, cmax);
         if (lane == 0) {
             s_min[warp] = lmin;
             s_max[warp] = lmax;
+            s_cmin[warp] = cmin;
+            s_cmax[warp] = cmax;
         }
         __syncthreads();
         if (!s_ok) break;
-        int bmin = INT_MAX, bmax = -1;
+        int bmin = INT_MAX, bmax = -1, bcmin = INT_MAX, bcmax = -1;
         for (int w = 0; w < kPushThreads / 32; ++w) {
             bmin = min(bmin, s_min[w]);
             bmax = max(bmax, s_max[w]);
+            bcmin = min(bcmin, s_cmin[w]);
+            bcmax = max(bcmax, s_cmax[w]);
         }
         const int tlo = max(bmin - 1, 0);
         const int thi = min(bmax + 2, a.i_win);
         const int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
-        for (int q = t; q < trows * NR; q += kPushThreads) {
-            t_rho[q] = 0.f;
-            t_jm[q] = 0.f;
-        }
+        const int tclo = max(bcmin - 1, 0);
+        const int tcols = (bmax < 0) ? 0 : min(bcmax + 2, nr) - tclo + 1;
+        // warp w clears (and later flushes) tile row w; trows <= kTileRows = warps per block
+        if (warp < trows)
+            for (int cq = lane; cq < tcols; cq += 32) {
+                t_rho[warp * tcols + cq] = 0.f;
+                t_jm[warp * tcols + cq] = 0.f;
+            }
         __syncthreads();
-        const Tile tj{t_jm, tlo, trows, a.jm, NR};
-        const Tile tq{t_rho, tlo, trows, a.rho, NR};
+        const Tile tj{t_jm, tlo, trows, tclo, tcols, a.jm, NR};
+        const Tile tq{t_rho, tlo, trows, tclo, tcols, a.rho, NR};
 
         // ---- phase A: thread-contiguous push
         DepAcc dj{-1, 0, 0.f, 0.f, 0.f, 0.f};
@@ -492,12 +512,13 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bulk_s2g(P.vz + base, s_vz, bytes);
             bulk_commit();
         }
-        for (int q = t; q < trows * NR; q += kPushThreads) {
-            float vq = t_rho[q], vj = t_jm[q];
-            int gidx = (tlo + q / NR) * NR + (q % NR);
-            if (vq != 0.f) atomicAdd(&a.rho[gidx], vq);
-            if (vj != 0.f) atomicAdd(&a.jm[gidx], vj);
-        }
+        if (warp < trows)
+            for (int cq = lane; cq < tcols; cq += 32) {
+                const float vq = t_rho[warp * tcols + cq], vj = t_jm[warp * tcols + cq];
+                const int gidx = (tlo + warp) * NR + tclo + cq;
+                if (vq != 0.f) atomicAdd(&a.rho[gidx], vq);
+                if (vj != 0.f) atomicAdd(&a.jm[gidx], vj);
+            }
         __syncthreads();
     }
     if (t == 0) bulk_wait_all();
