@@ -261,11 +261,14 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
 
     // dynamic schedule: a block takes the next unprocessed chunk when it is
     // done with its last (electron chunks first), which evens out the blocks'
-    // shares of cheap and expensive chunks
+    // shares of cheap and expensive chunks; the next index is taken before the
+    // barrier that ends a chunk.  The node tiles start zeroed and every flush
+    // zeroes the entries it reads, so a chunk finds its tile clear.
     __shared__ int s_chunk;
+    for (int q = t; q < 2 * kTileRows * NR; q += kPushThreads) t_rho[q] = 0.f;   // t_jm follows t_rho
+    if (t == 0) s_chunk = atomicAdd(&a.st->push_chunk, 1);
+    __syncthreads();
     for (;;) {
-        if (t == 0) s_chunk = atomicAdd(&a.st->push_chunk, 1);
-        __syncthreads();
         const int chunk = s_chunk;
         if (chunk >= ce + ci) break;
         const int sp = chunk < ce ? 0 : 1;
@@ -335,13 +338,6 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         const int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
         const int tclo = max(bcmin - 1, 0);
         const int tcols = (bmax < 0) ? 0 : min(bcmax + 2, nr) - tclo + 1;
-        // warp w clears (and later flushes) tile row w; trows <= kTileRows = warps per block
-        if (warp < trows)
-            for (int cq = lane; cq < tcols; cq += 32) {
-                t_rho[warp * tcols + cq] = 0.f;
-                t_jm[warp * tcols + cq] = 0.f;
-            }
-        __syncthreads();
         const Tile tj{t_jm, tlo, trows, tclo, tcols, a.jm, NR};
         const Tile tq{t_rho, tlo, trows, tclo, tcols, a.rho, NR};
 
@@ -512,13 +508,20 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bulk_s2g(P.vz + base, s_vz, bytes);
             bulk_commit();
         }
+        // warp w flushes and clears tile row w (trows <= kTileRows = warps per block)
         if (warp < trows)
             for (int cq = lane; cq < tcols; cq += 32) {
-                const float vq = t_rho[warp * tcols + cq], vj = t_jm[warp * tcols + cq];
+                const int q = warp * tcols + cq;
+                const float vq = t_rho[q], vj = t_jm[q];
+                t_rho[q] = 0.f;
+                t_jm[q] = 0.f;
                 const int gidx = (tlo + warp) * NR + tclo + cq;
                 if (vq != 0.f) atomicAdd(&a.rho[gidx], vq);
                 if (vj != 0.f) atomicAdd(&a.jm[gidx], vj);
             }
+        // every thread read this chunk's index before the barrier after the
+        // tile bounds, so it can be replaced here
+        if (t == 0) s_chunk = atomicAdd(&a.st->push_chunk, 1);
         __syncthreads();
     }
     if (t == 0) bulk_wait_all();
