@@ -86,3 +86,30 @@ def test_config_validation_limits(change, message):
     cfg = workloads.small().replace(**change)
     with pytest.raises(pp.PhasorPICError, match=message):
         pp.Cell(cfg)
+
+
+def test_trainer_and_tuning_arguments_are_checked_before_the_device():
+    """Bad options and NULL handles of the training and tuning entry points
+    come back as PP_E_ARG before any device work."""
+    import numpy as np
+    from paper_2609_15043_b300 import phasorpic as pp
+    rows = (256, 256, 256, 32)
+    w = [np.zeros((r, 256), np.float32) for r in rows]
+    b = [np.zeros(r, np.float32) for r in rows]
+    for change in (dict(n_in=0), dict(n_in=257), dict(n_out=0), dict(n_out=33), dict(batch=0), dict(batch=4097),
+                   dict(lr=0.0), dict(beta1=1.0), dict(beta2=-0.1), dict(eps=0.0), dict(weight_decay=-1.0)):
+        kw = dict(n_in=206, n_out=12, w=w, b=b)
+        kw.update(change)
+        with pytest.raises(pp.PhasorPICError, match="PP_E_ARG"):
+            pp.Trainer(**kw)
+    with pytest.raises(ValueError):
+        pp.Trainer(206, 12, w[:3] + [np.zeros((16, 256), np.float32)], b)
+    lib = pp.lib                                  # PP_E_ARG = -7
+    assert lib.pp_trainer_steps(None) == -1
+    assert lib.pp_trainer_destroy(None) == -7
+    assert lib.pp_trainer_load(None, None, None, 1) == -7
+    assert lib.pp_trainer_epoch(None, None, 1, None) == -7
+    assert lib.pp_get_tuning(None, None) == -7
+    assert lib.pp_set_tuning(None, None) == -7
+    assert lib.pp_autotune(None, 1, None, None, None) == -7
+    assert lib.pp_batch_autotune(None, 1, None, None, None) == -7
