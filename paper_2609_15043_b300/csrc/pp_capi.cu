@@ -69,6 +69,9 @@ static void free_cell(Cell* c) {
     for (cudaEvent_t e : c->gev_pool) cudaEventDestroy(e);
     if (c->period_exec) cudaGraphExecDestroy(c->period_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_st) cudaFreeHost(c->h_st);
     delete c;
@@ -100,6 +103,26 @@ static void one_step(Cell* c, cudaStream_t st) {
     phase_mark(c, PH_OTHER, true, st);
     launch_append(c, st);
     phase_mark(c, PH_OTHER, false, st);
+    // The step's counting sorts touch only the particle store, its slot counts
+    // and the sort bins; the Poisson solve and the sample touch node grids and
+    // the solver's fields only.  So the sorts run on the side stream beside
+    // them and join before anything that reads particles again (the next
+    // step, or the period end's summaries).
+    const bool sort_now = c->sort_count[0] + 1 >= c->sort_every[0] || c->sort_count[1] + 1 >= c->sort_every[1];
+    cudaStream_t ss = st;
+    if (sort_now && c->side_stream) {
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+        ss = c->side_stream;
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        if (++c->sort_count[sp] >= c->sort_every[sp]) {
+            phase_mark(c, PH_SORT, true, ss);
+            launch_sort(c, sp, ss);
+            phase_mark(c, PH_SORT, false, ss);
+            c->sort_count[sp] = 0;
+        }
+    }
     phase_mark(c, PH_POISSON, true, st);
     poisson_refine(c, std::cos(th1), std::sin(th1), st, false, nullptr, true);
     phase_mark(c, PH_POISSON, false, st);
@@ -107,15 +130,11 @@ static void one_step(Cell* c, cudaStream_t st) {
     double two_n = 2.0 / c->n_rf;
     launch_sample_accumulate(c, std::cos(th1), std::sin(th1), two_n * std::cos(th), two_n * std::sin(th), st);
     phase_mark(c, PH_OTHER, false, st);
-    c->s = s + 1;
-    for (int sp = 0; sp < 2; ++sp) {
-        if (++c->sort_count[sp] >= c->sort_every[sp]) {
-            phase_mark(c, PH_SORT, true, st);
-            launch_sort(c, sp, st);
-            phase_mark(c, PH_SORT, false, st);
-            c->sort_count[sp] = 0;
-        }
+    if (ss != st) {
+        cudaEventRecord(c->ev_join, ss);
+        cudaStreamWaitEvent(st, c->ev_join, 0);
     }
+    c->s = s + 1;
     if (c->s % c->n_rf == 0) {
         phase_mark(c, PH_PERIOD, true, st);
         period_end(c, st);
@@ -335,6 +354,14 @@ int pp_init_cell(const pp_config* cfg, pp_cell** out) {
     if (rc != PP_OK) {
         free_cell(c);
         return rc;
+    }
+    // without them the sorts simply stay on the step's stream
+    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->side_stream) cudaStreamDestroy(c->side_stream);
+        c->side_stream = nullptr;
+        cudaGetLastError();
     }
     *out = reinterpret_cast<pp_cell*>(c);
     return PP_OK;

@@ -238,6 +238,9 @@ struct Cell {
     // one captured RF period (valid while the sort phase and buffer parity match)
     cudaGraphExec_t period_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // the step's counting sorts run here beside its Poisson solve and sample
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int graph_cur[2] = {-1, -1};
     int graph_prof = 0;
     size_t graph_pairs = 0;                // event pairs recorded in the graph
