@@ -164,7 +164,13 @@ static int capture_period(Cell* c) {
         cudaGraphExecDestroy(c->period_exec);
         c->period_exec = nullptr;
     }
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // the period graph's kernels keep the capture stream's (highest) priority
+    // and the side stream's sorts the lowest, so that where they overlap the
+    // latency-bound Poisson chain is scheduled first
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (!c->cap_stream &&
+        cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess) {
         set_error("could not create the capture stream");
         return PP_E_CUDA;
     }
@@ -193,7 +199,7 @@ static int capture_period(Cell* c) {
         cudaGetLastError();
         return PP_OK;
     }
-    e = cudaGraphInstantiate(&c->period_exec, g, 0);
+    e = cudaGraphInstantiateWithFlags(&c->period_exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         c->period_exec = nullptr;
@@ -356,7 +362,9 @@ int pp_init_cell(const pp_config* cfg, pp_cell** out) {
         return rc;
     }
     // without them the sorts simply stay on the step's stream
-    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         if (c->side_stream) cudaStreamDestroy(c->side_stream);
