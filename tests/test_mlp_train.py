@@ -31,3 +31,27 @@ def test_trainer_fits_a_smooth_map(tmp_path):
     ref = Y[::10]
     rel = np.sqrt(np.mean((pred - ref) ** 2) / np.var(ref))
     assert rel < 0.2
+
+
+def test_standardise_constant_loads_are_predicted_by_their_mean():
+    """A load that never varied in the pairs gets scale 0 and a standardised
+    target of 0, so the network's output for it is ignored: forward returns
+    its mean exactly; a constant feature keeps scale 1."""
+    from paper_2609_15043_b300 import mlp_train
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((50, 6))
+    X[:, 2] = 10.0                                   # constant feature
+    Y = rng.standard_normal((50, 4)) * 3.0 + 1.0
+    Y[:, 1] = 0.0                                    # e.g. V_p of a particle-free cell
+    Y[:, 3] = -2.5
+    mu_in, sig_in, mu_out, sig_out, Xn, Yn = mlp_train.standardise(X, Y)
+    assert sig_in[2] == 1.0 and np.all(Xn[:, 2] == 0.0)
+    assert sig_out[1] == 0.0 and sig_out[3] == 0.0 and sig_out[0] > 0 and sig_out[2] > 0
+    assert np.all(Yn[:, 1] == 0.0) and np.all(Yn[:, 3] == 0.0)
+    assert np.allclose(Yn[:, 0], (Y[:, 0] - Y[:, 0].mean()) / Y[:, 0].std(), rtol=1e-6)
+    rows = (256, 256, 256, 32)
+    p = dict(w=[mlp.bf16_bits((rng.standard_normal((r, 256)) / 16).astype(np.float32)) for r in rows],
+             b=[(rng.standard_normal(r) * 0.1).astype(np.float32) for r in rows],
+             mu_in=mu_in, sig_in=sig_in, mu_out=mu_out, sig_out=sig_out)
+    y = mlp.forward(p, X[0])
+    assert y[1] == 0.0 and y[3] == -2.5
