@@ -15,5 +15,5 @@ M_AR = 39.948 * AMU        # kg, argon atom (the Ar+ ion mass is taken equal)
 KB = 1.380649e-23          # J/K
 TORR = 133.322368          # Pa
 
-E_EXC = 11.55              # eV, Ar excitation threshold (BASELINE config 1)
+E_EXC = 11.55              # eV, Ar excitation threshold of the argon workloads
 E_ION = 15.76              # eV, Ar ionisation threshold

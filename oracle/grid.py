@@ -1,9 +1,12 @@
 """RZ grid geometry for the oracle.
 
 Nodes (i, j) sit at z_i = i*dz, R_j = j*dr, i = 0..nz, j = 0..nr; cell (i, j)
-spans [z_i, z_{i+1}] x [R_j, R_{j+1}].  The reading of the paper's silent
-points (cell counts, window slab, coil compartment, turn discs, axis control
-volume) is the one listed in DESIGN.md "Readings".
+spans [z_i, z_{i+1}] x [R_j, R_{j+1}].  Readings of the paper's silent
+points: the configured sizes are cell counts; a quartz slab over the full
+radius separates the plasma region from a particle-free coil compartment
+under a grounded lid; a turn is the set of nodes inside its wire disc (the
+nearest node when the disc holds none); the axis node's control volume uses
+A_z = pi*(dr/2)**2 and has no R- face.
 
 Node control volumes and faces follow Sec. 2.3 (Eq. areas):
     A_z = 2*pi*R_j*dr (j >= 1),   A_z = pi*(dr/2)**2 on the axis (j = 0),

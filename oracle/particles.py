@@ -21,9 +21,9 @@ with T = float64 it is the accuracy reference.  Transcendental functions
 (cos/sin of scattering angles, log in Box-Muller) only shape continuous
 values, never a decision of the same step.
 
-Cross sections are this project's analytic rational functions of energy
-("Readings"): thresholds 11.55 and 15.76 eV, magnitudes of the
-right order for argon; they are not database fits.
+Cross sections are this project's analytic rational functions of energy (a
+reading: the paper gives none): thresholds 11.55 and 15.76 eV, magnitudes of
+the right order for argon; they are not database fits.
 """
 import math
 import numpy as np
