@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--settle", type=int, default=-1, metavar="PERIODS",
+                    help="untimed periods before the warm-up that take the seeded populations through the "
+                         "initial sheath formation (-1: until the live count changes by < 1%% per period, "
+                         "at most 80 periods)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cell60")
     ap.add_argument("--cfg", action="append", default=[], metavar="KEY=VALUE",
@@ -163,8 +167,10 @@ def push_kernel_hash():
 
 
 def profiled_traffic(workload):
-    """DRAM bytes per push-kernel launch from the committed ncu summary, valid
-    only while the kernel source is unchanged (hash recorded in the summary)."""
+    """DRAM bytes per particle of one push-kernel launch from the committed ncu
+    summary (its bytes per launch over its particles per launch), valid only
+    while the kernel source is unchanged (hash recorded in the summary); the
+    caller scales it to the timed launches' particles."""
     path = os.path.join(ROOT, "profiles", "push_kernel_%s.md" % workload)
     try:
         txt = open(path).read()
@@ -172,9 +178,10 @@ def profiled_traffic(workload):
         return None
     h = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not t or h.group(1) != push_kernel_hash():
+    n = re.search(r"particles_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or not n or h.group(1) != push_kernel_hash():
         return None
-    return float(t.group(1))
+    return float(t.group(1)) / float(n.group(1))
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -273,6 +280,19 @@ def run_ours(args, cfg, ws, rank, local):
         print(json.dumps({"profile_steps": args.profile_steps, "counters": cell.counters()}), flush=True)
         cell.close()
         return
+    # settle: the seeded uniform populations lose a share of their electrons
+    # while the sheaths form; the timed periods start once the live count has
+    # levelled, so value, e2e and the roofline describe the same population
+    settle = 0
+    live_prev = sum(cell.counters()[k] for k in ("live_e", "live_i"))
+    limit = args.settle if args.settle >= 0 else 80
+    while settle < limit:
+        cell.advance_period(1, sh)
+        settle += 1
+        live = sum(cell.counters()[k] for k in ("live_e", "live_i"))
+        if args.settle < 0 and abs(live - live_prev) < 0.01 * live_prev:
+            break
+        live_prev = live
     # the timed region records events around the particle kernel; the period
     # graph is captured with them during warm-up
     cell.set_profiling(True, level=1)
@@ -305,6 +325,7 @@ def run_ours(args, cfg, ws, rank, local):
     cell.set_profiling(False)
     launches = pp.launch_count() - l0
     c1 = cell.counters()
+    status = cell.status()
     psteps = c1["particle_steps"] - c0["particle_steps"]
     ms_all, ps_all = reduce_over_ranks(ms, psteps, dist)
     value = ps_all / (ms_all / 1e3)
@@ -351,7 +372,8 @@ def run_ours(args, cfg, ws, rank, local):
     per_launch_particles = psteps / max(push_n, 1)
     bpp = BYTES_PER_PARTICLE_STEP if args.form == "fused" else BYTES_PER_PARTICLE_STEP_FP64
     achieved = bpp * per_launch_particles / (push_ms / push_n / 1e3) / 1e9
-    traffic = profiled_traffic(args.workload) if args.form == "fused" else None
+    tpp = profiled_traffic(args.workload) if args.form == "fused" else None
+    traffic = tpp * per_launch_particles if tpp is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -365,6 +387,9 @@ def run_ours(args, cfg, ws, rank, local):
                    "parallelism": "independent cell per GPU" if ws > 1 else "1 cell",
                    "form": args.form,
                    "tuning": cell.tuning(),
+                   "settle_periods": settle,
+                   "n_live": {"start": [c0["live_e"], c0["live_i"]], "end": [c1["live_e"], c1["live_i"]]},
+                   "status": status,
                    "time_to_stationary": None,
                    "time_to_stationary_mode": "bench.py --time-to-stationary (minutes; not part of this run)"},
         "roofline": {"bound": "hbm", "kernel": "push_kernel" if args.form == "fused" else "push_plain",

@@ -70,6 +70,9 @@ class OracleCell:
         self._compose()
         # --- particles ----------------------------------------------------------
         self.weights = weights
+        self._species = {}
+        self.implicit = bool(getattr(cfg, "implicit_es", 0))
+        self.chi_last = None
         self.P = [None, None]
         self.next_uid = [0, 0]
         self.window_q = np.zeros((g.NZ, g.NR))
@@ -84,6 +87,14 @@ class OracleCell:
                           vr=np.array(vr), vt=np.array(vt), vz=np.array(vz),
                           uid=np.asarray(uid, np.int64).copy())
         self.next_uid[sp] = int(np.max(uid)) + 1 if len(uid) else 0
+
+    def species(self, sp, T):
+        """Species constants in T (computed once per species and type; they
+        depend only on the configuration and the macro weight)."""
+        key = (sp, np.dtype(T).name)
+        if key not in self._species:
+            self._species[key] = particles.SpeciesConstants(self.cfg, sp, self.weights[sp], T)
+        return self._species[key]
 
     def theta(self, s):
         return 2.0 * math.pi * (s % self.n_rf) / self.n_rf
@@ -100,24 +111,50 @@ class OracleCell:
                 vals[i, j] = phik[k]
         return vals
 
-    def deposit_charge(self, T):
-        """Q at the current positions (used once before the first step)."""
-        Q = np.zeros((self.g.NZ, self.g.NR))
+    def deposit_species(self, T):
+        """Charge of each species at the current positions (C per node)."""
+        Qs = [np.zeros((self.g.NZ, self.g.NR)), np.zeros((self.g.NZ, self.g.NR))]
         for sp in (0, 1):
             P = self.P[sp]
-            sc = particles.SpeciesConstants(self.cfg, sp, self.weights[sp], T)
+            sc = self.species(sp, T)
             live = P['cell'] >= 0
             cell = P['cell'][live]
             ir, iz = cell % self.cfg.nr, cell // self.cfg.nr
             w = particles.bilinear(P['dr'][live].astype(T), P['dz'][live].astype(T), T)
             for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), w):
-                np.add.at(Q, (iz + di, ir + dj), (sc.qw * wk).astype(np.float64))
-        return Q
+                np.add.at(Qs[sp], (iz + di, ir + dj), (sc.qw * wk).astype(np.float64))
+        return Qs
+
+    def deposit_charge(self, T):
+        """Q at the current positions (used once before the first step)."""
+        Qs = self.deposit_species(T)
+        return Qs[0] + Qs[1]
+
+    def susceptibility(self, Qs, T):
+        """chi on the nodes from the species charges of the predicted
+        populations (Sec. 2.3): chi = sum_s (q_s/m_s) dt^2 (Q_s / V) /
+        (eps0 eps_r), with V the node weighting volume and eps_r the node mean
+        of the adjacent cells; zero where no particle deposits."""
+        vol = self.geo.vol
+        chi = np.zeros((self.g.NZ, self.g.NR))
+        m = vol > 0
+        for sp in (0, 1):
+            chi[m] += self.species(sp, T).chi_per_charge * Qs[sp][m] / vol[m]
+        chi[m] /= self.geo.eps_node[m]
+        return chi
+
+    def solve_potential(self, Q, th, chi):
+        dv = self.dirichlet_values(th)
+        if chi is None:
+            return self.poisson.solve(Q, dv)
+        return self.poisson.solve_chi(Q, dv, chi)
 
     def prime(self, T=np.float32):
-        """phi^0 from the initial positions and theta_0."""
-        Q = self.deposit_charge(T)
-        self.phi = self.poisson.solve(Q + self.window_q, self.dirichlet_values(self.theta(0)))
+        """phi^0 from the initial positions and theta_0 (with the initial
+        populations' susceptibility in the direct-implicit form)."""
+        Qs = self.deposit_species(T)
+        self.chi_last = self.susceptibility(Qs, T) if self.implicit else None
+        self.phi = self.solve_potential(Qs[0] + Qs[1] + self.window_q, self.theta(0), self.chi_last)
 
     # ------------------------------------------------------------------------
     def node_fields(self, th, T):
@@ -142,28 +179,43 @@ class OracleCell:
             F[:, comp, 3] = f32[1:iw + 1, 1:nr + 1].ravel()
         return F
 
-    def step(self, T=np.float32):
-        """One PIC step; returns per-step information."""
+    def step(self, T=np.float32, drive=None):
+        """One PIC step; returns per-step information.
+
+        drive: optional callable (theta_s, E_theta nodes at theta_s) -> node
+        current moment (A m) of a prescribed, non-particle current carrier
+        (a test load such as an ohmic conductor).  Its moment is added to the
+        particles' J_theta deposit and its work sum(J E) to the field-side
+        inductive power, exactly as a particle's q w v_theta is."""
         cfg, g = self.cfg, self.g
         s = self.s
         th_old = self.theta(s)
         F = self.node_fields(th_old, T)
-        Q = np.zeros((g.NZ, g.NR))
+        Qs = [np.zeros((g.NZ, g.NR)), np.zeros((g.NZ, g.NR))]
         J = np.zeros((g.NZ, g.NR))
         stats = dict(p_ind=0.0, p_es=0.0, absorbed=0, pushed=0, nu_viol=0,
                      coll=np.zeros((2, 3), np.int64))
         events = []
         for sp in (0, 1):
-            sc = particles.SpeciesConstants(cfg, sp, self.weights[sp], T)
+            if self.P[sp] is None:
+                continue
+            sc = self.species(sp, T)
             ev = particles.push_species(self.P[sp], F, sc, self.geo, s, cfg.seed, T,
-                                        Q, J, self.window_q, stats)
+                                        Qs[sp], J, self.window_q, stats, implicit=self.implicit)
             events.extend(ev)
+        Q = Qs[0] + Qs[1]
+        if drive is not None:
+            Et = self.Ec * math.cos(th_old) - self.Ess * math.sin(th_old)   # Eq. et_reconstruct
+            Jd = np.asarray(drive(th_old, Et), dtype=np.float64)
+            J += Jd
+            stats['p_ind'] += float(np.sum(Jd * Et))
         self._append(events, T)
         # Poisson at t_{s+1}
         th_new = self.theta(s + 1)
-        dv = self.dirichlet_values(th_new)
-        self.phi = self.poisson.solve(Q + self.window_q, dv)
-        Qk = fields.turn_charge(g, self.phi, self.geo.turn_nodes)
+        chi = self.susceptibility(Qs, T) if self.implicit else None
+        self.phi = self.solve_potential(Q + self.window_q, th_new, chi)
+        Qk = fields.turn_charge(g, self.phi, self.geo.turn_nodes, chi=chi)
+        self.chi_last = chi
         Vk = self.turn_potentials(th_new)
         # accumulations (Eq. fourier, Eq. pind, Eq. pcap samples)
         N = self.n_rf
@@ -274,7 +326,6 @@ class OracleCell:
                                                        self.omega, self.vg, icap, vp)
         self._reset_accumulators()
         # phi at the cycle boundary with the new turn potentials
-        self.phi = self.poisson.solve(self.Q_last + self.window_q,
-                                      self.dirichlet_values(self.theta(self.s)))
+        self.phi = self.solve_potential(self.Q_last + self.window_q, self.theta(self.s), self.chi_last)
         self.records.append(rec)
         return rec

@@ -71,15 +71,40 @@ class PoissonSolver:
         b = self.rhs(Q, phi_dirichlet)
         return self.lu.solve(b).reshape(self.g.NZ, self.g.NR)
 
+    def solve_chi(self, Q, phi_dirichlet, chi):
+        """Eq. poisson with the susceptibility chi (a fresh factorisation:
+        chi changes every step)."""
+        A = poisson_matrix_chi(self.A, self.dirichlet, chi)
+        b = self.rhs(Q, phi_dirichlet)
+        return spla.spsolve(A, b).reshape(self.g.NZ, self.g.NR)
+
     def residual(self, phi, Q, phi_dirichlet):
         b = self.rhs(Q, phi_dirichlet)
         return (self.A @ phi.ravel() - b).reshape(self.g.NZ, self.g.NR)
 
 
-def turn_charge(g, phi, turn_nodes):
+def poisson_matrix_chi(A0, dirichlet, chi):
+    """The operator of Eq. poisson with the susceptibility chi on the nodes:
+    every face coefficient eps_f A_f / d_f of the chi = 0 operator A0 (rows of
+    non-Dirichlet nodes) is multiplied by 1 + (chi_p + chi_nb)/2, the face
+    factor of Eq. epseff, and the diagonal is minus the row's face sum."""
+    A = A0.tocoo()
+    r, c, v = A.row, A.col, A.data.copy()
+    d = dirichlet.ravel()
+    x = np.asarray(chi, dtype=np.float64).ravel()
+    off = (r != c) & ~d[r]
+    v[off] = v[off] * (1.0 + 0.5 * (x[r[off]] + x[c[off]]))
+    on = (r == c) & ~d[r]
+    face_sum = np.bincount(r[off], weights=v[off], minlength=A.shape[0])
+    v[on] = -face_sum[r[on]]
+    return sp.csc_matrix((v, (r, c)), shape=A.shape)
+
+
+def turn_charge(g, phi, turn_nodes, chi=None):
     """Q_k of Eq. facecharge summed over the external faces of each turn.
     Faces to a node of another turn count for both turns; faces to metal or
-    boundary nodes count with the node's Dirichlet value."""
+    boundary nodes count with the node's Dirichlet value.  With a
+    susceptibility chi the face coefficient is that of Eq. epseff."""
     member = {}
     for k, nodes in enumerate(turn_nodes):
         for n in nodes:
@@ -100,6 +125,8 @@ def turn_charge(g, phi, turn_nodes):
                 else:
                     A, d = g.area_r(j, dj), g.dr
                 eps = g.eps_face(i, j, di, dj)
+                if chi is not None:
+                    eps = eps * (1.0 + 0.5 * (chi[i, j] + chi[ii, jj]))
                 Q[k] += EPS0 * eps * (phi[i, j] - phi[ii, jj]) / d * A
     return Q
 

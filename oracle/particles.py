@@ -14,6 +14,17 @@ from the textbook methods:
     Philox2x32-10); a candidate's process is chosen by comparing u * nu_max
     with the cumulative real frequencies (uniforms from Philox4x32-10).
 
+Direct-implicit form (Sec. 2.3, Eq. poisson with chi; Langdon, Cohen &
+Friedman 1983): the stored state is the predicted one, (x~^s, v~^{s-1/2}).
+The electrostatic force of a step is applied implicitly at the new time level,
+v^{s-1/2} = v~^{s-1/2} + (q/m) dt E^s(x~^s), x^s = x~^s + (q/m) dt^2 E^s(x~^s),
+by the next step's particle pass, once E^s has been solved with the
+susceptibility of the predicted populations (chi = sum_s q_s n_s (q_s/m_s)
+dt^2 / (eps0 eps_r)).  The inductive E_theta and the RF B stay explicit
+(the Boris step with E_r = E_z = 0); every field is gathered at the predicted
+position.  The current moment is taken at the corrected position x^s; the
+charge is deposited at the next predicted position, per species.
+
 The step is written once over a dtype T.  With T = float32 every operation is
 a single IEEE float32 operation in the order the kernels use, so integer
 outcomes (cells, absorptions, collisions) are decided exactly as on the GPU;
@@ -28,7 +39,7 @@ the right order for argon; they are not database fits.
 import math
 import numpy as np
 
-from .constants import QE, ME, M_AR, KB, E_EXC, E_ION
+from .constants import QE, ME, M_AR, KB, E_EXC, E_ION, EPS0
 from . import philox
 
 DEAD = -1
@@ -90,6 +101,12 @@ class SpeciesConstants:
         self.sp = sp
         self.q, self.m, self.w = q, m, weight
         self.qmh = T(q / m * cfg.dt / 2.0)
+        # direct-implicit electrostatic kick (Sec. 2.3): velocity and
+        # position response to E^{s} at the predicted position, per unit field
+        self.qmd = T(q / m * cfg.dt)
+        self.kres = T(q / m * cfg.dt * cfg.dt / dr)     # cells per (V/m), radial
+        self.kzes = T(q / m * cfg.dt * cfg.dt / dz)     # cells per (V/m), axial
+        self.chi_per_charge = q / m * cfg.dt * cfg.dt / EPS0   # FP64: chi = this * (charge / volume)
         self.dtr = T(cfg.dt / dr)
         self.dtz = T(cfg.dt / dz)
         self.qw = T(q * weight)
@@ -135,7 +152,68 @@ def _gauss3(ua, ub, uc, ud, T):
             (rc * np.cos(angd)).astype(T))
 
 
-def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
+def _carry(i, f, T):
+    """Integer cell carry of an offset f (cells) added to cell index i: the
+    offset is brought back into [0, 1) (a rounding to exactly 1 moves on)."""
+    one = T(1.0)
+    k = np.clip(np.floor(f), T(-1048576.0), T(1048576.0))       # beyond this: outside anyway
+    f = (f - k).astype(T)
+    i = i + k.astype(np.int64)
+    fix = f >= one
+    f = np.where(fix, f - one, f).astype(T)
+    return i + fix, f
+
+
+def _window_charge(window_q, ir2, drn, qw, i_win, nr, T):
+    """Permanent window charge of particles absorbed on the window surface:
+    linear weights in R on the surface nodes."""
+    one = T(1.0)
+    rpos = ir2.astype(T) + drn
+    j0 = np.floor(rpos).astype(np.int64)
+    f = (rpos - j0.astype(T)).astype(T)
+    qd = np.full(j0.shape, qw, T)
+    np.add.at(window_q, (np.full(j0.shape, i_win), j0), (qd * (one - f)).astype(np.float64))
+    np.add.at(window_q, (np.full(j0.shape, i_win), np.minimum(j0 + 1, nr)), (qd * f).astype(np.float64))
+
+
+def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, window_q, stats):
+    """The implicit electrostatic kick of the previous step at the predicted
+    position (v += (q/m) dt E, x += (q/m) dt^2 E).  A correction through the
+    axis reflects (r -> -r, v_r -> -v_r); a correction out of the plasma region
+    absorbs the particle there (window charge on the window surface).
+    Returns the corrected arrays and the mask of particles still alive."""
+    nr, i_win = geo.cfg.nr, geo.i_win
+    vr_c = (vr + sc.qmd * Er).astype(T)
+    vz_c = (vz + sc.qmd * Ez).astype(T)
+    irc, drc = _carry(ir, (dr + sc.kres * Er).astype(T), T)
+    izc, dzc = _carry(iz, (dz + sc.kzes * Ez).astype(T), T)
+    neg = irc < 0
+    if np.any(neg):
+        rpos = (-(irc[neg].astype(T) + drc[neg])).astype(T)
+        j = np.floor(rpos)
+        irc[neg] = j.astype(np.int64)
+        drc[neg] = (rpos - j).astype(T)
+        vr_c[neg] = -vr_c[neg]
+    hit_e = izc < 0
+    hit_w = (~hit_e) & (irc >= nr)
+    hit_d = (~hit_e) & (~hit_w) & (izc >= i_win)
+    stats['absorbed'] += int(np.count_nonzero(hit_e | hit_w | hit_d))
+    if np.any(hit_d):
+        _window_charge(window_q, irc[hit_d], drc[hit_d], sc.qw, i_win, nr, T)
+    alive = ~(hit_e | hit_w | hit_d)
+    # electrostatic work of the kick with the mean of the pre- and post-kick velocities
+    half = T(0.5)
+    vbr = ((vr + vr_c) * half).astype(np.float64)
+    vbz = ((vz + vz_c) * half).astype(np.float64)
+    stats['p_es'] += float(np.sum(float(sc.qw) * (vbr[alive] * Er[alive].astype(np.float64) +
+                                                  vbz[alive] * Ez[alive].astype(np.float64))))
+    P['cell'][idx[~alive]] = DEAD
+    P['dr'][idx[~alive]] = T(0.0)
+    P['dz'][idx[~alive]] = T(0.0)
+    return irc, izc, drc, dzc, vr_c, vz_c, alive
+
+
+def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=False):
     """Advance one species one step in place.
 
     P: dict with int64 'cell' (DEAD when absorbed), T arrays 'dr','dz','vr',
@@ -145,6 +223,10 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     Q, J: FP64 node grids receiving the charge (C) at the new positions and the
        current moment q w vbar_theta (A m) at the old positions.
     window_q: FP64 node grid of the permanent window surface charge.
+    implicit: the direct-implicit form (module docstring): the stored state is
+       the predicted one; the gathered E_r, E_z are applied as the previous
+       step's implicit kick, the Boris step carries E_theta and B only, J is
+       taken at the corrected position and Q at the next predicted one.
     Returns the list of ionisation events (electrons only).
     """
     nr = geo.cfg.nr
@@ -165,6 +247,17 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     Et = _gather(F, cell, w, 2)
     Br = _gather(F, cell, w, 3)
     Bz = _gather(F, cell, w, 4)
+    n_entry = int(idx.size)
+
+    if implicit:
+        ir, iz, dr, dz, vr, vz, ok = _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo,
+                                                         T, window_q, stats)
+        idx, ir, iz, dr, dz, vr, vt, vz = (a[ok] for a in (idx, ir, iz, dr, dz, vr, vt, vz))
+        Et, Br, Bz = Et[ok], Br[ok], Bz[ok]
+        cell = iz * nr + ir
+        w = bilinear(dr, dz, T)             # current moment at the corrected position
+        Er = np.zeros_like(Et)
+        Ez = np.zeros_like(Et)
 
     # --- Boris in the local frame (x = r, y = theta, z); B_theta = 0 ----------
     hx, hy, hz = sc.qmh * Er, sc.qmh * Et, sc.qmh * Ez
@@ -189,9 +282,10 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), w):
         np.add.at(J, (iz + di, ir + dj), (jm * wk).astype(np.float64))
     stats['p_ind'] += float(np.sum(jm.astype(np.float64) * Et.astype(np.float64)))
-    stats['p_es'] += float(np.sum(sc.qw.astype(np.float64) *
-                                  (vbr.astype(np.float64) * Er.astype(np.float64) +
-                                   vbz.astype(np.float64) * Ez.astype(np.float64))))
+    if not implicit:
+        stats['p_es'] += float(np.sum(sc.qw.astype(np.float64) *
+                                      (vbr.astype(np.float64) * Er.astype(np.float64) +
+                                       vbz.astype(np.float64) * Ez.astype(np.float64))))
 
     # --- move ------------------------------------------------------------------
     a = vnx * sc.dtr
@@ -269,7 +363,7 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats):
     P['vr'][idx] = vr2
     P['vt'][idx] = vt2
     P['vz'][idx] = vnz
-    stats['pushed'] += int(idx.size)
+    stats['pushed'] += n_entry
     return events
 
 

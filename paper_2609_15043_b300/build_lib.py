@@ -1,9 +1,15 @@
 """Builds libphasorpic.so in-tree for sm_103a with nvcc.
 
-Flags: -gencode arch=compute_103a,code=sm_103a -lineinfo -O3 --fmad=false
-(no multiply-add contraction: the float32 decision path of the particle step
-then rounds exactly like the oracle's float32 instantiation).
+Flags: -gencode arch=compute_103a,code=sm_103a -lineinfo -O3.  The two
+particle-step sources (the fused FP32 kernel and the plain FP64 form) are
+compiled with --fmad=false: their cell crossings, absorptions and collision
+decisions then round exactly like the oracle's float32 / float64
+instantiations, and the arithmetic that decides nothing (deposit weights,
+moments, power tallies) is fused explicitly with fma intrinsics.  Every other
+source (field solves, period end, MLP) lets the compiler contract.  Sources
+compile in parallel to objects under _build/ and link into one library.
 """
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -12,6 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasorpic.so")
 SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu", "pp_mlp_train.cu", "pp_period.cu"]
+NO_CONTRACT = {"pp_particles.cu", "pp_plain.cu"}
+BUILD = os.path.join(HERE, "_build")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def nvcc():
@@ -30,21 +39,36 @@ def needs_build():
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def _compile(src, verbose):
+    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    cmd = [nvcc(), "-O3", "-std=c++17"] + ARCH + ["-lineinfo", "-Xcompiler", "-fPIC", "-c"]
+    if src in NO_CONTRACT:
+        cmd += ["--fmad=false"]
+    if verbose:
+        cmd += ["-Xptxas", "-v"]
+    cmd += ["-o", obj, os.path.join(CSRC, src)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return src, obj, r
+
+
 def build(force=False, verbose=False):
     if not force and not needs_build():
         return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-           "--fmad=false", "-Xcompiler", "-fPIC", "-shared", "-Xlinker", "-z", "-Xlinker", "defs",
-           "-o", LIB + ".tmp"]
-    if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, f) for f in SOURCES] + ["-lcudart"]
+    os.makedirs(BUILD, exist_ok=True)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        results = list(ex.map(lambda f: _compile(f, verbose), SOURCES))
+    for src, _, r in results:
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("nvcc failed compiling %s" % src)
+        if verbose:
+            sys.stderr.write(r.stderr)
+    cmd = [nvcc()] + ARCH + ["-shared", "-Xlinker", "-z", "-Xlinker", "defs", "-o", LIB + ".tmp"]
+    cmd += [obj for _, obj, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libphasorpic.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libphasorpic.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -518,11 +518,13 @@ __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi
         if (j == 0) Er = 0.0;
         else if (j == NR - 1) Er = -(phi[n] - phi[n - 1]) / dr;
         else Er = -(phi[n + 1] - phi[n - 1]) / (2.0 * dr);
-        double Et = Ec[n] * cs - Ess[n] * sn;
+        // products and sums rounded separately (no contraction): the gather
+        // fields then round to float exactly as the oracle's FP64 -> float32
+        double Et = __dsub_rn(__dmul_rn(Ec[n], cs), __dmul_rn(Ess[n], sn));
         double Br = 0.0, Bz = 0.0;
         if (magnetic) {
-            Br = B[n] * cs + B[nnodes + n] * sn;
-            Bz = B[2 * nnodes + n] * cs + B[3 * nnodes + n] * sn;
+            Br = __dadd_rn(__dmul_rn(B[n], cs), __dmul_rn(B[nnodes + n], sn));
+            Bz = __dadd_rn(__dmul_rn(B[2 * nnodes + n], cs), __dmul_rn(B[3 * nnodes + n], sn));
         }
         s_v[q][0] = (T)Er;
         s_v[q][1] = (T)Ez;
@@ -693,8 +695,8 @@ __global__ void bphasor_kernel(const double* Ec, const double* Ess, double* B, i
     auto curl = [&](const double* f) {
         if (j == 0) return 2.0 * (f[n + 1] - f[n]) / dr;
         double R = j * dr;
-        if (j == NR - 1) return (R * f[n] - (R - dr) * f[n - 1]) / (dr * R);
-        return ((R + dr) * f[n + 1] - (R - dr) * f[n - 1]) / (2.0 * dr * R);
+        if (j == NR - 1) return __dsub_rn(__dmul_rn(R, f[n]), __dmul_rn(R - dr, f[n - 1])) / (dr * R);
+        return __dsub_rn(__dmul_rn(R + dr, f[n + 1]), __dmul_rn(R - dr, f[n - 1])) / (2.0 * dr * R);
     };
     B[n] = ddz(Ess) / omega;
     B[nn + n] = ddz(Ec) / omega;

@@ -35,7 +35,8 @@ constexpr int kPPT = PP_PPT;                      // particles per thread per ch
 constexpr int kChunk = kPushThreads * kPPT;
 constexpr int kTileRows = 8;                      // node rows of the shared deposit tile
 constexpr int kMaxNR = 513;                       // node columns supported by the tile
-constexpr int kEventCap = 8192;                   // ionisation events per step
+constexpr int kEventMin = 8192;                   // ionisation events per step, at least
+constexpr int kAppendThreads = 1024;              // events ranked per block of the append kernel
 constexpr int kMaxCapNodes = 128;                 // turn nodes handled by the capacitance matrix
 constexpr int kMaxPcrLevels = 10;                 // cyclic reduction of z systems of up to 1024 rows
 
@@ -92,6 +93,7 @@ struct DevState {
     unsigned long long step;                 // PIC steps completed (drives the RNG counters)
     unsigned int status;
     int n_events;                            // events recorded this step
+    int append_done;                         // blocks of the append kernel that finished ranking
     int accepted;                            // last period end accepted
     long long period;
     int has_record;
@@ -163,6 +165,8 @@ struct Cell {
     uint32_t* d_next_uid = nullptr;         // [2]
     uint32_t* d_hist = nullptr;             // counting-sort bins (ncell + 2)
     Event* d_events = nullptr;
+    int event_cap = 0;                      // ionisation events one step can record
+    uint32_t* d_ev_perm = nullptr;          // events in parent-uid order (append kernel)
 
     // grids
     double* d_phi = nullptr;

@@ -120,6 +120,7 @@ template <typename T>
 struct CollCtx {
     uint32_t key0, key1;
     EventT<T>* ev;
+    int ev_cap;
     DevState* st;
     T vth_gas_ion;
 };
@@ -169,7 +170,7 @@ __device__ __forceinline__ void electron_collision(const CollCtx<T>& a, uint32_t
         iso_dir(T(a1.a), T(a1.b), ex_, ey_, ez_);
         gauss3(T(a1.c), T(a1.d), T(b1.a), T(b1.b), g0, g1, g2);
         int slot = atomicAdd(&a.st->n_events, 1);
-        if (slot < kEventCap) {
+        if (slot < a.ev_cap) {
             EventT<T> e;
             e.parent = uid;
             e.cell = cell;

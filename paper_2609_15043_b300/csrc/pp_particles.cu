@@ -198,6 +198,7 @@ struct PushArgs {
     const unsigned long long* step;  // device step counter (RNG counter word)
     uint32_t key0, key1;
     Event* ev;
+    int ev_cap;
     DevState* st;
 };
 
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         __syncthreads();
         // ---- phase B: collisions of the candidates
         const int nc = s_ncand;
-        const CollCtx<float> cc{a.key0, a.key1, a.ev, a.st, a.sp[1].vth_gas};
+        const CollCtx<float> cc{a.key0, a.key1, a.ev, a.ev_cap, a.st, a.sp[1].vth_gas};
         if (t < nc) {
             unsigned pc[6] = {0, 0, 0, 0, 0, 0};
             for (int c = t; c < nc; c += kPushThreads) {
@@ -599,6 +600,7 @@ void launch_push(Cell* c, cudaStream_t st) {
     a.key0 = (uint32_t)(c->cfg.seed & 0xffffffffu);
     a.key1 = (uint32_t)(c->cfg.seed >> 32);
     a.ev = c->d_events;
+    a.ev_cap = c->event_cap;
     a.st = c->d_st;
     size_t shm = PushSmem::bytes(c->NR);
     push_prepare(c);
@@ -638,65 +640,54 @@ void launch_deposit_only(Cell* c, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- append events
-// One block: sort this step's events by parent uid (bitonic, in shared
-// memory) and append the e- / Ar+ pairs with uid = next_uid + rank.
+// The step's ionisation events are appended as e- / Ar+ pairs with uid =
+// next_uid + rank, rank = the event's position in parent-uid order (a parent
+// ionises at most once per step, so the parent uids are distinct and the rank
+// of an event is the number of events with a smaller parent uid).  Block b
+// ranks events [b*kAppendThreads, (b+1)*kAppendThreads) against all events,
+// staged through shared memory in tiles, and scatters their indices into
+// `perm`; the last block to finish (arrival counter, no waiting) writes the
+// pairs and updates the slot counts, uids and counters.  The grid covers the
+// event capacity; blocks beyond the step's event count return at once.
 template <typename T>
-__global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next_uid, const EventT<T>* ev,
-                              DevState* st, int64_t cap_e, int64_t cap_i) {
-    __shared__ uint32_t key[kEventCap];
-    __shared__ uint16_t val[kEventCap];
-    int n_ev = min(st->n_events, kEventCap);
-    if (n_ev == 0) return;
-    int P2 = 1;
-    while (P2 < n_ev) P2 <<= 1;
-    for (int q = threadIdx.x; q < P2; q += blockDim.x) {
-        key[q] = (q < n_ev) ? ev[q].parent : 0xFFFFFFFFu;
-        val[q] = (uint16_t)q;
+__global__ void __launch_bounds__(kAppendThreads) append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot,
+                                                                uint32_t* next_uid, const EventT<T>* ev,
+                                                                uint32_t* perm, int ev_cap, DevState* st,
+                                                                int64_t cap_e, int64_t cap_i) {
+    constexpr int kTile = 4096;
+    __shared__ uint32_t tile[kTile];
+    __shared__ int s_last;
+    const int n_ev = min(st->n_events, ev_cap);
+    const int first = blockIdx.x * kAppendThreads;
+    if (n_ev == 0 || first >= n_ev) return;
+    const int nblk = (n_ev + kAppendThreads - 1) / kAppendThreads;
+    const int q = first + (int)threadIdx.x;
+    const uint32_t kq = (q < n_ev) ? ev[q].parent : 0u;
+    int rank = 0;
+    for (int base = 0; base < n_ev; base += kTile) {
+        const int m = min(kTile, n_ev - base);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kAppendThreads) tile[j] = ev[base + j].parent;
+        __syncthreads();
+        if (q < n_ev)
+            for (int j = 0; j < m; ++j) rank += tile[j] < kq ? 1 : 0;
     }
+    if (q < n_ev) perm[rank] = (uint32_t)q;
+    // the last block to arrive sees every rank
+    __threadfence();
     __syncthreads();
-    if (n_ev <= 256) {
-        // few events (the usual case): a parent has at most one ionisation per
-        // step, so the keys are distinct and an event's rank is the number of
-        // smaller keys -- one pass instead of the sorting network
-        int rank = 0;
-        uint32_t kq = 0;
-        const int q = threadIdx.x;
-        if (q < n_ev) {
-            kq = key[q];
-            for (int j = 0; j < n_ev; ++j) rank += key[j] < kq ? 1 : 0;
-        }
-        __syncthreads();
-        if (q < n_ev) val[rank] = (uint16_t)q;
-        __syncthreads();
-        P2 = 0;                          // skip the network below
-    }
-    for (int k = 2; k <= P2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int q = threadIdx.x; q < P2; q += blockDim.x) {
-                int l = q ^ j;
-                if (l > q) {
-                    bool up = (q & k) == 0;
-                    uint32_t kq = key[q], kl = key[l];
-                    if ((kq > kl) == up) {
-                        key[q] = kl;
-                        key[l] = kq;
-                        uint16_t t = val[q];
-                        val[q] = val[l];
-                        val[l] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    int ne = nslot[0], ni = nslot[1];
+    if (threadIdx.x == 0) s_last = (atomicAdd(&st->append_done, 1) == nblk - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int ne = nslot[0], ni = nslot[1];
     int n_add = n_ev;
     if ((int64_t)ne + n_add > cap_e) n_add = (int)(cap_e - ne);
     if ((int64_t)ni + n_add > cap_i) n_add = (int)(cap_i - ni);
     if (n_add < 0) n_add = 0;
-    uint32_t ue = next_uid[0], ui = next_uid[1];
-    for (int r = threadIdx.x; r < n_add; r += blockDim.x) {
-        const EventT<T> e = ev[val[r]];
+    const uint32_t ue = next_uid[0], ui = next_uid[1];
+    for (int r = threadIdx.x; r < n_add; r += kAppendThreads) {
+        const EventT<T> e = ev[((volatile uint32_t*)perm)[r]];
         pe.cell[ne + r] = e.cell;
         pe.dr[ne + r] = e.dr;
         pe.dz[ne + r] = e.dz;
@@ -724,16 +715,20 @@ __global__ void append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot, uint32_t* next
         st->per[C_CREATED] += (unsigned long long)n_add;
         if (n_add < n_ev) st->status |= PP_ST_CAPACITY;
         st->n_events = 0;
+        st->append_done = 0;
     }
 }
 
 void launch_append(Cell* c, cudaStream_t st) {
+    const unsigned nb = (unsigned)((c->event_cap + kAppendThreads - 1) / kAppendThreads);
     if (c->fp64)
-        append_kernel<double><<<1, 1024, 0, st>>>(c->pd[0][c->cur[0]], c->pd[1][c->cur[1]], c->d_nslot,
-                                                  c->d_next_uid, c->d_events64, c->d_st, c->cap[0], c->cap[1]);
+        append_kernel<double><<<nb, kAppendThreads, 0, st>>>(c->pd[0][c->cur[0]], c->pd[1][c->cur[1]], c->d_nslot,
+                                                             c->d_next_uid, c->d_events64, c->d_ev_perm,
+                                                             c->event_cap, c->d_st, c->cap[0], c->cap[1]);
     else
-        append_kernel<float><<<1, 1024, 0, st>>>(c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot,
-                                                 c->d_next_uid, c->d_events, c->d_st, c->cap[0], c->cap[1]);
+        append_kernel<float><<<nb, kAppendThreads, 0, st>>>(c->pb[0][c->cur[0]], c->pb[1][c->cur[1]], c->d_nslot,
+                                                            c->d_next_uid, c->d_events, c->d_ev_perm, c->event_cap,
+                                                            c->d_st, c->cap[0], c->cap[1]);
     count_launch();
 }
 

@@ -23,6 +23,7 @@ struct PlainArgs {
     const unsigned long long* step;
     uint32_t key0, key1;
     EventT<T>* ev;
+    int ev_cap;
     DevState* st;
 };
 
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
     const int n0 = a.nslot[0], n1 = a.nslot[1];
     const int nr = a.nr, NR = a.NR;
     const uint32_t step = (uint32_t)(*a.step);
-    const CollCtx<T> cc{a.key0, a.key1, a.ev, a.st, a.sp[1].vth_gas};
+    const CollCtx<T> cc{a.key0, a.key1, a.ev, a.ev_cap, a.st, a.sp[1].vth_gas};
     const T one = T(1.0);
     double acc_ind = 0.0, acc_es = 0.0;
     // 0..4 processes, 5 nu violations, 6 pushed, 7 absorbed e, 8 absorbed i
@@ -217,6 +218,7 @@ void launch_push_plain(Cell* c, cudaStream_t st) {
     a.key0 = (uint32_t)(c->cfg.seed & 0xffffffffu);
     a.key1 = (uint32_t)(c->cfg.seed >> 32);
     a.ev = c->d_events64;
+    a.ev_cap = c->event_cap;
     a.st = c->d_st;
     // grid: a whole number of waves of 8 blocks per SM over the slots of both species
     int dev = 0, nsm = 148;

@@ -396,8 +396,18 @@ int setup_cell(Cell* c) {
             }
         }
     }
+    // ionisation events of one step: at least kEventMin, else 1/64 of the
+    // electron capacity (a step that creates more than 1.5 % of the
+    // population in pairs is far outside any regime the method resolves)
+    {
+        int64_t ec = (c->cap[0] + 63) / 64;
+        ec = ec < kEventMin ? kEventMin : ec;
+        ec = ec > (int64_t)1 << 22 ? (int64_t)1 << 22 : ec;
+        c->event_cap = (int)((ec + kAppendThreads - 1) / kAppendThreads * kAppendThreads);
+    }
+    c->d_ev_perm = c->alloc<uint32_t>(c->event_cap);
     if (c->fp64) {
-        c->d_events64 = c->alloc<EventT<double>>(kEventCap);
+        c->d_events64 = c->alloc<EventT<double>>(c->event_cap);
         c->d_F64 = c->alloc<double>((size_t)c->i_win * f.nr * 20);
         c->d_rho64 = c->alloc<double>(c->nnodes);
         c->d_jm64 = c->alloc<double>(c->nnodes);
@@ -405,7 +415,7 @@ int setup_cell(Cell* c) {
     c->d_nslot = c->alloc<int>(2);
     c->d_next_uid = c->alloc<uint32_t>(2);
     c->d_hist = c->alloc<uint32_t>((size_t)c->i_win * c->nr + 2);
-    c->d_events = c->alloc<Event>(kEventCap);
+    c->d_events = c->alloc<Event>(c->event_cap);
     c->d_phi = c->alloc<double>(c->nnodes);
     c->d_F = c->alloc<float>((size_t)c->i_win * c->nr * 20);
     c->d_rho = c->alloc<float>(c->nnodes);

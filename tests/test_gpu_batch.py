@@ -74,3 +74,34 @@ def test_batch_rejects_cells_off_the_period_boundary():
     with pytest.raises(pp.PhasorPICError):
         batch.advance_period(1)
     batch.close()
+
+
+def test_batch_cells_against_oracle():
+    """Each cell of a batch against the oracle over one period (the oracle
+    runs each cell alone): the particle-free cell to rounding, the ions-only
+    cells to the period tolerances of the single-cell parity tests."""
+    require_gpu()
+    from paper_2609_15043_b300 import phasorpic as pp
+    from gpu_common import oracle_cell
+    cfgs, pops = _cases()
+    batch = pp.Batch(cfgs)
+    for c, p in zip(batch.cells, pops):
+        for sp in (0, 1):
+            c.set_particles(sp, p[sp])
+    batch.advance_period(1)
+    for i, (cfg, p, b) in enumerate(zip(cfgs, pops, batch.cells)):
+        oc = oracle_cell(cfg, p)
+        oc.prime(np.float32)
+        for _ in range(oc.n_rf):
+            oc.step(np.float32)
+        ro, rb = oc.records[-1], b.turn_phasors()
+        assert rb["n_samples"] == ro["n_samples"] == oc.n_rf, i
+        assert rb["n_live"] == ro["n_live"], i
+        tol = 1e-8 if i == 0 else 1e-3
+        for k in ("icap", "qhat"):
+            assert _rel(rb[k], ro[k]) < tol, (i, k, _rel(rb[k], ro[k]))
+        assert _rel(rb["x_next"], ro["x_next"]) < (1e-9 if i == 0 else 1e-4), i
+        if i > 0:
+            assert _rel(rb["vp"], ro["vp"]) < 1e-3, i
+        assert b.status() == 0
+    batch.close()

@@ -50,3 +50,36 @@ def test_deposit_conserves_charge_at_bench_size():
     q = g.grid(pp.GRID_CHARGE)
     assert abs(q.sum() - total) <= 1e-5 * qe * w * c["live_i"]
     g.close()
+
+
+def test_event_buffer_scales_with_the_population():
+    """The step's event buffer holds 1/64 of the electron capacity (at least
+    8192): with room for 4e6 electrons, a burst of well over 8192 ionisations
+    in one step is appended in full, in parent-uid order, exactly as the
+    oracle appends it (new pairs, uids, cells and offsets bit-exact)."""
+    require_gpu()
+    from paper_2609_15043_b300 import workloads
+    from gpu_common import oracle_cell, oracle_live, by_uid
+    cfg = workloads.small().replace(n_init=100000, te_ev=60.0, pressure_pa=3.0 * 133.322368,
+                                    capacity_factor=40.0)
+    pops = [workloads.population(cfg, sp) for sp in (0, 1)]
+    oc = oracle_cell(cfg, pops)
+    oc.prime(np.float32)
+    g = gpu_cell(cfg, pops)
+    g.set_potential(oc.phi)
+    g.advance_steps(1)
+    info = oc.step(np.float32)
+    c = g.counters()
+    assert c["e_ionisation"] > EVENT_CAP
+    assert c["created"] == c["e_ionisation"] == info["events"]
+    assert g.status() == 0
+    for sp in (0, 1):
+        pg = by_uid(g.get_particles(sp))
+        po = oracle_live(oc.P[sp])
+        assert np.array_equal(pg["uid"], po["uid"].astype(np.uint32))
+        assert np.array_equal(pg["cell"], po["cell"].astype(np.uint32))
+        new = pg["uid"] >= cfg.n_init
+        assert np.sum(new) == info["events"]
+        for k in ("dr", "dz"):
+            assert np.array_equal(pg[k][new], po[k][new])
+    g.close()

@@ -106,3 +106,58 @@ def test_graph_period_equals_step_loop():
     assert a.turn_phasors()["period"] == 1 and a.counters()["steps"] == 2 * a.n_rf
     a.close()
     b.close()
+
+
+def _periods_pair(cfg, pops, n_periods):
+    oc = oracle_cell(cfg, pops)
+    oc.prime(np.float32)
+    g = gpu_cell(cfg, pops)
+    g.set_potential(oc.phi)
+    recs = []
+    for _ in range(n_periods):
+        for _ in range(oc.n_rf):
+            oc.step(np.float32)
+        g.advance_steps(g.n_rf)
+        recs.append((oc.records[-1], g.turn_phasors()))
+    return oc, g, recs
+
+
+def test_controller_particle_free_periods_against_oracle():
+    """The port-power controller (Eqs. pfilter, ptrend, pcontrol with the
+    symmetric limiter) on the device against the oracle's PowerController over
+    four particle-free periods: the filtered power carries state from period
+    to period, so every period's V_g and relaxed state must agree."""
+    require_gpu()
+    from paper_2609_15043_b300 import workloads
+    cfg = workloads.small().replace(power_control=1, p_target=3.0)
+    oc, g, recs = _periods_pair(cfg, _pops(cfg, False, False), 4)
+    moved = 0
+    for ro, rg in recs:
+        assert rg["accepted"] and rg["n_samples"] == oc.n_rf
+        assert rg["vg"] == pytest.approx(ro["vg"], rel=1e-12)
+        assert rg["p_port"] == pytest.approx(ro["p_port"], rel=1e-9)
+        assert rg["vg_next"] == pytest.approx(ro["vg_next"], rel=1e-12)
+        assert _rel(rg["x_next"], ro["x_next"]) < 1e-9
+        moved += rg["vg_next"] != rg["vg"]
+    assert moved == len(recs)                  # the controller acted every period
+    assert g.status() == 0
+    g.close()
+
+
+def test_controller_ions_only_periods_against_oracle():
+    """The controller with a kinetic load (ions only, no gas) over two
+    periods: the first period's V_g update sees the same applied state on
+    both sides, the second one the relaxed states of the first."""
+    require_gpu()
+    from paper_2609_15043_b300 import workloads
+    cfg = workloads.small().replace(pressure_pa=0.0, power_control=1, p_target=3.0)
+    oc, g, recs = _periods_pair(cfg, _pops(cfg, False, True), 2)
+    (ro1, rg1), (ro2, rg2) = recs
+    assert rg1["vg_next"] == pytest.approx(ro1["vg_next"], rel=1e-9)
+    assert rg2["vg"] == pytest.approx(ro2["vg"], rel=1e-9)
+    assert rg2["vg_next"] == pytest.approx(ro2["vg_next"], rel=1e-4)
+    for ro, rg in recs:
+        assert _rel(rg["x_next"], ro["x_next"]) < 1e-4
+        assert rg["p_port"] == pytest.approx(ro["p_port"], rel=1e-4)
+    assert g.status() == 0
+    g.close()
