@@ -101,7 +101,12 @@ typedef struct pp_config {
                                         state, global atomics), the comparison baseline of the
                                         default fused FP32 kernel; fields and circuit are FP64 in
                                         both forms */
-    int32_t reserved0;               /* must be 0 */
+    int32_t implicit_es;             /* 1: direct-implicit electrostatics (Sec. 2.3, Eqs. poisson,
+                                        epseff, implicit_charge_relation): the particle store holds
+                                        predicted states, the electrostatic kick of a step is applied
+                                        by the next step's pass with the field solved with the
+                                        susceptibility chi of the predicted populations; 0: explicit
+                                        leapfrog (chi = 0) */
 } pp_config;
 
 /* Completed-period record (Sec. 2.4 diagnostics; Eqs. vpind, icap, pport,
@@ -393,6 +398,8 @@ int pp_get_vacuum_impedance(pp_cell* cell, double* zvac, double* eps_rec, double
 #define PP_GRID_WINDOW 5         /* permanent window surface charge (C) */
 #define PP_GRID_CHARGE 6         /* charge deposited in the last step (C) */
 #define PP_GRID_JMOM 7           /* q w vbar_theta deposited in the last step (A m) */
+#define PP_GRID_CHARGE_E 8       /* the electrons' part of PP_GRID_CHARGE (C) */
+#define PP_GRID_CHARGE_I 9       /* the ions' part of PP_GRID_CHARGE (C) */
 #define PP_GRID_U0 16            /* unit field U_k is PP_GRID_U0 + k */
 
 int pp_get_grid(pp_cell* cell, int which, double* host, int64_t n, void* stream);
@@ -457,9 +464,11 @@ int pp_get_counters(pp_cell* cell, int64_t* out, void* stream);
 
 /*
  * pp_get_poisson_stats -- diagnostics of the most recent Poisson solve: *sweeps
- * gets the FP64 residual evaluations made (refinement sweeps + 1) and rel[k]
- * (16 entries) the relative residual max|b - A phi| / max(|b| + sum|A_ij phi_j|)
- * before sweep k (turn nodes contribute their Dirichlet mismatch).
+ * gets the FP64 residual evaluations made (refinement sweeps + 1, or CG
+ * iterations + 1 for the persistent CG solve) and rel[k] (16 entries) the
+ * relative residual max|b - A phi| / max(|b| + sum|A_ij phi_j|) before sweep k
+ * (turn nodes contribute their Dirichlet mismatch); the CG solve reports only
+ * its final value, in rel[min(sweeps - 1, 15)], the other entries 0.
  * Synchronises `stream`.
  */
 int pp_get_poisson_stats(pp_cell* cell, int* sweeps, double* rel, void* stream);

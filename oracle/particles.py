@@ -185,6 +185,10 @@ def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, win
     nr, i_win = geo.cfg.nr, geo.i_win
     vr_c = (vr + sc.qmd * Er).astype(T)
     vz_c = (vz + sc.qmd * Ez).astype(T)
+    # electrostatic work of the kick with the mean of the pre- and post-kick velocities
+    half = T(0.5)
+    vbr = ((vr + vr_c) * half).astype(np.float64)
+    vbz = ((vz + vz_c) * half).astype(np.float64)
     irc, drc = _carry(ir, (dr + sc.kres * Er).astype(T), T)
     izc, dzc = _carry(iz, (dz + sc.kzes * Ez).astype(T), T)
     neg = irc < 0
@@ -201,10 +205,6 @@ def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, win
     if np.any(hit_d):
         _window_charge(window_q, irc[hit_d], drc[hit_d], sc.qw, i_win, nr, T)
     alive = ~(hit_e | hit_w | hit_d)
-    # electrostatic work of the kick with the mean of the pre- and post-kick velocities
-    half = T(0.5)
-    vbr = ((vr + vr_c) * half).astype(np.float64)
-    vbz = ((vz + vz_c) * half).astype(np.float64)
     stats['p_es'] += float(np.sum(float(sc.qw) * (vbr[alive] * Er[alive].astype(np.float64) +
                                                   vbz[alive] * Ez[alive].astype(np.float64))))
     P['cell'][idx[~alive]] = DEAD

@@ -17,7 +17,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasorpic.so")
-SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu", "pp_mlp_train.cu", "pp_period.cu"]
+SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_pcg.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu",
+           "pp_mlp_train.cu", "pp_period.cu"]
 NO_CONTRACT = {"pp_particles.cu", "pp_plain.cu"}
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

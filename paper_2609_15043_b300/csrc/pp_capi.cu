@@ -639,9 +639,9 @@ int pp_prime(pp_cell* h, void* stream) {
 namespace pp {
 static int pp_prime_on(Cell* c, cudaStream_t st) {
     if (c->fp64)
-        cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * c->nnodes, st);
+        cudaMemsetAsync(c->d_rho64, 0, sizeof(double) * 2 * c->nnodes, st);
     else
-        cudaMemsetAsync(c->d_rho, 0, sizeof(float) * c->nnodes, st);
+        cudaMemsetAsync(c->d_rho, 0, sizeof(float) * 2 * c->nnodes, st);
     launch_deposit_only(c, st);
     double th = theta(c, c->s);
     poisson_refine(c, std::cos(th), std::sin(th), st, false, nullptr);
@@ -1023,15 +1023,27 @@ int pp_get_grid(pp_cell* h, int which, double* host, int64_t n, void* stream) {
         case PP_GRID_JS: src = c->d_Js; break;
         case PP_GRID_WINDOW: src = c->d_win; break;
         case PP_GRID_CHARGE:
+        case PP_GRID_CHARGE_E:
+        case PP_GRID_CHARGE_I:
         case PP_GRID_JMOM: {
-            if (c->fp64) {
-                src = which == PP_GRID_CHARGE ? c->d_rho64 : c->d_jm64;
-                break;
+            // the charge is held per species; PP_GRID_CHARGE is their sum
+            const int p0 = which == PP_GRID_CHARGE_I ? 1 : 0;
+            const int p1 = which == PP_GRID_CHARGE ? 2 : p0 + 1;
+            const bool charge = which != PP_GRID_JMOM;
+            for (int q = 0; q < c->nnodes; ++q) host[q] = 0.0;
+            for (int part = p0; part < p1; ++part) {
+                if (c->fp64) {
+                    std::vector<double> tmp(c->nnodes);
+                    cudaMemcpy(tmp.data(), (charge ? c->d_rho64 : c->d_jm64) + (size_t)part * c->nnodes,
+                               sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
+                    for (int q = 0; q < c->nnodes; ++q) host[q] += tmp[q];
+                } else {
+                    std::vector<float> tmp(c->nnodes);
+                    cudaMemcpy(tmp.data(), (charge ? c->d_rho : c->d_jm) + (size_t)part * c->nnodes,
+                               sizeof(float) * c->nnodes, cudaMemcpyDeviceToHost);
+                    for (int q = 0; q < c->nnodes; ++q) host[q] += (double)tmp[q];
+                }
             }
-            std::vector<float> tmp(c->nnodes);
-            cudaMemcpy(tmp.data(), which == PP_GRID_CHARGE ? c->d_rho : c->d_jm, sizeof(float) * c->nnodes,
-                       cudaMemcpyDeviceToHost);
-            for (int q = 0; q < c->nnodes; ++q) host[q] = tmp[q];
             return cuda_check(cudaGetLastError(), "pp_get_grid");
         }
         default:
@@ -1067,16 +1079,16 @@ int pp_poisson_solve(pp_cell* h, const double* q, const double* turn_phi, double
     cudaDeviceSynchronize();
     // stash the step state that the standalone solve overwrites
     std::vector<double> phi_save(c->nnodes), win_save(c->nnodes);
-    std::vector<float> rho_save(c->nnodes);
+    std::vector<float> rho_save((size_t)2 * c->nnodes);
     cudaMemcpy(phi_save.data(), c->d_phi, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
     cudaMemcpy(win_save.data(), c->d_win, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
-    cudaMemcpy(rho_save.data(), c->d_rho, sizeof(float) * c->nnodes, cudaMemcpyDeviceToHost);
-    std::vector<double> rho64_save(c->fp64 ? c->nnodes : 0);
-    if (c->fp64) cudaMemcpy(rho64_save.data(), c->d_rho64, sizeof(double) * c->nnodes, cudaMemcpyDeviceToHost);
+    cudaMemcpy(rho_save.data(), c->d_rho, sizeof(float) * 2 * c->nnodes, cudaMemcpyDeviceToHost);
+    std::vector<double> rho64_save(c->fp64 ? (size_t)2 * c->nnodes : 0);
+    if (c->fp64) cudaMemcpy(rho64_save.data(), c->d_rho64, sizeof(double) * 2 * c->nnodes, cudaMemcpyDeviceToHost);
     // the charge goes in FP64 through the window array (exact), rho = 0
     cudaMemcpy(c->d_win, q, sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
-    cudaMemset(c->d_rho, 0, sizeof(float) * c->nnodes);
-    if (c->fp64) cudaMemset(c->d_rho64, 0, sizeof(double) * c->nnodes);
+    cudaMemset(c->d_rho, 0, sizeof(float) * 2 * c->nnodes);
+    if (c->fp64) cudaMemset(c->d_rho64, 0, sizeof(double) * 2 * c->nnodes);
     cudaMemset(c->d_phi, 0, sizeof(double) * c->nnodes);
     cudaMemcpy(c->d_ext_targets, turn_phi, sizeof(double) * c->nturns, cudaMemcpyHostToDevice);
     poisson_refine(c, 1.0, 0.0, 0, true, c->d_ext_targets);
@@ -1103,8 +1115,8 @@ int pp_poisson_solve(pp_cell* h, const double* q, const double* turn_phi, double
     }
     cudaMemcpy(c->d_phi, phi_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_win, win_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
-    cudaMemcpy(c->d_rho, rho_save.data(), sizeof(float) * c->nnodes, cudaMemcpyHostToDevice);
-    if (c->fp64) cudaMemcpy(c->d_rho64, rho64_save.data(), sizeof(double) * c->nnodes, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_rho, rho_save.data(), sizeof(float) * 2 * c->nnodes, cudaMemcpyHostToDevice);
+    if (c->fp64) cudaMemcpy(c->d_rho64, rho64_save.data(), sizeof(double) * 2 * c->nnodes, cudaMemcpyHostToDevice);
     return rc;
 }
 
@@ -1166,7 +1178,11 @@ int pp_get_poisson_stats(pp_cell* h, int* sweeps, double* rel, void* stream) {
     if (rc) return rc;
     int n = c->h_st->piters + 1;
     if (sweeps) *sweeps = n;
-    if (rel)
+    if (rel && c->use_pcg) {
+        // the CG solve keeps only its final relative residual
+        for (int k = 0; k < 16; ++k) rel[k] = 0.0;
+        rel[n - 1 < 15 ? n - 1 : 15] = c->h_st->prel;
+    } else if (rel)
         for (int k = 0; k < 16; ++k) {
             double r = 0, sc = 0;
             memcpy(&r, &c->h_st->pnorm[2 * k], sizeof(double));

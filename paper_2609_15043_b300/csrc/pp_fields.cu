@@ -261,7 +261,9 @@ __device__ __forceinline__ double turn_target(const DevState* st, const double* 
 struct PoisArgs {
     const double* phi;
     const float* rho;
+    const float* rho_i;            // ion charge (added when set)
     const double* rho64;           // node charge of the plain FP64 form (used when set)
+    const double* rho64_i;
     const double* win;
     const double* eps_row;
     const double* az;
@@ -307,7 +309,8 @@ __global__ void poisson_residual(PoisArgs a) {
             double t2 = a.az[j] * emz * (a.phi[n - a.NR] - pc);
             double t3 = eb * a.arp[j] * (a.phi[n + 1] - pc);
             double t4 = (j > 0) ? eb * a.arm[j] * (a.phi[n - 1] - pc) : 0.0;
-            double q = a.rho64 ? a.rho64[n] : (double)a.rho[n];
+            double q = a.rho64 ? a.rho64[n] + (a.rho64_i ? a.rho64_i[n] : 0.0)
+                               : (double)a.rho[n] + (a.rho_i ? (double)a.rho_i[n] : 0.0);
             double b = -(q + a.win[n]) * a.inv2pieps0;
             double r = b - (((t1 + t2) + t3) + t4);
             a.r32[idx] = (float)r;
@@ -510,7 +513,8 @@ __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi
         // row and column by the tiles at the edge)
         const bool own = (q / (kFpCols + 1) < kFpRows || i == i_win) && (q % (kFpCols + 1) < kFpCols || j == NR - 1);
         if (own) {
-            rho[n] = T(0);
+            rho[n] = T(0);              // electrons
+            rho[nnodes + n] = T(0);     // ions
             jm[n] = T(0);
         }
         double Ez = (i == 0) ? -(phi[n + NR] - phi[n]) / dz : -(phi[n + NR] - phi[n - NR]) / (2.0 * dz);
@@ -765,6 +769,18 @@ void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_
 
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
                    const double* d_targets, bool in_step) {
+    if (c->use_pcg) {
+        // turn potentials and fresh bookkeeping (inside a step the field
+        // preparation has imposed them already), then the persistent solve
+        if (!in_step) {
+            const int K = c->ntn;
+            poisson_set_turns<<<(K + 63) / 64 > 0 ? (K + 63) / 64 : 1, 64, 0, st>>>(
+                c->d_phi, c->d_tn_node, c->d_tn_k, K, c->d_st, external_targets ? d_targets : nullptr, c->nturns,
+                cs, sn);
+            count_launch();
+        }
+        return pcg_refine(c, cs, sn, st, external_targets ? d_targets : nullptr, in_step);
+    }
     int rows = c->ps.rows, M = c->ps.M;
     int nint = rows * M;
     int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
@@ -774,7 +790,9 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     PoisArgs a;
     a.phi = c->d_phi;
     a.rho = c->d_rho;
+    a.rho_i = c->d_rho + c->nnodes;
     a.rho64 = c->fp64 ? c->d_rho64 : nullptr;
+    a.rho64_i = c->fp64 ? c->d_rho64 + c->nnodes : nullptr;
     a.win = c->d_win;
     a.eps_row = c->d_eps_row;
     a.az = c->d_az;
@@ -909,7 +927,9 @@ extern "C" int pp_poisson_solve_noalloc(pp_cell* h, const double* d_q, const dou
     PoisArgs a;
     a.phi = d_phi;
     a.rho = rho0;
+    a.rho_i = nullptr;
     a.rho64 = nullptr;
+    a.rho64_i = nullptr;
     a.win = d_q;
     a.eps_row = c->d_eps_row;
     a.az = c->d_az;

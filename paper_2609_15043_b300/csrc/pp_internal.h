@@ -58,6 +58,7 @@ using ParticleBuf = PBuf<float>;
 template <typename T>
 struct SpecT {          // constants of one species in T (rounded once from FP64)
     T qmh, dtr, dtz, qw, numax, pnull, ng, ce, inv_ce, loss, vth_gas;
+    T qmd, kres, kzes;  // direct-implicit kick: (q/m) dt, (q/m) dt^2 / dr, (q/m) dt^2 / dz
 };
 using SpeciesConst = SpecT<float>;
 
@@ -108,6 +109,7 @@ struct DevState {
     unsigned long long pnorm[2 * 16];
     int pdone;
     int push_chunk;                          // next chunk of the particle kernel's dynamic schedule
+    int phi_prev_ok;                         // the previous step's potential is stored (CG initial guess)
     int piters;
     double prel;
 };
@@ -155,7 +157,7 @@ struct Cell {
     SpecT<double> scd[2];
     EventT<double>* d_events64 = nullptr;
     double* d_F64 = nullptr;
-    double* d_rho64 = nullptr;
+    double* d_rho64 = nullptr;              // electrons, then ions (2 x nnodes)
     double* d_jm64 = nullptr;
     int cur[2] = {0, 0};
     int64_t cap[2] = {0, 0};
@@ -168,10 +170,28 @@ struct Cell {
     int event_cap = 0;                      // ionisation events one step can record
     uint32_t* d_ev_perm = nullptr;          // events in parent-uid order (append kernel)
 
+    // direct-implicit electrostatics: susceptibility from the species charges
+    bool implicit = false;
+    double chi_qm[2] = {0, 0};              // q_s / m_s of each species
+    double* d_chiw = nullptr;               // per node: dt^2 / (eps0 V eps_r), 0 outside the plasma rows
+    // persistent preconditioned-CG Poisson solve (used whenever the grid fits it;
+    // the direct-implicit form needs it)
+    bool use_pcg = false;
+    int pcg_blocks = 0;                     // CTAs of the solve's cluster
+    double* d_pcg0 = nullptr;               // chi-free FP64 face coefficients of the interior unknowns
+    float* d_pcg0f = nullptr;               // the same in FP32
+    double* d_pcg = nullptr;                // a solve's FP64 face coefficients (with chi)
+    float* d_pcg32 = nullptr;               // FP32 coefficients and the inner CG vectors
+    double* d_pcg_acc = nullptr;            // per-CTA partial sums
+    float* d_pcg_zrow = nullptr;            // per interior row: z couplings below, above, radial weight
+    float* d_pcg_mu = nullptr;              // radial eigenvalues of the separable preconditioner
+    float* d_pcg_chib = nullptr;            // chi averaged over each node row
+    double* d_phi_prev = nullptr;           // the previous step's potential (initial guess)
+
     // grids
     double* d_phi = nullptr;
     float* d_F = nullptr;                   // 5 float4 per plasma cell
-    float* d_rho = nullptr;                 // node charge of the step (C)
+    float* d_rho = nullptr;                 // node charge of the step (C): electrons, then ions (2 x nnodes)
     float* d_jm = nullptr;                  // node current moment (A m)
     double* d_win = nullptr;                // window surface charge (C)
     double* d_vol = nullptr;                // node weighting volumes (plasma rows)
@@ -203,6 +223,7 @@ struct Cell {
     // Poisson: FP32 separable inner solve + capacitance correction
     SepSolver<float> ps;
     int pcr_levels = 0;                     // cyclic-reduction levels of the z systems
+    std::vector<double> ps_mu;              // radial eigenvalues of the Poisson separable solver
     float* d_pcr_a = nullptr;               // levels x rows x M
     float* d_pcr_g = nullptr;               // levels x rows x M
     float* d_pcr_ib = nullptr;              // rows x M
@@ -309,6 +330,10 @@ void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, con
 void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
                          cudaStream_t st);
 void launch_compose(Cell* c, bool from_new, cudaStream_t st);
+int pcg_supported(Cell* c);
+void pcg_alloc(Cell* c, const std::vector<double>& az, const std::vector<double>& arp,
+               const std::vector<double>& arm, const std::vector<double>& mu);
+int pcg_refine(Cell* c, double cs, double sn, cudaStream_t st, const double* ext, bool in_step);
 void ml_features(Cell* c, cudaStream_t st);          // summaries + feature vector
 void ml_predict(Cell* c, cudaStream_t st);           // network on the feature vector
 int ml_configure(Cell* c, const pp_mlp* m, double alpha_ml, int collect);

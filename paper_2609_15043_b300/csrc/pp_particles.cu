@@ -190,10 +190,11 @@ struct PushArgs {
     const int* nslot;
     SpeciesConst sp[2];
     const float* F;
-    float* rho;
+    float* rho[2];                  // per species (the susceptibility needs them apart)
     float* jm;
     double* win;
     int nr, NR, i_win;
+    int implicit;                   // direct-implicit electrostatics
     uint32_t div_magic, div_shift;  // cell / nr = umulhi(cell, magic) >> shift
     const unsigned long long* step;  // device step counter (RNG counter word)
     uint32_t key0, key1;
@@ -334,13 +335,17 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bcmin = min(bcmin, s_cmin[w]);
             bcmax = max(bcmax, s_cmax[w]);
         }
-        const int tlo = max(bmin - 1, 0);
-        const int thi = min(bmax + 2, a.i_win);
+        // the implicit correction moves a particle by less than a cell: the
+        // tile then spans one more row and column on each side
+        const int pad = a.implicit;
+        const int tlo = max(bmin - 1 - pad, 0);
+        const int thi = min(bmax + 2 + pad, a.i_win);
         const int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
-        const int tclo = max(bcmin - 1, 0);
-        const int tcols = (bmax < 0) ? 0 : min(bcmax + 2, nr) - tclo + 1;
+        const int tclo = max(bcmin - 1 - pad, 0);
+        const int tcols = (bmax < 0) ? 0 : min(bcmax + 2 + pad, nr) - tclo + 1;
+        float* const rho_sp = a.rho[sp];
         const Tile tj{t_jm, tlo, trows, tclo, tcols, a.jm, NR};
-        const Tile tq{t_rho, tlo, trows, tclo, tcols, a.rho, NR};
+        const Tile tq{t_rho, tlo, trows, tclo, tcols, rho_sp, NR};
 
         // ---- phase A: thread-contiguous push
         DepAcc dj{-1, 0, 0.f, 0.f, 0.f, 0.f};
@@ -358,10 +363,10 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             if (p >= nact) continue;
             const uint32_t cell = s_cell[p];
             if (cell == kDead) continue;
-            const int iz = (int)(__umulhi(cell, a.div_magic) >> a.div_shift);
-            const int ir = (int)cell - iz * nr;
-            const float dr = s_dr[p], dz = s_dz[p];
-            const float vr = s_vr[p], vt = s_vt[p], vz = s_vz[p];
+            const int iz0 = (int)(__umulhi(cell, a.div_magic) >> a.div_shift);
+            const int ir0 = (int)cell - iz0 * nr;
+            const float dr0 = s_dr[p], dz0 = s_dz[p];
+            const float vr0 = s_vr[p], vt = s_vt[p], vz0 = s_vz[p];
             if (cell != fcell) {
                 const float4* f = reinterpret_cast<const float4*>(a.F) + (size_t)cell * 5;
                 f0 = __ldg(f);
@@ -373,13 +378,79 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             }
             // gather (bilinear weights at the old position)
             const float one = 1.0f;
-            float wa = one - dr, wb = one - dz;
-            float w00 = wa * wb, w01 = dr * wb, w10 = wa * dz, w11 = dr * dz;
+            float wa = one - dr0, wb = one - dz0;
+            float w00 = wa * wb, w01 = dr0 * wb, w10 = wa * dz0, w11 = dr0 * dz0;
             float Er = w00 * f0.x + w01 * f0.y + w10 * f0.z + w11 * f0.w;
             float Ez = w00 * f1.x + w01 * f1.y + w10 * f1.z + w11 * f1.w;
             float Et = w00 * f2.x + w01 * f2.y + w10 * f2.z + w11 * f2.w;
             float Br = w00 * f3.x + w01 * f3.y + w10 * f3.z + w11 * f3.w;
             float Bz = w00 * f4.x + w01 * f4.y + w10 * f4.z + w11 * f4.w;
+            int ir = ir0, iz = iz0;
+            float dr = dr0, dz = dz0, vr = vr0, vz = vz0;
+            if (a.implicit) {
+                // the previous step's implicit kick with E^s at the predicted
+                // position: v += (q/m) dt E, x += (q/m) dt^2 E (cells), a pass
+                // through the axis reflects, leaving the plasma region absorbs
+                const float vrc = vr + S.qmd * Er, vzc = vz + S.qmd * Ez;
+                float tr = dr + S.kres * Er, tz = dz + S.kzes * Ez;
+                float kr = fminf(fmaxf(floorf(tr), -1048576.0f), 1048576.0f);
+                tr = tr - kr;
+                int irc = ir + (int)kr;
+                if (tr >= one) {
+                    tr = tr - one;
+                    irc += 1;
+                }
+                float kz = fminf(fmaxf(floorf(tz), -1048576.0f), 1048576.0f);
+                tz = tz - kz;
+                int izc = iz + (int)kz;
+                if (tz >= one) {
+                    tz = tz - one;
+                    izc += 1;
+                }
+                float vr_k = vrc;
+                if (irc < 0) {
+                    const float rpos = -((float)irc + tr);
+                    const float jf = floorf(rpos);
+                    irc = (int)jf;
+                    tr = rpos - jf;
+                    vr_k = -vrc;
+                }
+                const bool ce = izc < 0;
+                const bool cw = !ce && irc >= nr;
+                const bool cd = !ce && !cw && izc >= a.i_win;
+                if (ce || cw || cd) {
+                    if (cd) {
+                        float rpos = (float)irc + tr;
+                        int j0 = (int)floorf(rpos);
+                        float fr = rpos - (float)j0;
+                        atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
+                        atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+                    }
+                    ++cnt[0];
+                    ++cnt[1 + sp];
+                    s_cell[p] = kDead;
+                    s_dr[p] = 0.0f;
+                    s_dz[p] = 0.0f;
+                    continue;
+                }
+                // electrostatic work of the kick (mean of the pre- and post-kick velocities)
+                acc_es = __fmaf_rn(S.qw, __fmaf_rn((vr + vrc) * 0.5f, Er, ((vz + vzc) * 0.5f) * Ez), acc_es);
+                ir = irc;
+                iz = izc;
+                dr = tr;
+                dz = tz;
+                vr = vr_k;
+                vz = vzc;
+                // the current moment is deposited at the corrected position
+                wa = one - dr;
+                wb = one - dz;
+                w00 = wa * wb;
+                w01 = dr * wb;
+                w10 = wa * dz;
+                w11 = dr * dz;
+                Er = 0.0f;      // the Boris step carries E_theta and B only
+                Ez = 0.0f;
+            }
             // Boris in the local frame (x = r, y = theta, z); B_theta = 0
             float hx = S.qmh * Er, hy = S.qmh * Et, hz = S.qmh * Ez;
             float vmx = vr + hx, vmy = vt + hy, vmz = vz + hz;
@@ -399,8 +470,8 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             float vbr = (vr + vnx) * 0.5f;
             float vbz = (vz + vnz) * 0.5f;
             float jmv = S.qw * vbt;
-            acc_ind += jmv * Et;
-            acc_es += S.qw * (vbr * Er + vbz * Ez);
+            acc_ind = __fmaf_rn(jmv, Et, acc_ind);
+            if (!a.implicit) acc_es = __fmaf_rn(S.qw, __fmaf_rn(vbr, Er, vbz * Ez), acc_es);
             ++cnt[0];
             dep_run(dj, tj, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
             // move (cell units): r' = |(r + a, b)| written as r + delta
@@ -517,7 +588,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                 t_rho[q] = 0.f;
                 t_jm[q] = 0.f;
                 const int gidx = (tlo + warp) * NR + tclo + cq;
-                if (vq != 0.f) atomicAdd(&a.rho[gidx], vq);
+                if (vq != 0.f) atomicAdd(&rho_sp[gidx], vq);
                 if (vj != 0.f) atomicAdd(&a.jm[gidx], vj);
             }
         // every thread read this chunk's index before the barrier after the
@@ -588,7 +659,9 @@ void launch_push(Cell* c, cudaStream_t st) {
     }
     a.nslot = c->d_nslot;
     a.F = c->d_F;
-    a.rho = c->d_rho;
+    a.rho[0] = c->d_rho;
+    a.rho[1] = c->d_rho + c->nnodes;
+    a.implicit = c->implicit ? 1 : 0;
     a.jm = c->d_jm;
     a.win = c->d_win;
     a.nr = c->nr;
@@ -630,10 +703,12 @@ void launch_deposit_only(Cell* c, cudaStream_t st) {
         int64_t n = c->cap[s];
         unsigned nb = (unsigned)((n + 255) / 256);
         if (c->fp64)
-            deposit_only<double><<<nb, 256, 0, st>>>(c->pd[s][c->cur[s]], c->d_nslot, s, c->scd[s].qw, c->d_rho64,
+            deposit_only<double><<<nb, 256, 0, st>>>(c->pd[s][c->cur[s]], c->d_nslot, s, c->scd[s].qw,
+                                                     c->d_rho64 + (size_t)s * c->nnodes,
                                                      c->nr, c->NR);
         else
-            deposit_only<float><<<nb, 256, 0, st>>>(c->pb[s][c->cur[s]], c->d_nslot, s, c->sc[s].qw, c->d_rho,
+            deposit_only<float><<<nb, 256, 0, st>>>(c->pb[s][c->cur[s]], c->d_nslot, s, c->sc[s].qw,
+                                                    c->d_rho + (size_t)s * c->nnodes,
                                                     c->nr, c->NR);
         count_launch();
     }

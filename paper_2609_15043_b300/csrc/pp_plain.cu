@@ -16,10 +16,11 @@ struct PlainArgs {
     const int* nslot;
     SpecT<T> sp[2];
     const T* F;            // per plasma cell: (Er, Ez, Etheta, Br, Bz) x corners 00, 01, 10, 11
-    T* rho;                // node charge of the step (C)
+    T* rho[2];             // node charge of the step per species (C)
     T* jm;                 // node current moment (A m)
     double* win;           // window surface charge (C)
     int nr, NR, i_win;
+    int implicit;          // direct-implicit electrostatics
     const unsigned long long* step;
     uint32_t key0, key1;
     EventT<T>* ev;
@@ -55,10 +56,11 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         const SpecT<T> S = sp ? a.sp[1] : a.sp[0];
         const uint32_t cell = P.cell[q];
         if (cell == kDead) continue;
-        const int iz = (int)(cell / (uint32_t)nr);
-        const int ir = (int)cell - iz * nr;
-        const T dr = P.dr[q], dz = P.dz[q];
-        const T vr = P.vr[q], vt = P.vt[q], vz = P.vz[q];
+        int iz = (int)(cell / (uint32_t)nr);
+        int ir = (int)cell - iz * nr;
+        T dr = P.dr[q], dz = P.dz[q];
+        T vr = P.vr[q], vz = P.vz[q];
+        const T vt = P.vt[q];
         const T* f = a.F + (size_t)cell * 20;
         // gather (bilinear weights at the old position)
         T wa = one - dr, wb = one - dz;
@@ -68,6 +70,67 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         T Et = w00 * f[8] + w01 * f[9] + w10 * f[10] + w11 * f[11];
         T Br = w00 * f[12] + w01 * f[13] + w10 * f[14] + w11 * f[15];
         T Bz = w00 * f[16] + w01 * f[17] + w10 * f[18] + w11 * f[19];
+        ++cnt[6];
+        if (a.implicit) {
+            // the previous step's implicit kick at the predicted position
+            // (the fused kernel's arithmetic in T)
+            const T vrc = vr + S.qmd * Er, vzc = vz + S.qmd * Ez;
+            T tr = dr + S.kres * Er, tz = dz + S.kzes * Ez;
+            T kr = fmin_t(fmax_t(floor_t(tr), T(-1048576.0)), T(1048576.0));
+            tr = tr - kr;
+            int irc = ir + (int)kr;
+            if (tr >= one) {
+                tr = tr - one;
+                irc += 1;
+            }
+            T kz = fmin_t(fmax_t(floor_t(tz), T(-1048576.0)), T(1048576.0));
+            tz = tz - kz;
+            int izc = iz + (int)kz;
+            if (tz >= one) {
+                tz = tz - one;
+                izc += 1;
+            }
+            T vr_k = vrc;
+            if (irc < 0) {
+                const T rpos = -((T)irc + tr);
+                const T jf = floor_t(rpos);
+                irc = (int)jf;
+                tr = rpos - jf;
+                vr_k = -vrc;
+            }
+            const bool ce = izc < 0;
+            const bool cw = !ce && irc >= nr;
+            const bool cd = !ce && !cw && izc >= a.i_win;
+            if (ce || cw || cd) {
+                if (cd) {
+                    T rpos = (T)irc + tr;
+                    int j0 = (int)floor_t(rpos);
+                    T fr = rpos - (T)j0;
+                    atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
+                    atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+                }
+                ++cnt[7 + sp];
+                P.cell[q] = kDead;
+                P.dr[q] = T(0.0);
+                P.dz[q] = T(0.0);
+                continue;
+            }
+            acc_es += (double)(S.qw * (((vr + vrc) * T(0.5)) * Er + ((vz + vzc) * T(0.5)) * Ez));
+            ir = irc;
+            iz = izc;
+            dr = tr;
+            dz = tz;
+            vr = vr_k;
+            vz = vzc;
+            wa = one - dr;
+            wb = one - dz;
+            w00 = wa * wb;
+            w01 = dr * wb;
+            w10 = wa * dz;
+            w11 = dr * dz;
+            Er = T(0.0);
+            Ez = T(0.0);
+        }
         // Boris in the local frame (x = r, y = theta, z); B_theta = 0
         T hx = S.qmh * Er, hy = S.qmh * Et, hz = S.qmh * Ez;
         T vmx = vr + hx, vmy = vt + hy, vmz = vz + hz;
@@ -88,8 +151,7 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         T vbz = (vz + vnz) * T(0.5);
         T jmv = S.qw * vbt;
         acc_ind += (double)(jmv * Et);
-        acc_es += (double)(S.qw * (vbr * Er + vbz * Ez));
-        ++cnt[6];
+        if (!a.implicit) acc_es += (double)(S.qw * (vbr * Er + vbz * Ez));
         add4(a.jm, NR, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
         // move (cell units): r' = |(r + a, b)| written as r + delta
         T am = vnx * S.dtr, bm = vny * S.dtr, cm = vnz * S.dtz;
@@ -141,7 +203,7 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         if (alive) {
             ncell = (uint32_t)(iz2 * nr + ir2);
             T wa2 = one - drn, wb2 = one - dzn;
-            add4(a.rho, NR, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
+            add4(a.rho[sp], NR, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
                  S.qw * (drn * dzn));
             uint32_t r = philox2x32_10(P.uid[q], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31), a.key0 ^ a.key1);
             if (T(u01(r)) < S.pnull) {
@@ -208,7 +270,9 @@ void launch_push_plain(Cell* c, cudaStream_t st) {
     }
     a.nslot = c->d_nslot;
     a.F = c->d_F64;
-    a.rho = c->d_rho64;
+    a.rho[0] = c->d_rho64;
+    a.rho[1] = c->d_rho64 + c->nnodes;
+    a.implicit = c->implicit ? 1 : 0;
     a.jm = c->d_jm64;
     a.win = c->d_win;
     a.nr = c->nr;

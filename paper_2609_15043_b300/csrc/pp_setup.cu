@@ -175,6 +175,10 @@ static void species_constants(Cell* c) {
         d.inv_ce = kQe / (0.5 * m);
         d.loss = 2.0 * kMe / kMAr;
         d.vth_gas = std::sqrt(kKb * f.t_gas / kMAr);
+        d.qmd = q / m * f.dt;
+        d.kres = q / m * f.dt * f.dt / c->dr;
+        d.kzes = q / m * f.dt * f.dt / c->dz;
+        c->chi_qm[sp] = q / m;
         SpeciesConst& s = c->sc[sp];
         s.qmh = (float)d.qmh;
         s.dtr = (float)d.dtr;
@@ -187,6 +191,9 @@ static void species_constants(Cell* c) {
         s.inv_ce = (float)d.inv_ce;
         s.loss = (float)d.loss;
         s.vth_gas = (float)d.vth_gas;
+        s.qmd = (float)d.qmd;
+        s.kres = (float)d.kres;
+        s.kzes = (float)d.kzes;
     }
 }
 
@@ -210,7 +217,9 @@ int setup_cell(Cell* c) {
     if (f.nz - 1 > (1 << kMaxPcrLevels)) return fail("nz exceeds the supported axial node count");
     if (f.n_turns < 1 || f.n_turns > PP_MAX_TURNS) return fail("n_turns out of range");
     if (f.freq <= 0 || f.dt <= 0) return fail("freq and dt must be positive");
-    if ((f.plain_fp64 != 0 && f.plain_fp64 != 1) || f.reserved0 != 0) return fail("plain_fp64 must be 0 or 1");
+    if (f.plain_fp64 != 0 && f.plain_fp64 != 1) return fail("plain_fp64 must be 0 or 1");
+    if (f.implicit_es != 0 && f.implicit_es != 1) return fail("implicit_es must be 0 or 1");
+    c->implicit = f.implicit_es == 1;
     c->nr = f.nr;
     c->nz = f.nz;
     c->NR = f.nr + 1;
@@ -409,7 +418,7 @@ int setup_cell(Cell* c) {
     if (c->fp64) {
         c->d_events64 = c->alloc<EventT<double>>(c->event_cap);
         c->d_F64 = c->alloc<double>((size_t)c->i_win * f.nr * 20);
-        c->d_rho64 = c->alloc<double>(c->nnodes);
+        c->d_rho64 = c->alloc<double>((size_t)2 * c->nnodes);
         c->d_jm64 = c->alloc<double>(c->nnodes);
     }
     c->d_nslot = c->alloc<int>(2);
@@ -418,10 +427,23 @@ int setup_cell(Cell* c) {
     c->d_events = c->alloc<Event>(c->event_cap);
     c->d_phi = c->alloc<double>(c->nnodes);
     c->d_F = c->alloc<float>((size_t)c->i_win * c->nr * 20);
-    c->d_rho = c->alloc<float>(c->nnodes);
+    c->d_rho = c->alloc<float>((size_t)2 * c->nnodes);
     c->d_jm = c->alloc<float>(c->nnodes);
     c->d_win = c->alloc<double>(c->nnodes);
     c->d_vol = upload<double>(c, vol);
+    {
+        // susceptibility weight per node: chi = (q_e/m_e rho_e + q_i/m_i rho_i) * chiw with
+        // chiw = dt^2 / (eps0 V eps_r), eps_r the mean of the node's adjacent cells (Sec. 2.3)
+        std::vector<double> chiw(c->nnodes, 0.0);
+        for (int i = 0; i <= c->i_win; ++i) {
+            const double eps_n = i == 0 ? c->eps_row[0] : 0.5 * (c->eps_row[i - 1] + c->eps_row[i]);
+            for (int j = 0; j < NR; ++j) {
+                const double v = vol[i * NR + j];
+                chiw[i * NR + j] = v > 0 ? f.dt * f.dt / (kEps0 * v * eps_n) : 0.0;
+            }
+        }
+        c->d_chiw = upload<double>(c, chiw);
+    }
     c->d_Ec = c->alloc<double>(c->nnodes);
     c->d_Ess = c->alloc<double>(c->nnodes);
     c->d_Ecp = c->alloc<double>(c->nnodes);
@@ -482,6 +504,7 @@ int setup_cell(Cell* c) {
         }
         std::vector<double> mu, V;
         radial_basis(T, D, M, mu, V);
+        c->ps_mu = mu;
         std::vector<double> Vt((size_t)M * M);
         for (int j = 0; j < M; ++j)
             for (int m = 0; m < M; ++m) Vt[(size_t)m * M + j] = V[(size_t)j * M + m];
@@ -716,6 +739,19 @@ int setup_cell(Cell* c) {
         c->ntn_pad = Kp;
         c->d_Zt = upload<float>(c, Zt);
     }
+    // ---- the persistent CG solve (needed by the direct-implicit form, whose
+    // operator is not separable; used for the explicit form too when it fits)
+    const bool cg_ok = pcg_supported(c) != 0;
+    c->use_pcg = c->implicit && cg_ok;
+    if (c->implicit) {
+        if (!cg_ok) return fail("implicit_es: the grid exceeds the CG Poisson solve (M <= 512, a multiple of 4, rows <= 1024)");
+        // Eq. facecharge uses the chi-free face coefficients: every face of a
+        // turn node must see chi = 0, i.e. both nodes above the plasma rows
+        for (int k = 0; k < N; ++k)
+            for (int n : c->turn_nodes[k])
+                if (n / NR <= c->i_win + 1) return fail("implicit_es: a turn node touches the plasma rows");
+    }
+    if (c->use_pcg) pcg_alloc(c, az, arp, arm, c->ps_mu);
     cudaError_t err = cudaDeviceSynchronize();
     if (err != cudaSuccess) {
         set_error(std::string("CUDA error during init: ") + cudaGetErrorString(err));

@@ -3,7 +3,7 @@ on the device through pp_ml_configure / pp_mlp_forward).
 
   python -m paper_2609_15043_b300.mlp_train collect --out pairs.npz [--cells 16 --periods 150 --n-init 250000
                                                    --density 1e16 --p-min 20 --p-max 150]
-  python -m paper_2609_15043_b300.mlp_train train --pairs pairs.npz --out weights.npz [--epochs 300 --device gpu]
+  python -m paper_2609_15043_b300.mlp_train train --pairs pairs.npz --out weights.npz [--epochs 300]
 
 collect: runs a batch of cells shaped like the 128x192 workload (seeds and
 controller targets varied, fewer macroparticles per cell) with feature
@@ -11,8 +11,8 @@ collection on, and stores the pairs (features after period n, measured loads
 of period n+1).  train: fits the 3x256 ReLU network to the standardised loads
 with Adam on mean squared error on the device (pp_trainer_*: FP32 master
 weights, BF16 tensor-core products), keeps the weights of the best
-validation epoch and stores their BF16 patterns; `--device cpu` runs the same
-fit in numpy (FP32 throughout) instead.
+validation epoch and stores their BF16 patterns.  There is no host form of
+the fit: training runs on the project's tensor-core kernels only.
 """
 import argparse
 import math
@@ -134,94 +134,20 @@ def _init(rng, n_in, n_out):
     return W, b
 
 
-def _forward(W, b, x):
-    hs = [x]
-    h = x
-    for l in range(3):
-        h = np.maximum(h @ W[l].T + b[l], 0.0)
-        hs.append(h)
-    return h @ W[3].T + b[3], hs
-
-
 def train(args):
-    if getattr(args, "device", "gpu") == "gpu":
-        d = np.load(args.pairs)
-        params, info = fit_device(d["X"], d["Y"], epochs=args.epochs, batch=args.batch, lr=args.lr,
-                                  weight_decay=args.weight_decay, seed=args.seed)
-        print("best epoch %d  validation mse %.4g  (%d device steps)" % (info["best_epoch"], info["best_mse"],
-                                                                        info["steps"]), file=sys.stderr, flush=True)
-        save_params(args.out, params)
-        print("saved", args.out)
-        return
-    _train_numpy(args)
+    d = np.load(args.pairs)
+    params, info = fit_device(d["X"], d["Y"], epochs=args.epochs, batch=args.batch, lr=args.lr,
+                              weight_decay=args.weight_decay, seed=args.seed)
+    print("best epoch %d  validation mse %.4g  (%d device steps)" % (info["best_epoch"], info["best_mse"],
+                                                                    info["steps"]), file=sys.stderr, flush=True)
+    save_params(args.out, params)
+    print("saved", args.out)
 
 
 def save_params(path, p):
     np.savez(path, w0=p["w"][0], w1=p["w"][1], w2=p["w"][2], w3=p["w"][3], b0=p["b"][0], b1=p["b"][1],
              b2=p["b"][2], b3=p["b"][3], mu_in=p["mu_in"], sig_in=p["sig_in"], mu_out=p["mu_out"],
              sig_out=p["sig_out"])
-
-
-def _train_numpy(args):
-    d = np.load(args.pairs)
-    X, Y = d["X"].astype(np.float64), d["Y"].astype(np.float64)
-    n_in, n_out = X.shape[1], Y.shape[1]
-    mu_in, sig_in, mu_out, sig_out, xs, ys = standardise(X, Y)
-    Xn = np.zeros((len(X), WIDTH), np.float32)
-    Xn[:, :n_in] = xs
-    Yn = np.zeros((len(Y), OUT_PAD), np.float32)
-    Yn[:, :n_out] = ys
-    rng = np.random.default_rng(args.seed)
-    perm = rng.permutation(len(X))
-    n_val = max(len(X) // 10, 1)
-    val, tr = perm[:n_val], perm[n_val:]
-    W, b = _init(rng, n_in, n_out)
-    mW = [np.zeros_like(w) for w in W]
-    vW = [np.zeros_like(w) for w in W]
-    mb = [np.zeros_like(x) for x in b]
-    vb = [np.zeros_like(x) for x in b]
-    lr, b1, b2, eps = args.lr, 0.9, 0.999, 1e-8
-    mask = np.zeros(OUT_PAD, np.float32)
-    mask[:n_out] = 1.0
-    step = 0
-    best = (float("inf"), None)
-    for epoch in range(args.epochs):
-        order = rng.permutation(tr)
-        for s0 in range(0, len(order), args.batch):
-            idx = order[s0:s0 + args.batch]
-            x, y = Xn[idx], Yn[idx]
-            out, hs = _forward(W, b, x)
-            g = (out - y) * mask * np.float32(2.0 / (len(idx) * n_out))
-            gW = [None] * 4
-            gb = [None] * 4
-            for l in (3, 2, 1, 0):
-                gW[l] = g.T @ hs[l]
-                gb[l] = g.sum(0)
-                if l > 0:
-                    g = (g @ W[l]) * (hs[l] > 0)
-            step += 1
-            for l in range(4):
-                for p, gp, m, v in ((W, gW, mW, vW), (b, gb, mb, vb)):
-                    m[l] = b1 * m[l] + (1 - b1) * gp[l]
-                    v[l] = b2 * v[l] + (1 - b2) * gp[l] * gp[l]
-                    mh = m[l] / (1 - b1 ** step)
-                    vh = v[l] / (1 - b2 ** step)
-                    p[l] -= (lr * mh / (np.sqrt(vh) + eps)).astype(np.float32)
-                W[l] -= np.float32(lr * args.weight_decay) * W[l]
-        # keep the weights of the best validation epoch (the loads are noisy:
-        # past that point the fit learns the noise)
-        ov, _ = _forward(W, b, Xn[val])
-        mse = float(np.mean(((ov - Yn[val]) * mask)[:, :n_out] ** 2))
-        if mse < best[0]:
-            best = (mse, ([w.copy() for w in W], [x.copy() for x in b], epoch))
-        if epoch % 50 == 0 or epoch == args.epochs - 1:
-            print("epoch %d  validation mse (standardised) %.4g" % (epoch, mse), file=sys.stderr, flush=True)
-    W, b, best_epoch = best[1]
-    print("best epoch %d  validation mse %.4g" % (best_epoch, best[0]), file=sys.stderr, flush=True)
-    wbits = [_bf16_bits(w) for w in W]
-    np.savez(args.out, w0=wbits[0], w1=wbits[1], w2=wbits[2], w3=wbits[3], b0=b[0], b1=b[1], b2=b[2], b3=b[3],
-             mu_in=mu_in, sig_in=sig_in, mu_out=mu_out, sig_out=sig_out)
-    print("saved", args.out)
 
 
 def load_params(path):
@@ -252,8 +178,6 @@ def main():
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=7)
     t.add_argument("--weight-decay", type=float, default=1e-2)
-    t.add_argument("--device", choices=("gpu", "cpu"), default="gpu",
-                   help="gpu: pp_trainer_* on the tensor cores; cpu: the same fit in numpy")
     a = ap.parse_args()
     collect(a) if a.cmd == "collect" else train(a)
 

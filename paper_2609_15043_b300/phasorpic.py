@@ -25,7 +25,8 @@ ERRORS = {-1: "PP_E_CONFIG", -2: "PP_E_NOCONV", -3: "PP_E_SAMPLES", -4: "PP_E_NA
           -6: "PP_E_CUDA", -7: "PP_E_ARG", -8: "PP_E_CAPACITY"}
 ST_NOCONV, ST_EVENTS, ST_CAPACITY, ST_SAMPLES, ST_TIMEOUT = 1, 2, 4, 8, 16
 
-GRID_PHI, GRID_EC, GRID_ESS, GRID_JC, GRID_JS, GRID_WINDOW, GRID_CHARGE, GRID_JMOM = range(8)
+GRID_PHI, GRID_EC, GRID_ESS, GRID_JC, GRID_JS, GRID_WINDOW, GRID_CHARGE, GRID_JMOM, GRID_CHARGE_E, GRID_CHARGE_I = \
+    range(10)
 GRID_U0 = 16
 
 EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp_last_error",
@@ -71,7 +72,7 @@ class PPConfig(C.Structure):
         ("poisson_max_iter", C.c_int32),
         ("poisson_tol", C.c_double),
         ("plain_fp64", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("implicit_es", C.c_int32),
     ]
 
 
@@ -223,6 +224,7 @@ def make_config(cfg, capacity=None, weight=None, poisson_max_iter=2, poisson_tol
     c.poisson_max_iter = poisson_max_iter
     c.poisson_tol = poisson_tol
     c.plain_fp64 = int(getattr(cfg, "plain_fp64", 0))
+    c.implicit_es = int(getattr(cfg, "implicit_es", 0))
     return c
 
 
@@ -480,7 +482,15 @@ def _poisson_stats(self, stream=0):
     return rel[:n.value]
 
 
+def _poisson_evaluations(self, stream=0):
+    """FP64 residual evaluations of the most recent Poisson solve (CG: iterations + 1)."""
+    n = C.c_int()
+    _check(lib.pp_get_poisson_stats(self.h, C.byref(n), None, C.c_void_p(stream)), "pp_get_poisson_stats")
+    return n.value
+
+
 Cell.poisson_stats = _poisson_stats
+Cell.poisson_evaluations = _poisson_evaluations
 
 
 def _set_profiling(self, on=True, level=2):

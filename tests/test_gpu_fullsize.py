@@ -6,7 +6,7 @@ seeded inputs."""
 import numpy as np
 import pytest
 
-from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live
+from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live, check_step_potential
 
 pytestmark = pytest.mark.gpu
 
@@ -36,13 +36,16 @@ def test_vacuum_impedance_at_bench_size(cell60_inputs):
     g.close()
 
 
-def test_one_step_parity_at_bench_size(cell60_inputs):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_one_step_parity_at_bench_size(cell60_inputs, implicit):
     """One PIC step of all 8e6 macroparticles from the oracle's potential:
     cells, uids, absorptions and collision counts bit-exact, float32 state
-    within 2e-5, deposited charge and current within 1e-6 of the total."""
+    within 2e-5, deposited charge and current within 1e-6 of the total; in the
+    direct-implicit form also the potential of the step's chi solve."""
     require_gpu()
     from paper_2609_15043_b300 import phasorpic as pp
     cfg, pops = cell60_inputs
+    cfg = cfg.replace(implicit_es=implicit)
     oc = oracle_cell(cfg, pops)
     oc.prime(np.float32)
     g = gpu_cell(cfg, pops)
@@ -69,4 +72,5 @@ def test_one_step_parity_at_bench_size(cell60_inputs):
     assert np.max(np.abs(q - info["Q"])) <= 1e-6 * np.sum(np.abs(info["Q"]))
     j = g.grid(pp.GRID_JMOM)
     assert np.max(np.abs(j - info["J"])) <= 1e-6 * np.sum(np.abs(info["J"]))
+    check_step_potential(oc, g)
     g.close()

@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live
+from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live, check_step_potential
 
 pytestmark = pytest.mark.gpu
 
@@ -113,14 +113,21 @@ def _step_compare(cfg, pops, steps=1):
     return oc, g, info, tot
 
 
-def test_one_step_parity(small_inputs):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_one_step_parity(small_inputs, implicit):
     """One full PIC step from identical state and field: cells, absorptions,
     collision counts and ionisation products bit-exact, float32 state within
-    2e-5, deposited charge within 1e-6 of the total."""
+    2e-5, deposited charge within 1e-6 of the total.  In the direct-implicit
+    form (Sec. 2.3) the step also solves Eq. poisson with the susceptibility of
+    the predicted populations: the new potential against the oracle's direct
+    solve of the same operator."""
     require_gpu()
     cfg, pops = small_inputs
+    cfg = cfg.replace(implicit_es=implicit)
     from paper_2609_15043_b300 import phasorpic as pp
     oc, g, info, tot = _step_compare(cfg, pops)
+    check_step_potential(oc, g)
+    assert g.poisson_stats()[g.poisson_stats() > 0][-1] <= 1e-10
     cnt = g.counters()
     assert cnt["particle_steps"] == tot['pushed']
     assert cnt["absorbed"] == tot['absorbed']
@@ -147,12 +154,14 @@ def test_one_step_parity(small_inputs):
     g.close()
 
 
-def test_ten_steps_from_shared_fields(small_inputs):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_ten_steps_from_shared_fields(small_inputs, implicit):
     """Ten consecutive steps, each started from the oracle's potential: the
     particle populations (including ionisation products and their uids) stay
     bit-identical in their integer state."""
     require_gpu()
     cfg, pops = small_inputs
+    cfg = cfg.replace(implicit_es=implicit)
     oc, g, info, tot = _step_compare(cfg, pops, steps=10)
     cnt = g.counters()
     assert cnt["absorbed"] == tot['absorbed']

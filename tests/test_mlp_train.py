@@ -1,12 +1,17 @@
-"""The numpy form of the proposal network's trainer (`--device cpu`): it fits a
-learnable synthetic map, and its exported BF16 model evaluated by the
-oracle's forward pass reproduces the map."""
+"""The proposal network's trainer (`mlp_train train`, device kernels): it
+fits a learnable synthetic map, and its exported BF16 model evaluated by the
+oracle's forward pass reproduces the map; load standardisation on the host."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
 
+@pytest.mark.gpu
 def test_trainer_fits_a_smooth_map(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
     from paper_2609_15043_b300 import mlp_train
     rng = np.random.default_rng(0)
     n_in, n_out, n = 206, 12, 3000
@@ -23,7 +28,6 @@ def test_trainer_fits_a_smooth_map(tmp_path):
         lr = 2e-3
         seed = 1
         weight_decay = 0.0
-        device = "cpu"
     mlp_train.train(A_)
     p = mlp_train.load_params(A_.out)
     assert [w.shape for w in p["w"]] == [(256, 256)] * 3 + [(32, 256)]
