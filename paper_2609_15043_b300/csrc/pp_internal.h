@@ -77,6 +77,16 @@ enum {
 };
 
 // device-resident scalars of one cell
+// Shared-memory plan of the cluster CG Poisson solve: cluster size, what lives
+// in shared memory (the radial eigenbasis, the band vectors), the band and
+// mode counts, the z rows per lane, and the byte offsets of the regions.
+struct PcgPlan {
+    int C = 0, v_sm = 0, vec_sm = 0, nbmax = 0, Mp = 0, nm_max = 0, Lc = 0;
+    long long off_V = -1, off_vec = -1, off_in = 0, off_d = 0, off_free = 0, off_fac = 0, off_chi = 0;
+    size_t smem = 0;
+    long long gvec_stride = 0;              // floats of one CTA's private global region (vectors not in shared memory)
+};
+
 struct DevState {
     double x[2 * (2 * PP_MAX_TURNS + 1)];    // applied circuit state
     double vg_amp;
@@ -174,10 +184,10 @@ struct Cell {
     bool implicit = false;
     double chi_qm[2] = {0, 0};              // q_s / m_s of each species
     double* d_chiw = nullptr;               // per node: dt^2 / (eps0 V eps_r), 0 outside the plasma rows
-    // persistent preconditioned-CG Poisson solve (used whenever the grid fits it;
-    // the direct-implicit form needs it)
+    // persistent preconditioned-CG Poisson solve (the direct-implicit form's)
     bool use_pcg = false;
     int pcg_blocks = 0;                     // CTAs of the solve's cluster
+    PcgPlan pcg_plan;                       // its shared-memory plan, chosen at set-up
     double* d_pcg0 = nullptr;               // chi-free FP64 face coefficients of the interior unknowns
     float* d_pcg0f = nullptr;               // the same in FP32
     double* d_pcg = nullptr;                // a solve's FP64 face coefficients (with chi)

@@ -744,7 +744,7 @@ int setup_cell(Cell* c) {
     const bool cg_ok = pcg_supported(c) != 0;
     c->use_pcg = c->implicit && cg_ok;
     if (c->implicit) {
-        if (!cg_ok) return fail("implicit_es: the grid exceeds the CG Poisson solve (M <= 512, a multiple of 4, rows <= 1024)");
+        if (!cg_ok) return fail("implicit_es: the grid exceeds the CG Poisson solve (radial nodes a multiple of 4 and at most 16 per CTA of the cluster, at most 384 interior node rows, shared memory)");
         // Eq. facecharge uses the chi-free face coefficients: every face of a
         // turn node must see chi = 0, i.e. both nodes above the plasma rows
         for (int k = 0; k < N; ++k)
