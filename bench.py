@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=1, help="PIC steps of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--es", default="implicit", choices=["implicit", "explicit"],
+                    help="electrostatics: the paper's direct-implicit form (default) or the explicit push")
+    ap.add_argument("--tts-workload", default="coarse60",
+                    help="workload of the time-to-stationary part of the default run")
+    ap.add_argument("--tts-periods", type=int, default=400, help="cap of that part (periods per form)")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-stationary part")
     ap.add_argument("--form", default="fused", choices=["fused", "fp64"],
                     help="particle form: the fused FP32 kernel or the plain FP64 form")
     ap.add_argument("--time-to-stationary", action="store_true",
@@ -96,10 +102,11 @@ def reduce_over_ranks(ms, psteps, dist):
 
 def workload_desc(cfg, name):
     return ("%s: %dx%d cells over r<=%.2f m, z<=%.2f m, %d macroparticles/species, %d turns, Ar %.0f mTorr, "
-            "dt=T/%d, n0=%.0e m^-3%s" % (name, cfg.nr, cfg.nz, cfg.r_max, cfg.z_max, cfg.n_init, len(cfg.turn_r),
-                                          cfg.pressure_pa / 133.322368 * 1e3, round(1 / (cfg.freq * cfg.dt)),
-                                          cfg.density,
-                                          (", controller target %.0f W" % cfg.p_target) if cfg.power_control else ""))
+            "dt=T/%d, n0=%.0e m^-3%s, %s electrostatics" % (
+                name, cfg.nr, cfg.nz, cfg.r_max, cfg.z_max, cfg.n_init, len(cfg.turn_r),
+                cfg.pressure_pa / 133.322368 * 1e3, round(1 / (cfg.freq * cfg.dt)), cfg.density,
+                (", controller target %.0f W" % cfg.p_target) if cfg.power_control else "",
+                "direct-implicit" if cfg.implicit_es else "explicit"))
 
 
 # ---------------------------------------------------------------- clocks
@@ -208,39 +215,91 @@ def time_oracle(oc, steps):
     return time.perf_counter() - t0, pushed
 
 
+def _farm_worker(conn, cfg, w, P):
+    """One host core of the CPU baseline: the oracle as it stands on an
+    independent cell with 1/P of the workload's macroparticles (its own
+    seed), primed untimed, then timed PIC steps on request."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    oc = make_oracle(cfg.replace(n_init=max(1, cfg.n_init // P), seed=cfg.seed + 1000 + w))
+    conn.send("ready")
+    while True:
+        steps = conn.recv()
+        if steps is None:
+            break
+        conn.send(time_oracle(oc, steps))
+    conn.close()
+
+
+class OracleFarm:
+    """The FP64 oracle on every host core at once: P independent cells of N/P
+    macroparticles per species, one per spawned process (no process inherits
+    a CUDA context).  step() returns the longest process's time and the
+    particle-steps of all processes."""
+
+    def __init__(self, cfg, cores):
+        import multiprocessing as mpr
+        ctx = mpr.get_context("spawn")
+        self.conns, self.procs = [], []
+        for w in range(cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_farm_worker, args=(b, cfg, w, cores), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            c.recv()
+
+    def step(self, steps):
+        for c in self.conns:
+            c.send(steps)
+        res = [c.recv() for c in self.conns]
+        return max(r[0] for r in res), sum(r[1] for r in res)
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
 def cpu_baseline(cfg, args):
-    oc = make_oracle(cfg)
-    dt, pushed = time_oracle(oc, args.cpu_steps)
-    return {"value": pushed / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d PIC step(s) of the full workload (%d particle-steps, %.1f s), FP64 numpy/scipy "
-                      "oracle, single thread; host has %d cores" % (args.cpu_steps, pushed, dt, os.cpu_count())}
+    cores = os.cpu_count() or 1
+    farm = OracleFarm(cfg, cores)
+    dt, pushed = farm.step(args.cpu_steps)
+    farm.close()
+    return {"value": pushed / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d PIC step(s) on each of %d host cores, each core an independent cell of the workload "
+                      "with 1/%d of its macroparticles (%d particle-steps in all, %.1f s), FP64 numpy/scipy "
+                      "oracle" % (args.cpu_steps, cores, cores, pushed, dt)}
 
 
 def run_reference(args, cfg, ws, rank):
     """The reference arm is the oracle itself on the host cores: each bench
-    step is `--cpu-steps` oracle PIC steps of the same workload (a bounded
-    sample; a whole RF period would take hours)."""
+    step is `--cpu-steps` oracle PIC steps on every core, each core an
+    independent cell of the workload with 1/P of its macroparticles (a
+    bounded sample; a whole RF period would take hours)."""
     if rank != 0:
         return
-    oc = make_oracle(cfg)
+    cores = os.cpu_count() or 1
+    farm = OracleFarm(cfg, cores)
     for _ in range(min(args.warmup, 1)):
-        time_oracle(oc, 1)
+        farm.step(1)
     total_t, total_p = 0.0, 0
     for _ in range(args.steps):
-        dt, pushed = time_oracle(oc, args.cpu_steps)
+        dt, pushed = farm.step(args.cpu_steps)
         total_t += dt
         total_p += pushed
+    farm.close()
     value = total_p / total_t
-    sample = ("%d x %d PIC step(s) of the full workload after %d warm-up step(s), FP64 numpy/scipy oracle, "
-              "single thread; host has %d cores" % (args.steps, args.cpu_steps, min(args.warmup, 1),
-                                                    os.cpu_count()))
+    sample = ("%d x %d PIC step(s) on each of %d host cores, each core an independent cell of the workload with "
+              "1/%d of its macroparticles, FP64 numpy/scipy oracle" % (args.steps, args.cpu_steps, cores, cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(cfg, args.workload),
                        "step": "%d oracle PIC step(s) per bench step" % args.cpu_steps},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -390,8 +449,7 @@ def run_ours(args, cfg, ws, rank, local):
                    "settle_periods": settle,
                    "n_live": {"start": [c0["live_e"], c0["live_i"]], "end": [c1["live_e"], c1["live_i"]]},
                    "status": status,
-                   "time_to_stationary": None,
-                   "time_to_stationary_mode": "bench.py --time-to-stationary (minutes; not part of this run)"},
+                   "time_to_stationary": None},
         "roofline": {"bound": "hbm", "kernel": "push_kernel" if args.form == "fused" else "push_plain",
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -405,13 +463,30 @@ def run_ours(args, cfg, ws, rank, local):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args)
-    print(json.dumps(line), flush=True)
     cell.close()
+    del cell
+    torch.cuda.empty_cache()
+    if ws == 1 and not args.no_tts:
+        # the second half of the metric: periods and wall time to a stationary
+        # state for the fused FP32 and the plain FP64 form, from the same
+        # seeded state, and their agreement
+        from paper_2609_15043_b300 import workloads as wl
+        tcfg = wl.WORKLOADS[args.tts_workload]().replace(implicit_es=cfg.implicit_es)
+        out, traces = stationary_runs(tcfg, ["fused", "fp64"], args.tts_periods)
+        line["config"]["time_to_stationary"] = tts_summary(tcfg, args.tts_workload, out, traces, args.tts_periods)
+    print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------- batch of cells
+def batch_slice(cfgs, rank, ws):
+    """The cells rank `rank` of `ws` advances: a disjoint, interleaved slice
+    of the batch, every cell with its own configuration and seed, so that a
+    cell's physics does not depend on the number of ranks."""
+    return cfgs[rank::ws]
+
+
 def run_batch(args, ws, rank, local):
     """A step is one RF period of every cell of the mixed-size batch (one
     pp_batch_advance_period); ranks take disjoint slices of the cell list."""
@@ -425,7 +500,7 @@ def run_batch(args, ws, rank, local):
         dist.init_process_group("gloo")
     from paper_2609_15043_b300 import phasorpic as pp, workloads
     cfgs_all = workloads.batch_cells()
-    cfgs = cfgs_all[rank::ws]
+    cfgs = batch_slice(cfgs_all, rank, ws)
     batch = pp.Batch(cfgs)
     for c, cfg in zip(batch.cells, cfgs):
         for sp in (0, 1):
@@ -511,19 +586,15 @@ def run_batch(args, ws, rank, local):
 
 
 # ---------------------------------------------------------------- time to stationarity
-def run_stationary(args, cfg, local):
+def stationary_runs(cfg, forms, max_periods, ml_weights=None, alpha_ml=1.0):
     """Wall time from the initial populations to the first stationary period
-    (paper_2609_15043_b300.stationarity), for the fused FP32 form and the
-    plain FP64 form from the same seeded state; each period's record is read
-    back for the test, as a user would."""
+    (paper_2609_15043_b300.stationarity) of each form, all from the same
+    seeded state; each period's record is read back for the test, as a user
+    would.  Returns the per-form results and traces."""
     import torch
-    torch.cuda.set_device(local)
     from paper_2609_15043_b300 import phasorpic as pp, workloads
     from paper_2609_15043_b300.stationarity import StationarityMonitor
     out, traces = {}, {}
-    forms = [f for f in args.forms.split(",") if f]
-    if args.ml_weights and "fused_ml" not in forms:
-        forms.append("fused_ml")
     for form in forms:
         c = cfg.replace(plain_fp64=1 if form == "fp64" else 0)
         cell = pp.Cell(c)
@@ -531,7 +602,7 @@ def run_stationary(args, cfg, local):
             cell.set_particles(sp, workloads.population(c, sp))
         if form == "fused_ml":
             from paper_2609_15043_b300.mlp_train import load_params
-            cell.ml_configure(load_params(args.ml_weights), alpha_ml=args.alpha_ml)
+            cell.ml_configure(load_params(ml_weights), alpha_ml=alpha_ml)
         sh = torch.cuda.current_stream().cuda_stream
         mon = StationarityMonitor(len(c.turn_r), c.p_target if c.power_control else None)
         torch.cuda.synchronize()
@@ -539,31 +610,74 @@ def run_stationary(args, cfg, local):
         cell.prime(sh)
         trace = []
         periods = 0
-        for periods in range(1, args.max_periods + 1):
+        for periods in range(1, max_periods + 1):
             cell.advance_period(1, sh)
             rec = cell.turn_phasors(sh)
             trace.append({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in rec.items()
                           if k in ("p_port", "p_ind", "p_cap", "p_cu", "eps_bal", "vg", "n_live", "accepted",
                                    "ml_err", "ml_tau", "ml_used")})
+            trace[-1]["x_abs"] = np.abs(np.asarray(rec["x_applied"])).tolist()
             if mon.update(rec):
                 break
         wall = time.perf_counter() - t0
         stationary = mon.stationary_at is not None
         out[form] = {"stationary": stationary, "periods": periods, "wall_s": wall,
-                     "ms_per_period": 1e3 * wall / periods, "last_window": mon.last,
+                     "ms_per_period": 1e3 * wall / periods,
+                     "last_window": {k: float(v) for k, v in mon.last.items()},
+                     "window_means": mon.window_means(),
                      "status": cell.status(),
                      "proposals_used": sum(1 for r in trace if r.get("ml_used"))}
         traces[form] = trace
         cell.close()
         del cell
         torch.cuda.empty_cache()
+    return out, traces
+
+
+def same_accuracy(out, traces, a="fused", b="fp64"):
+    """The fused FP32 form against the plain FP64 form: relative differences
+    of the stationary-window means (powers, |applied circuit state|), and of
+    the first period's record (both forms start from the same seeded state
+    and draw the same collision numbers)."""
+    fa, fb = out.get(a), out.get(b)
+    if not fa or not fb:
+        return None
+
+    def rel(x, y):
+        x, y = np.asarray(x, float), np.asarray(y, float)
+        keep = np.abs(y) > 1e-3 * np.max(np.abs(y))
+        return float(np.max(np.abs(x[keep] - y[keep]) / np.abs(y[keep]))) if np.any(keep) else 0.0
+
+    r = {}
+    if fa["stationary"] and fb["stationary"]:
+        wa, wb = fa["window_means"], fb["window_means"]
+        r["window_power_rel_diff"] = rel(wa["p"], wb["p"])
+        r["window_state_rel_diff"] = rel(wa["x_abs"], wb["x_abs"])
+    ta, tb = traces[a][0], traces[b][0]
+    r["period1_power_rel_diff"] = rel([ta[k] for k in ("p_port", "p_ind", "p_cap", "p_cu")],
+                                      [tb[k] for k in ("p_port", "p_ind", "p_cap", "p_cu")])
+    r["period1_state_rel_diff"] = rel(ta["x_abs"], tb["x_abs"])
+    return r
+
+
+def tts_summary(cfg, name, out, traces, max_periods):
     f, d = out.get("fused"), out.get("fp64")
     ratio = (d["wall_s"] / f["wall_s"]) if f and d and f["stationary"] and d["stationary"] else None
+    return {"workload": workload_desc(cfg, name), "max_periods": max_periods,
+            "criteria": "trailing 100 periods: |P_port-P_target|<=1%, balance<=0.5%, half-window drift<=0.5%",
+            "forms": out, "fp64_over_fused_wall": ratio, "same_accuracy": same_accuracy(out, traces)}
+
+
+def run_stationary(args, cfg, local):
+    """--time-to-stationary: the stationary runs of the chosen forms alone."""
+    import torch
+    torch.cuda.set_device(local)
+    forms = [f for f in args.forms.split(",") if f]
+    if args.ml_weights and "fused_ml" not in forms:
+        forms.append("fused_ml")
+    out, traces = stationary_runs(cfg, forms, args.max_periods, args.ml_weights, args.alpha_ml)
     line = {"metric": "time to a stationary state, fused FP32 vs plain FP64 PIC, 1 B300",
-            "config": {"workload": workload_desc(cfg, args.workload), "max_periods": args.max_periods,
-                       "criteria": "trailing 100 periods: |P_port-P_target|<=1%, balance<=0.5%, "
-                                   "half-window drift<=0.5%"},
-            "time_to_stationary": out, "fp64_over_fused_wall": ratio}
+            "time_to_stationary": tts_summary(cfg, args.workload, out, traces, args.max_periods)}
     if args.trace_out:
         with open(args.trace_out, "w") as fh:
             json.dump(traces, fh)
@@ -638,6 +752,7 @@ def main():
             cur = getattr(cfg, k)
             over[k] = type(cur)(float(v)) if isinstance(cur, (int, float)) else v
         cfg = cfg.replace(**over)
+    cfg = cfg.replace(implicit_es=1 if args.es == "implicit" else 0)
     if args.impl == "reference":
         run_reference(args, cfg, ws, rank)
     elif args.time_to_stationary:

@@ -236,7 +236,7 @@ class OracleCell:
         self.created += len(events)
         self.s += 1
         self.Q_last = Q
-        info = dict(stats=stats, events=len(events), Q=Q, J=J, Qk=Qk)
+        info = dict(stats=stats, events=len(events), Q=Q, J=J, Qk=Qk, Qs=Qs)
         if self.s % N == 0:
             info['record'] = self.period_end()
         return info

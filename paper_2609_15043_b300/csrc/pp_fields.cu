@@ -4,6 +4,8 @@
 // fields for the gather, turn charges and the per-step harmonic accumulation.
 #include "pp_internal.h"
 
+#include <atomic>
+
 #include <cmath>
 #include <string>
 
@@ -236,10 +238,16 @@ void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, con
     gemm_rm<T><<<grd, blk, 0, st>>>(rhs, s.Vf, s.t0, s.rows, s.M, s.M, skip);
     int mb = tri_modes_per_block<T>(s.rows);
     size_t shm = (size_t)(3 * mb + 1) * s.rows * sizeof(T);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
+    // the large shared-memory attribute, once per device (an attribute belongs
+    // to the device that is current when it is set); concurrent first calls
+    // set it twice, which is harmless
+    static std::atomic<unsigned long long> attr_devs[2];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(attr_devs[sizeof(T) == 8].load() & bit)) {
         cudaFuncSetAttribute(tri_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set[sizeof(T) == 8] = true;
+        attr_devs[sizeof(T) == 8].fetch_or(bit);
     }
     tri_solve<T><<<(s.M + mb - 1) / mb, 256, shm, st>>>(s.t0, s.t1, s.cp, s.invd, s.lo, s.rows, s.M, mb, skip);
     gemm_rm<T><<<grd, blk, 0, st>>>(s.t1, s.Vb, out, s.rows, s.M, s.M, skip);

@@ -78,10 +78,7 @@ __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpDev m, const dou
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s.bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (t == 0) tc::mbar_init1(&s.bar);
     // standardised, BF16-rounded inputs (zero-padded rows and columns)
     for (int q = t; q < kRows * kW; q += blockDim.x) {
         int r = q / kW, k = q % kW;
@@ -110,16 +107,9 @@ __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpDev m, const dou
             for (int ks = 0; ks < kW / 16; ++ks) {
                 uint64_t da = sdesc(ab + (uint32_t)ks * step_a, 128, 256);
                 uint64_t db = sdesc(bb + (uint32_t)ks * step_b, 128, 256);
-                uint32_t acc = ks > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                    : "memory");
+                tc::mma_bf16(tmem, da, db, idesc, ks > 0 ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&s.bar))
-                         : "memory");
+            tc::mma_commit(&s.bar);
         }
         __syncwarp();
         // every thread waits; the block then agrees on the outcome
@@ -138,12 +128,7 @@ __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpDev m, const dou
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < N; c0 += 16) {
             uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(lane_addr + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
             if (layer < 3) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {

@@ -70,6 +70,15 @@ class StationarityMonitor:
             self.stationary_at = len(self.rows) - 1
         return ok
 
+    def window_means(self):
+        """Means over the trailing window: the four powers (P_port, P_ind,
+        P_cap, P_Cu) and the magnitudes of the applied circuit state."""
+        W = min(self.c.window, len(self.rows))
+        if W == 0:
+            return None
+        return {"p": np.asarray(self.rows[-W:]).mean(axis=0).tolist(),
+                "x_abs": np.asarray(self.mags[-W:]).mean(axis=0).tolist(), "periods": W}
+
     def check(self):
         W = self.c.window
         if len(self.rows) < W:

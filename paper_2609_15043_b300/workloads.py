@@ -102,6 +102,14 @@ def cell60():
     return CellConfig(nr=128, nz=192, n_init=4_000_000, power_control=1, p_target=60.0)
 
 
+def coarse60():
+    """The plasma of the 128x192 cell (same geometry, gas, density and 60 W
+    target) on a 64x96 grid with 5e5 macroparticles per species: a cell that
+    reaches a stationary state within a few hundred periods in both the
+    fused and the plain FP64 form."""
+    return CellConfig(nr=64, nz=96, n_init=500_000, power_control=1, p_target=60.0)
+
+
 def cell100():
     return CellConfig(nr=256, nz=384, n_init=16_000_000, pressure_pa=10e-3 * _TORR,
                       dt=1.0 / (800 * 13.56e6), turn_r=[0.02, 0.035, 0.05, 0.065, 0.08],
@@ -130,7 +138,7 @@ def batch_cells(n_cells=32, seed=20260915):
     return out
 
 
-WORKLOADS = {"small": small, "cell60": cell60, "cell100": cell100}
+WORKLOADS = {"small": small, "cell60": cell60, "coarse60": coarse60, "cell100": cell100}
 
 
 def macro_weight(cfg):

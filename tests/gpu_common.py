@@ -41,7 +41,7 @@ def oracle_live(P):
     return by_uid({k: v[live] for k, v in P.items()})
 
 
-def check_step_potential(oc, g, tol_solve=1e-8, tol_oracle=1e-4):
+def check_step_potential(oc, g, tol_solve=1e-8, tol_oracle=1e-4, T=np.float32):
     """The step's Poisson solve on the GPU: its potential against the
     oracle's solve of the same operator (Eq. poisson, with the susceptibility
     of the GPU's own species charges in the direct-implicit form) applied to the
@@ -50,7 +50,7 @@ def check_step_potential(oc, g, tol_solve=1e-8, tol_oracle=1e-4):
     of a quasi-neutral plasma is a small difference of the species' charges)."""
     from paper_2609_15043_b300 import phasorpic as pp
     qe, qi = g.grid(pp.GRID_CHARGE_E), g.grid(pp.GRID_CHARGE_I)
-    chi = oc.susceptibility([qe, qi], np.float32) if oc.implicit else None
+    chi = oc.susceptibility([qe, qi], T) if oc.implicit else None
     ref = oc.solve_potential(qe + qi + g.grid(pp.GRID_WINDOW), oc.theta(oc.s), chi)
     phi = g.grid(pp.GRID_PHI)
     scale = np.max(np.abs(ref))

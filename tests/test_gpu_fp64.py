@@ -8,7 +8,7 @@ current within 1e-12 of the total (atomic summation order)."""
 import numpy as np
 import pytest
 
-from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live
+from gpu_common import require_gpu, oracle_cell, gpu_cell, by_uid, oracle_live, check_step_potential
 
 pytestmark = pytest.mark.gpu
 
@@ -40,10 +40,14 @@ def _run(cfg, pops, steps):
     return oc, g, info, tot
 
 
-def test_fp64_one_step_parity(small_fp64):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_fp64_one_step_parity(small_fp64, implicit):
+    """One step in each electrostatic form; in the direct-implicit form also
+    the potential of the step's chi solve (from the FP64 species charges)."""
     require_gpu()
     from paper_2609_15043_b300 import phasorpic as pp
     cfg, pops = small_fp64
+    cfg = cfg.replace(implicit_es=implicit)
     oc, g, info, tot = _run(cfg, pops, 1)
     cnt = g.counters()
     assert cnt["particle_steps"] == tot["pushed"]
@@ -65,12 +69,19 @@ def test_fp64_one_step_parity(small_fp64):
     assert np.max(np.abs(q - info["Q"])) <= 1e-12 * np.sum(np.abs(info["Q"]))
     j = g.grid(pp.GRID_JMOM)
     assert np.max(np.abs(j - info["J"])) <= 1e-12 * np.sum(np.abs(info["J"]))
+    if implicit:
+        for sp, grid in ((0, pp.GRID_CHARGE_E), (1, pp.GRID_CHARGE_I)):
+            qs = g.grid(grid)
+            assert np.max(np.abs(qs - info["Qs"][sp])) <= 1e-12 * np.sum(np.abs(info["Qs"][sp]))
+        check_step_potential(oc, g, T=np.float64, tol_oracle=1e-8)
     g.close()
 
 
-def test_fp64_ten_steps(small_fp64):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_fp64_ten_steps(small_fp64, implicit):
     require_gpu()
     cfg, pops = small_fp64
+    cfg = cfg.replace(implicit_es=implicit)
     oc, g, info, tot = _run(cfg, pops, 10)
     cnt = g.counters()
     assert cnt["absorbed"] == tot["absorbed"]
