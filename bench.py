@@ -663,9 +663,13 @@ def same_accuracy(out, traces, a="fused", b="fp64"):
 def tts_summary(cfg, name, out, traces, max_periods):
     f, d = out.get("fused"), out.get("fp64")
     ratio = (d["wall_s"] / f["wall_s"]) if f and d and f["stationary"] and d["stationary"] else None
+    # the FP64 form still short of the criterion at the cap: its wall time so
+    # far bounds the ratio from below
+    lower = (d["wall_s"] / f["wall_s"]) if f and d and f["stationary"] and not d["stationary"] else None
     return {"workload": workload_desc(cfg, name), "max_periods": max_periods,
             "criteria": "trailing 100 periods: |P_port-P_target|<=1%, balance<=0.5%, half-window drift<=0.5%",
-            "forms": out, "fp64_over_fused_wall": ratio, "same_accuracy": same_accuracy(out, traces)}
+            "forms": out, "fp64_over_fused_wall": ratio, "fp64_over_fused_wall_at_least": lower,
+            "same_accuracy": same_accuracy(out, traces)}
 
 
 def run_stationary(args, cfg, local):
