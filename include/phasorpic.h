@@ -389,6 +389,39 @@ int pp_get_turn_phasors(pp_cell* cell, pp_period_record* out, void* stream);
  */
 int pp_get_vacuum_impedance(pp_cell* cell, double* zvac, double* eps_rec, double* r_rf);
 
+/* A particle-free verification problem (Sec. 3.1-3.3, the paper's Tests 1-3):
+ * current sheets in vacuum on an nr x nz cell grid over 0 <= R <= r_max,
+ * 0 <= z <= z_max.  Sheet k is node column src_j[k] (R = src_j dR) over node
+ * rows src_i0[k] .. src_i1[k] (inclusive), with the uniform source density
+ * g_k = 1 / (N_k dz dR) of Eq. shape (winding +1). */
+typedef struct pp_vacuum_problem {
+    int32_t nr, nz;
+    double r_max, z_max;
+    double freq;
+    int32_t n_src;
+    int32_t src_j[PP_MAX_TURNS];
+    int32_t src_i0[PP_MAX_TURNS];
+    int32_t src_i1[PP_MAX_TURNS];
+} pp_vacuum_problem;
+
+/*
+ * pp_vacuum_impedance -- Z_vac of the sheets (Eq. zvac, n_src^2 complex,
+ * row-major: 2 n_src^2 doubles, real parts 0) from the N unit problems
+ * K U_k = g_k (Eq. unitfield, magnetoquasistatic: no w^2/c^2 term), solved on
+ * the device in FP64 by the separable solver of the cell's Helmholtz
+ * operator, and the reciprocity error (Eq. reciprocity).  E_theta takes
+ * Dirichlet values on every boundary node (axis, outer radius, both axial
+ * rows): zero when `boundary` is NULL, else boundary[k * nodes + n] for unit
+ * problem k (n = i (nr + 1) + j; interior entries ignored), e.g. the
+ * manufactured axial solutions of Test 3.  `ufields` (optional) receives the
+ * N unit fields on all nodes.  Host pointers; allocates and frees its own
+ * device memory and synchronises the device.  PP_E_CONFIG on an invalid
+ * problem (grid limits nr <= 1024, nz <= 8192, sheets on interior nodes),
+ * PP_E_CUDA on a device error.
+ */
+int pp_vacuum_impedance(const pp_vacuum_problem* problem, const double* boundary, double* zvac, double* eps_rec,
+                        double* ufields);
+
 /* Node grids (FP64, (nz+1)*(nr+1), row-major in z) readable by pp_get_grid. */
 #define PP_GRID_PHI 0            /* electrostatic potential of the last solve */
 #define PP_GRID_EC 1             /* composed E_c */

@@ -1004,6 +1004,15 @@ int pp_get_vacuum_impedance(pp_cell* h, double* zvac, double* eps_rec, double* r
     return PP_OK;
 }
 
+int pp_vacuum_impedance(const pp_vacuum_problem* problem, const double* boundary, double* zvac, double* eps_rec,
+                        double* ufields) {
+    if (!problem || !zvac) {
+        set_error("pp_vacuum_impedance: NULL problem or output");
+        return PP_E_ARG;
+    }
+    return vacuum_impedance(problem, boundary, zvac, eps_rec, ufields);
+}
+
 int pp_get_grid(pp_cell* h, int which, double* host, int64_t n, void* stream) {
     Cell* c = reinterpret_cast<Cell*>(h);
     if (!c || !host || n < c->nnodes) {

@@ -204,6 +204,53 @@ static int on_grid(double x, double h, int* k) {
     return 1;
 }
 
+// The FP64 separable solver of the Helmholtz operator (Eq. helmholtz_op) on
+// the interior unknowns i = 1..NZ-2, j = 1..NR-2 (E_theta = 0 on the axis and
+// the outer boundaries): the radial generalised eigenbasis T v = mu D v
+// (D = R) and per-mode Thomas factors in z; k2base = mu0 eps0 w^2 (0: MQS)
+// times the node-row average of eps_row.
+static void build_helmholtz(Cell* c, double k2base) {
+    const int NR = c->NR, rows = c->NZ - 2, MH = NR - 2;
+    const double dr = c->dr, dz = c->dz;
+    std::vector<double> T((size_t)MH * MH, 0.0), D(MH);
+    for (int jj = 0; jj < MH; ++jj) {
+        int j = jj + 1;
+        double R = j * dr, bj = R + dr / 2, bm = R - dr / 2;
+        T[(size_t)jj * MH + jj] = -(bj + bm) / (dr * dr) - 1.0 / R;
+        if (jj + 1 < MH) T[(size_t)jj * MH + jj + 1] = bj / (dr * dr);
+        if (jj > 0) T[(size_t)jj * MH + jj - 1] = bm / (dr * dr);
+        D[jj] = R;
+    }
+    std::vector<double> mu, V;
+    radial_basis(T, D, MH, mu, V);
+    std::vector<double> Vf((size_t)MH * MH), Vb((size_t)MH * MH);
+    for (int jj = 0; jj < MH; ++jj)
+        for (int m = 0; m < MH; ++m) {
+            Vf[(size_t)jj * MH + m] = D[jj] * V[(size_t)jj * MH + m];
+            Vb[(size_t)m * MH + jj] = V[(size_t)jj * MH + m];
+        }
+    std::vector<double> lo(rows), up(rows), diag((size_t)rows * MH), cp, invd;
+    for (int ii = 0; ii < rows; ++ii) {
+        int i = ii + 1;
+        double epsn = 0.5 * (c->eps_row[i - 1] + c->eps_row[i]);
+        lo[ii] = (ii > 0) ? 1.0 / (dz * dz) : 0.0;
+        up[ii] = 1.0 / (dz * dz);
+        for (int m = 0; m < MH; ++m) diag[(size_t)ii * MH + m] = -2.0 / (dz * dz) + mu[m] + k2base * epsn;
+    }
+    thomas_factors(lo, up, diag, rows, MH, cp, invd);
+    SepSolver<double>& s = c->hs;
+    s.rows = rows;
+    s.M = MH;
+    s.Vf = upload<double>(c, Vf);
+    s.Vb = upload<double>(c, Vb);
+    s.cp = upload<double>(c, cp);
+    s.invd = upload<double>(c, invd);
+    s.lo = upload<double>(c, lo);
+    s.t0 = c->alloc<double>((size_t)rows * MH);
+    s.t1 = c->alloc<double>((size_t)rows * MH);
+    c->d_hstage = c->alloc<double>((size_t)2 * rows * MH);
+}
+
 static int fail(const char* msg) {
     set_error(msg);
     return PP_E_CONFIG;
@@ -570,47 +617,7 @@ int setup_cell(Cell* c) {
         c->d_rT = c->alloc<double>(kMaxCapNodes);
     }
     // ---- Helmholtz FP64 separable solver (radial unknowns j = 1..NR-2)
-    {
-        int MH = NR - 2;
-        std::vector<double> T((size_t)MH * MH, 0.0), D(MH);
-        for (int jj = 0; jj < MH; ++jj) {
-            int j = jj + 1;
-            double R = j * dr, bj = R + dr / 2, bm = R - dr / 2;
-            T[(size_t)jj * MH + jj] = -(bj + bm) / (dr * dr) - 1.0 / R;
-            if (jj + 1 < MH) T[(size_t)jj * MH + jj + 1] = bj / (dr * dr);
-            if (jj > 0) T[(size_t)jj * MH + jj - 1] = bm / (dr * dr);
-            D[jj] = R;
-        }
-        std::vector<double> mu, V;
-        radial_basis(T, D, MH, mu, V);
-        std::vector<double> Vf((size_t)MH * MH), Vb((size_t)MH * MH);
-        for (int jj = 0; jj < MH; ++jj)
-            for (int m = 0; m < MH; ++m) {
-                Vf[(size_t)jj * MH + m] = D[jj] * V[(size_t)jj * MH + m];
-                Vb[(size_t)m * MH + jj] = V[(size_t)jj * MH + m];
-            }
-        double k2base = f.full_helmholtz ? kMu0 * kEps0 * c->omega * c->omega : 0.0;
-        std::vector<double> lo(rows), up(rows), diag((size_t)rows * MH), cp, invd;
-        for (int ii = 0; ii < rows; ++ii) {
-            int i = ii + 1;
-            double epsn = 0.5 * (c->eps_row[i - 1] + c->eps_row[i]);
-            lo[ii] = (ii > 0) ? 1.0 / (dz * dz) : 0.0;
-            up[ii] = 1.0 / (dz * dz);
-            for (int m = 0; m < MH; ++m) diag[(size_t)ii * MH + m] = -2.0 / (dz * dz) + mu[m] + k2base * epsn;
-        }
-        thomas_factors(lo, up, diag, rows, MH, cp, invd);
-        SepSolver<double>& s = c->hs;
-        s.rows = rows;
-        s.M = MH;
-        s.Vf = upload<double>(c, Vf);
-        s.Vb = upload<double>(c, Vb);
-        s.cp = upload<double>(c, cp);
-        s.invd = upload<double>(c, invd);
-        s.lo = upload<double>(c, lo);
-        s.t0 = c->alloc<double>((size_t)rows * MH);
-        s.t1 = c->alloc<double>((size_t)rows * MH);
-        c->d_hstage = c->alloc<double>((size_t)2 * rows * MH);
-    }
+    build_helmholtz(c, f.full_helmholtz ? kMu0 * kEps0 * c->omega * c->omega : 0.0);
     if (!c->d_hstage) {
         set_error("cudaMalloc failed for the solver storage");
         return PP_E_CUDA;
@@ -758,6 +765,104 @@ int setup_cell(Cell* c) {
         return PP_E_CUDA;
     }
     return PP_OK;
+}
+
+// ---------------------------------------------------------------- vacuum verification
+// Z_vac of current sheets in vacuum (the paper's particle-free Tests 1-3,
+// Sec. 3.1-3.3): the unit problems K U_k = g_k (Eq. unitfield, MQS) on the
+// device with the FP64 separable solver, Dirichlet values on the boundary
+// nodes (zero, or prescribed per unit problem), and the projection of
+// Eq. zvac with eps_rec (Eq. reciprocity) on the host.
+int vacuum_impedance(const pp_vacuum_problem* p, const double* boundary, double* zvac, double* eps_rec,
+                     double* ufields) {
+    if (p->nr < 3 || p->nz < 3 || p->r_max <= 0 || p->z_max <= 0 || p->freq <= 0)
+        return fail("pp_vacuum_impedance: grid and frequency must be positive (nr, nz >= 3)");
+    if (p->nr > 1024 || p->nz > 8192) return fail("pp_vacuum_impedance: grid too large (nr <= 1024, nz <= 8192)");
+    const int N = p->n_src;
+    if (N < 1 || N > PP_MAX_TURNS) return fail("pp_vacuum_impedance: n_src out of range");
+    for (int k = 0; k < N; ++k)
+        if (p->src_j[k] < 1 || p->src_j[k] > p->nr - 1 || p->src_i0[k] < 1 || p->src_i1[k] > p->nz - 1 ||
+            p->src_i1[k] < p->src_i0[k])
+            return fail("pp_vacuum_impedance: a sheet lies outside the interior nodes");
+    Cell* c = new Cell();
+    c->NR = p->nr + 1;
+    c->NZ = p->nz + 1;
+    c->nnodes = c->NR * c->NZ;
+    c->dr = p->r_max / p->nr;
+    c->dz = p->z_max / p->nz;
+    c->omega = 2.0 * kPi * p->freq;
+    c->eps_row.assign(p->nz, 1.0);
+    build_helmholtz(c, 0.0);
+    const int NR = c->NR, NZ = c->NZ, rows = c->hs.rows, MH = c->hs.M;
+    const size_t nint = (size_t)rows * MH;
+    const double dr = c->dr, dz = c->dz;
+    int rc = PP_OK;
+    if (!c->d_hstage) {
+        set_error("pp_vacuum_impedance: cudaMalloc failed");
+        rc = PP_E_CUDA;
+    }
+    std::vector<double> U((size_t)N * c->nnodes, 0.0), rhs(nint), sol(nint);
+    std::vector<double> gval(N);
+    for (int k = 0; k < N && rc == PP_OK; ++k) {
+        gval[k] = 1.0 / ((p->src_i1[k] - p->src_i0[k] + 1) * dz * dr);
+        const double* bnd = boundary ? boundary + (size_t)k * c->nnodes : nullptr;
+        // right-hand side mu0 w g_k of the interior equations, less the
+        // couplings to the boundary nodes' prescribed values
+        for (int ii = 0; ii < rows; ++ii)
+            for (int jj = 0; jj < MH; ++jj) {
+                const int i = ii + 1, j = jj + 1;
+                double v = 0.0;
+                if (j == p->src_j[k] && i >= p->src_i0[k] && i <= p->src_i1[k]) v = kMu0 * c->omega * gval[k];
+                if (bnd) {
+                    const double R = j * dr;
+                    if (i == 1) v -= bnd[j] / (dz * dz);
+                    if (i == NZ - 2) v -= bnd[(size_t)(NZ - 1) * NR + j] / (dz * dz);
+                    if (j == 1) v -= (R - dr / 2) / (R * dr * dr) * bnd[(size_t)i * NR];
+                    if (j == NR - 2) v -= (R + dr / 2) / (R * dr * dr) * bnd[(size_t)i * NR + NR - 1];
+                }
+                rhs[(size_t)ii * MH + jj] = v;
+            }
+        cudaMemcpy(c->d_hstage, rhs.data(), sizeof(double) * nint, cudaMemcpyHostToDevice);
+        sep_solve<double>(c->hs, c->d_hstage, c->d_hstage + nint, 0, nullptr);
+        const cudaError_t e = cudaMemcpy(sol.data(), c->d_hstage + nint, sizeof(double) * nint, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error(std::string("pp_vacuum_impedance: ") + cudaGetErrorString(e));
+            rc = PP_E_CUDA;
+            break;
+        }
+        double* Uk = U.data() + (size_t)k * c->nnodes;
+        for (int n = 0; n < c->nnodes; ++n) {
+            const int i = n / NR, j = n % NR;
+            if (i == 0 || i == NZ - 1 || j == 0 || j == NR - 1)
+                Uk[n] = bnd ? bnd[n] : 0.0;
+            else
+                Uk[n] = sol[(size_t)(i - 1) * MH + (j - 1)];
+        }
+    }
+    if (rc == PP_OK) {
+        // Eq. zvac: Z_kl = -i sum_n g_k U_l 2 pi R dz dR over sheet k's nodes
+        double zmax = 0.0, dmax = 0.0;
+        for (int k = 0; k < N; ++k)
+            for (int l = 0; l < N; ++l) {
+                double s = 0.0;
+                const int j = p->src_j[k];
+                for (int i = p->src_i0[k]; i <= p->src_i1[k]; ++i)
+                    s += gval[k] * U[(size_t)l * c->nnodes + (size_t)i * NR + j] * 2 * kPi * (j * dr) * dz * dr;
+                zvac[2 * (k * N + l)] = 0.0;
+                zvac[2 * (k * N + l) + 1] = -s;
+            }
+        for (int k = 0; k < N; ++k)
+            for (int l = 0; l < N; ++l) {
+                zmax = std::max(zmax, std::fabs(zvac[2 * (k * N + l) + 1]));
+                dmax = std::max(dmax, std::fabs(zvac[2 * (k * N + l) + 1] - zvac[2 * (l * N + k) + 1]));
+            }
+        if (eps_rec) *eps_rec = zmax > 0 ? dmax / zmax : 0.0;
+        if (ufields) memcpy(ufields, U.data(), sizeof(double) * U.size());
+    }
+    cudaDeviceSynchronize();
+    for (void* q : c->allocs) cudaFree(q);
+    delete c;
+    return rc;
 }
 
 }  // namespace pp

@@ -32,7 +32,7 @@ GRID_U0 = 16
 EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp_last_error",
            "pp_set_particles", "pp_get_particles", "pp_prime", "pp_advance_steps", "pp_advance_period",
            "pp_set_circuit_state", "pp_get_circuit_state", "pp_get_turn_phasors",
-           "pp_get_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
+           "pp_get_vacuum_impedance", "pp_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
            "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
            "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
            "pp_poisson_solve_noalloc", "pp_checkpoint", "pp_restore", "pp_get_particles64",
@@ -100,6 +100,12 @@ class PPTuning(C.Structure):
     _fields_ = [("sort_every", C.c_int32 * 2), ("push_blocks_per_sm", C.c_int32), ("reserved0", C.c_int32)]
 
 
+class PPVacuumProblem(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("nz", C.c_int32), ("r_max", C.c_double), ("z_max", C.c_double),
+                ("freq", C.c_double), ("n_src", C.c_int32), ("src_j", C.c_int32 * MAX_TURNS),
+                ("src_i0", C.c_int32 * MAX_TURNS), ("src_i1", C.c_int32 * MAX_TURNS)]
+
+
 class PPTrainOpts(C.Structure):
     _fields_ = [("n_in", C.c_int32), ("n_out", C.c_int32), ("batch", C.c_int32), ("reserved0", C.c_int32),
                 ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
@@ -127,6 +133,7 @@ def _load():
         "pp_get_circuit_state": (I, [V, V, P(D), V]),
         "pp_get_turn_phasors": (I, [V, P(PPRecord), V]),
         "pp_get_vacuum_impedance": (I, [V, V, P(D), V]),
+        "pp_vacuum_impedance": (I, [P(PPVacuumProblem), V, V, P(D), V]),
         "pp_get_grid": (I, [V, I, V, C.c_int64, V]),
         "pp_set_potential": (I, [V, V]),
         "pp_poisson_solve": (I, [V, V, V, V, V, P(I), P(D)]),
@@ -179,6 +186,30 @@ lib = _load()
 
 class PhasorPICError(RuntimeError):
     pass
+
+
+def vacuum_impedance(nr, nz, r_max, z_max, freq, sheets, boundary=None, unit_fields=False):
+    """pp_vacuum_impedance: Z_vac (complex n x n) and eps_rec of current sheets
+    in vacuum; sheets = [(j, i0, i1), ...] (node column, first and last node
+    row); boundary: optional (n, nz + 1, nr + 1) Dirichlet values of E_theta on
+    the boundary nodes of each unit problem.  Returns (Z, eps_rec) and the
+    unit fields when asked."""
+    p = PPVacuumProblem()
+    p.nr, p.nz, p.r_max, p.z_max, p.freq = nr, nz, r_max, z_max, freq
+    p.n_src = len(sheets)
+    for k, (j, i0, i1) in enumerate(sheets):
+        p.src_j[k], p.src_i0[k], p.src_i1[k] = j, i0, i1
+    n = len(sheets)
+    z = np.zeros(2 * n * n)
+    e = C.c_double()
+    bnd = None if boundary is None else np.ascontiguousarray(boundary, dtype=np.float64)
+    if bnd is not None and bnd.shape != (n, nz + 1, nr + 1):
+        raise ValueError("boundary must have shape (n_src, nz + 1, nr + 1)")
+    uf = np.zeros((n, nz + 1, nr + 1)) if unit_fields else None
+    _check(lib.pp_vacuum_impedance(C.byref(p), None if bnd is None else _ptr(bnd), _ptr(z), C.byref(e),
+                                   None if uf is None else _ptr(uf)), "pp_vacuum_impedance")
+    Z = z.view(complex).reshape(n, n)
+    return (Z, e.value, uf) if unit_fields else (Z, e.value)
 
 
 def _check(rc, what):

@@ -113,3 +113,15 @@ def test_trainer_and_tuning_arguments_are_checked_before_the_device():
     assert lib.pp_set_tuning(None, None) == -7
     assert lib.pp_autotune(None, 1, None, None, None) == -7
     assert lib.pp_batch_autotune(None, 1, None, None, None) == -7
+
+
+def test_vacuum_problem_is_validated_before_the_device():
+    """pp_vacuum_impedance refuses sheets off the interior nodes and empty
+    problems before any device work."""
+    from paper_2609_15043_b300 import phasorpic as pp
+    f = 13.56e6
+    for sheets in ([(0, 5, 10)], [(40, 5, 10)], [(10, 0, 10)], [(10, 5, 40)], [(10, 20, 10)], []):
+        with pytest.raises(pp.PhasorPICError, match="PP_E_CONFIG"):
+            pp.vacuum_impedance(40, 40, 0.04, 0.04, f, sheets)
+    with pytest.raises(pp.PhasorPICError, match="PP_E_CONFIG"):
+        pp.vacuum_impedance(2, 40, 0.04, 0.04, f, [(1, 5, 10)])
