@@ -472,8 +472,14 @@ def run_ours(args, cfg, ws, rank, local):
         # seeded state, and their agreement
         from paper_2609_15043_b300 import workloads as wl
         tcfg = wl.WORKLOADS[args.tts_workload]().replace(implicit_es=cfg.implicit_es)
-        out, traces = stationary_runs(tcfg, ["fused", "fp64"], args.tts_periods)
+        # with the learned proposal too, when the package ships a network
+        # trained (on the device) on pairs from this workload
+        wpath = os.path.join(ROOT, "paper_2609_15043_b300", "data", "proposal_%s.npz" % args.tts_workload)
+        forms = ["fused", "fp64"] + (["fused_ml"] if os.path.exists(wpath) else [])
+        out, traces = stationary_runs(tcfg, forms, args.tts_periods, wpath, args.alpha_ml)
         line["config"]["time_to_stationary"] = tts_summary(tcfg, args.tts_workload, out, traces, args.tts_periods)
+        if "fused_ml" in out:
+            line["config"]["time_to_stationary"]["proposal_weights"] = os.path.relpath(wpath, ROOT)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

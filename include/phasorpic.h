@@ -422,6 +422,26 @@ typedef struct pp_vacuum_problem {
 int pp_vacuum_impedance(const pp_vacuum_problem* problem, const double* boundary, double* zvac, double* eps_rec,
                         double* ufields);
 
+/*
+ * pp_vacuum_capacitance -- conductor charges of the sheets of `problem` as
+ * electrostatic conductors in a uniform dielectric eps_r (the capacitive
+ * channel of the paper's Test 3, Sec. 3.3): for unit problem l = 0..n_src-1
+ * the sheets carry the potentials sheet_v[l * n_src + k], the boundary nodes
+ * (both axial rows and the outer radius; the axis has no R- face) the values
+ * boundary[l * nodes + n], and the free nodes satisfy Laplace's equation with
+ * the FV operator of Eq. poisson (Eq. epseff with a uniform eps_r, Eq. areas).
+ * C[k * n_src + l] receives the Gauss-law charge of sheet k (Eq. facecharge
+ * over its external faces) in unit problem l; `phis` (optional) the n_src
+ * potentials on all nodes.  Every sheet must span all interior node rows
+ * (src_i0 = 1, src_i1 = nz - 1), which keeps the operator separable: the
+ * solves run in FP64 on the device (radial eigenbasis over the free columns,
+ * per-mode tridiagonal solves in z).  Host pointers; allocates and frees its
+ * own device memory and synchronises the device.  PP_E_CONFIG on an invalid
+ * problem, PP_E_ARG on NULL pointers, PP_E_CUDA on a device error.
+ */
+int pp_vacuum_capacitance(const pp_vacuum_problem* problem, double eps_r, const double* sheet_v,
+                          const double* boundary, double* C, double* phis);
+
 /* Node grids (FP64, (nz+1)*(nr+1), row-major in z) readable by pp_get_grid. */
 #define PP_GRID_PHI 0            /* electrostatic potential of the last solve */
 #define PP_GRID_EC 1             /* composed E_c */

@@ -1013,6 +1013,15 @@ int pp_vacuum_impedance(const pp_vacuum_problem* problem, const double* boundary
     return vacuum_impedance(problem, boundary, zvac, eps_rec, ufields);
 }
 
+int pp_vacuum_capacitance(const pp_vacuum_problem* problem, double eps_r, const double* sheet_v,
+                          const double* boundary, double* C, double* phis) {
+    if (!problem || !sheet_v || !boundary || !C) {
+        set_error("pp_vacuum_capacitance: NULL argument");
+        return PP_E_ARG;
+    }
+    return vacuum_capacitance(problem, eps_r, sheet_v, boundary, C, phis);
+}
+
 int pp_get_grid(pp_cell* h, int which, double* host, int64_t n, void* stream) {
     Cell* c = reinterpret_cast<Cell*>(h);
     if (!c || !host || n < c->nnodes) {

@@ -320,6 +320,8 @@ enum { PH_PUSH = 0, PH_POISSON, PH_SORT, PH_OTHER, PH_PERIOD, PH_N };
 int setup_cell(Cell* c);
 int vacuum_impedance(const pp_vacuum_problem* p, const double* boundary, double* zvac, double* eps_rec,
                      double* ufields);
+int vacuum_capacitance(const pp_vacuum_problem* p, double eps_r, const double* sheet_v, const double* boundary,
+                       double* C, double* phis);
 
 // ---------------------------------------------------------------- launchers
 void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_next, cudaStream_t st);

@@ -865,4 +865,152 @@ int vacuum_impedance(const pp_vacuum_problem* p, const double* boundary, double*
     return rc;
 }
 
+// Conductor charges of current-sheet conductors in a uniform dielectric (the
+// electrostatic channel of the paper's Test 3, Sec. 3.3): for each unit
+// problem l the sheets carry the potentials sheet_v[l][k], every boundary
+// node its prescribed value (the axial rows and the outer radius; no R- face
+// on the axis), and Laplace's equation (Eq. poisson without charge, the FV
+// operator of Eq. epseff with eps_r uniform) holds on the free nodes.  The
+// sheets span every interior node row, so with their columns as Dirichlet
+// columns the operator stays separable: a radial generalised eigenbasis on
+// the free columns and per-mode tridiagonal solves in z, in FP64 on the
+// device.  C[k][l] is the Gauss-law charge of sheet k (Eq. facecharge over
+// its external faces, Eq. areas) in unit problem l.
+int vacuum_capacitance(const pp_vacuum_problem* p, double eps_r, const double* sheet_v, const double* boundary,
+                       double* C, double* phis) {
+    if (p->nr < 3 || p->nz < 3 || p->r_max <= 0 || p->z_max <= 0 || !(eps_r > 0))
+        return fail("pp_vacuum_capacitance: grid and eps_r must be positive (nr, nz >= 3)");
+    if (p->nr > 1024 || p->nz > 8192) return fail("pp_vacuum_capacitance: grid too large (nr <= 1024, nz <= 8192)");
+    const int N = p->n_src;
+    if (N < 1 || N > PP_MAX_TURNS) return fail("pp_vacuum_capacitance: n_src out of range");
+    const int NR = p->nr + 1, NZ = p->nz + 1, rows = NZ - 2;
+    std::vector<int> col_sheet(NR, -1);
+    for (int k = 0; k < N; ++k) {
+        if (p->src_j[k] < 1 || p->src_j[k] > p->nr - 1 || p->src_i0[k] != 1 || p->src_i1[k] != p->nz - 1)
+            return fail("pp_vacuum_capacitance: every sheet must span all interior node rows of an interior column");
+        if (col_sheet[p->src_j[k]] >= 0) return fail("pp_vacuum_capacitance: two sheets share a column");
+        col_sheet[p->src_j[k]] = k;
+    }
+    const double dr = p->r_max / p->nr, dz = p->z_max / p->nz;
+    // free columns: the axis and every column below the outer radius that is
+    // not a sheet
+    std::vector<int> F;
+    for (int j = 0; j <= NR - 2; ++j)
+        if (col_sheet[j] < 0) F.push_back(j);
+    const int M = (int)F.size();
+    auto area_z = [&](int j) { return j == 0 ? kPi * (dr / 2) * (dr / 2) : 2 * kPi * (j * dr) * dr; };
+    auto rface = [&](int j, int s) { return 2 * kPi * (j * dr + s * dr / 2) * dz / dr; };   // A_r / dR
+    // radial operator on the free columns (couplings to sheet columns and to
+    // the outer radius go to the right-hand side) and the z-face weights
+    std::vector<double> T((size_t)M * M, 0.0), D(M);
+    for (int a = 0; a < M; ++a) {
+        const int j = F[a];
+        double diag = 0.0;
+        for (int s = -1; s <= 1; s += 2) {
+            if (j == 0 && s < 0) continue;
+            const double c = rface(j, s);
+            diag -= c;
+            const int jn = j + s;
+            if (jn >= 0 && jn <= NR - 2 && col_sheet[jn] < 0) {
+                const int b = (int)(std::lower_bound(F.begin(), F.end(), jn) - F.begin());
+                T[(size_t)a * M + b] = c;
+            }
+        }
+        T[(size_t)a * M + a] = diag;
+        D[a] = area_z(j) / dz;
+    }
+    std::vector<double> mu, V;
+    radial_basis(T, D, M, mu, V);
+    // D d2z phi + T phi = rhs with T V = D V Lambda, V' D V = I: per mode
+    // d2z c + Lambda c = V' rhs (forward transform V', backward V)
+    std::vector<double> Vf((size_t)M * M), Vb((size_t)M * M);
+    for (int a = 0; a < M; ++a)
+        for (int m = 0; m < M; ++m) {
+            Vf[(size_t)a * M + m] = V[(size_t)a * M + m];
+            Vb[(size_t)m * M + a] = V[(size_t)a * M + m];
+        }
+    std::vector<double> lo(rows), up(rows), diag((size_t)rows * M), cp, invd;
+    for (int ii = 0; ii < rows; ++ii) {
+        lo[ii] = ii > 0 ? 1.0 : 0.0;
+        up[ii] = 1.0;
+        for (int m = 0; m < M; ++m) diag[(size_t)ii * M + m] = -2.0 + mu[m];
+    }
+    thomas_factors(lo, up, diag, rows, M, cp, invd);
+    Cell* c = new Cell();
+    SepSolver<double>& s = c->hs;
+    s.rows = rows;
+    s.M = M;
+    s.Vf = upload<double>(c, Vf);
+    s.Vb = upload<double>(c, Vb);
+    s.cp = upload<double>(c, cp);
+    s.invd = upload<double>(c, invd);
+    s.lo = upload<double>(c, lo);
+    s.t0 = c->alloc<double>((size_t)rows * M);
+    s.t1 = c->alloc<double>((size_t)rows * M);
+    double* stage = c->alloc<double>((size_t)2 * rows * M);
+    int rc = PP_OK;
+    if (!stage || !s.t1) {
+        set_error("pp_vacuum_capacitance: cudaMalloc failed");
+        rc = PP_E_CUDA;
+    }
+    const size_t nint = (size_t)rows * M, nn = (size_t)NR * NZ;
+    std::vector<double> rhs(nint), sol(nint), phi(nn);
+    for (int l = 0; l < N && rc == PP_OK; ++l) {
+        const double* bnd = boundary + (size_t)l * nn;
+        const double* vk = sheet_v + (size_t)l * N;
+        // the node potentials known before the solve
+        for (size_t n = 0; n < nn; ++n) {
+            const int i = (int)(n / NR), j = (int)(n % NR);
+            const bool edge = i == 0 || i == NZ - 1 || j == NR - 1;
+            phi[n] = edge ? bnd[n] : (col_sheet[j] >= 0 ? vk[col_sheet[j]] : 0.0);
+        }
+        // right-hand side of the free nodes' equations (divided by eps):
+        // minus the couplings to the known potentials
+        for (int ii = 0; ii < rows; ++ii) {
+            const int i = ii + 1;
+            for (int a = 0; a < M; ++a) {
+                const int j = F[a];
+                double v = 0.0;
+                if (i == 1) v -= D[a] * phi[(size_t)j];
+                if (i == NZ - 2) v -= D[a] * phi[(size_t)(NZ - 1) * NR + j];
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    if (j == 0 && sg < 0) continue;
+                    const int jn = j + sg;
+                    if (jn == NR - 1 || col_sheet[jn] >= 0) v -= rface(j, sg) * phi[(size_t)i * NR + jn];
+                }
+                rhs[(size_t)ii * M + a] = v;
+            }
+        }
+        cudaMemcpy(stage, rhs.data(), sizeof(double) * nint, cudaMemcpyHostToDevice);
+        sep_solve<double>(s, stage, stage + nint, 0, nullptr);
+        const cudaError_t e = cudaMemcpy(sol.data(), stage + nint, sizeof(double) * nint, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error(std::string("pp_vacuum_capacitance: ") + cudaGetErrorString(e));
+            rc = PP_E_CUDA;
+            break;
+        }
+        for (int ii = 0; ii < rows; ++ii)
+            for (int a = 0; a < M; ++a) phi[(size_t)(ii + 1) * NR + F[a]] = sol[(size_t)ii * M + a];
+        if (phis) memcpy(phis + (size_t)l * nn, phi.data(), sizeof(double) * nn);
+        // Eq. facecharge: each sheet node's faces to nodes that are not of
+        // the same sheet (its vertical neighbours are, except at the ends)
+        for (int k = 0; k < N; ++k) {
+            const int j = p->src_j[k];
+            double q = 0.0;
+            for (int i = 1; i <= NZ - 2; ++i) {
+                const double pc = phi[(size_t)i * NR + j];
+                if (i == 1) q += area_z(j) / dz * (pc - phi[(size_t)j]);
+                if (i == NZ - 2) q += area_z(j) / dz * (pc - phi[(size_t)(NZ - 1) * NR + j]);
+                q += rface(j, +1) * (pc - phi[(size_t)i * NR + j + 1]);
+                q += rface(j, -1) * (pc - phi[(size_t)i * NR + j - 1]);
+            }
+            C[(size_t)k * N + l] = kEps0 * eps_r * q;
+        }
+    }
+    cudaDeviceSynchronize();
+    for (void* q : c->allocs) cudaFree(q);
+    delete c;
+    return rc;
+}
+
 }  // namespace pp

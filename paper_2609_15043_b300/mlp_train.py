@@ -39,8 +39,8 @@ def collect(args):
     import torch
     from . import phasorpic as pp, workloads
     rng = np.random.default_rng(args.seed)
-    base = workloads.cell60().replace(density=args.density, capacity_factor=args.capacity_factor,
-                                      implicit_es=1 if args.es == "implicit" else 0)
+    base = workloads.WORKLOADS[args.workload]().replace(density=args.density, capacity_factor=args.capacity_factor,
+                                                        implicit_es=1 if args.es == "implicit" else 0)
     cfgs = [base.replace(n_init=args.n_init, seed=args.seed + 101 * i,
                          p_target=float(rng.uniform(args.p_min, args.p_max)))
             for i in range(args.cells)]
@@ -172,6 +172,7 @@ def main():
     c.add_argument("--p-max", type=float, default=150.0)
     c.add_argument("--capacity-factor", type=float, default=1.5)
     c.add_argument("--es", default="implicit", choices=["implicit", "explicit"], help="electrostatics of the cells")
+    c.add_argument("--workload", default="cell60", help="cell shape of the collection runs (workloads.WORKLOADS)")
     t = sub.add_parser("train")
     t.add_argument("--pairs", required=True)
     t.add_argument("--out", required=True)

@@ -32,7 +32,7 @@ GRID_U0 = 16
 EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp_last_error",
            "pp_set_particles", "pp_get_particles", "pp_prime", "pp_advance_steps", "pp_advance_period",
            "pp_set_circuit_state", "pp_get_circuit_state", "pp_get_turn_phasors",
-           "pp_get_vacuum_impedance", "pp_vacuum_impedance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
+           "pp_get_vacuum_impedance", "pp_vacuum_impedance", "pp_vacuum_capacitance", "pp_get_grid", "pp_set_potential", "pp_poisson_solve",
            "pp_helmholtz_solve", "pp_get_status", "pp_get_counters", "pp_get_poisson_stats",
            "pp_set_profiling", "pp_get_phase_times", "pp_launch_count", "pp_n_rf", "pp_step_index",
            "pp_poisson_solve_noalloc", "pp_checkpoint", "pp_restore", "pp_get_particles64",
@@ -134,6 +134,7 @@ def _load():
         "pp_get_turn_phasors": (I, [V, P(PPRecord), V]),
         "pp_get_vacuum_impedance": (I, [V, V, P(D), V]),
         "pp_vacuum_impedance": (I, [P(PPVacuumProblem), V, V, P(D), V]),
+        "pp_vacuum_capacitance": (I, [P(PPVacuumProblem), D, V, V, V, V]),
         "pp_get_grid": (I, [V, I, V, C.c_int64, V]),
         "pp_set_potential": (I, [V, V]),
         "pp_poisson_solve": (I, [V, V, V, V, V, P(I), P(D)]),
@@ -210,6 +211,28 @@ def vacuum_impedance(nr, nz, r_max, z_max, freq, sheets, boundary=None, unit_fie
                                    None if uf is None else _ptr(uf)), "pp_vacuum_impedance")
     Z = z.view(complex).reshape(n, n)
     return (Z, e.value, uf) if unit_fields else (Z, e.value)
+
+
+def vacuum_capacitance(nr, nz, r_max, z_max, columns, eps_r, sheet_v, boundary, potentials=False):
+    """pp_vacuum_capacitance: C[k, l] = charge of sheet k (node column
+    columns[k], spanning every interior node row) in unit problem l, whose
+    sheet potentials are sheet_v[l] and boundary values boundary[l] (shape
+    (n, nz + 1, nr + 1)).  Returns C and, when asked, the potentials."""
+    p = PPVacuumProblem()
+    p.nr, p.nz, p.r_max, p.z_max, p.freq = nr, nz, r_max, z_max, 1.0
+    p.n_src = len(columns)
+    for k, j in enumerate(columns):
+        p.src_j[k], p.src_i0[k], p.src_i1[k] = j, 1, nz - 1
+    n = len(columns)
+    sv = np.ascontiguousarray(sheet_v, dtype=np.float64)
+    bnd = np.ascontiguousarray(boundary, dtype=np.float64)
+    if sv.shape != (n, n) or bnd.shape != (n, nz + 1, nr + 1):
+        raise ValueError("sheet_v must be (n, n) and boundary (n, nz + 1, nr + 1)")
+    Cm = np.zeros((n, n))
+    ph = np.zeros((n, nz + 1, nr + 1)) if potentials else None
+    _check(lib.pp_vacuum_capacitance(C.byref(p), float(eps_r), _ptr(sv), _ptr(bnd), _ptr(Cm),
+                                     None if ph is None else _ptr(ph)), "pp_vacuum_capacitance")
+    return (Cm, ph) if potentials else Cm
 
 
 def _check(rc, what):

@@ -2,8 +2,10 @@
 (pp_vacuum_impedance: the unit problems of Eq. unitfield solved by the
 device's FP64 separable Helmholtz solver, then the projection of Eq. zvac):
 Tests 1 and 2 (Sec. 3.1-3.2, Tables S1results, S1cases, S2results) on the
-paper's 1241 x 121 node grid and its sensitivity grids, and the inductive
-channel of Test 3 (Sec. 3.3: M_h with the manufactured axial boundaries).
+paper's 1241 x 121 node grid and its sensitivity grids, and Test 3 (Sec. 3.3):
+M_h with the manufactured axial boundaries, C_h from the Laplace solves with
+the sheets as conductors (pp_vacuum_capacitance), and the semidiscrete
+network state they give.
 Each result is checked against the printed numbers and against the oracle's
 sparse direct solve of the same problem."""
 import math
@@ -99,3 +101,60 @@ def test_test3_inductance_on_the_gpu():
     assert eta_m == pytest.approx(S3["eta_M_h1"], rel=0.02)
     ref = v.FiveNode(h).Mh
     assert np.max(np.abs(Mh - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def _t3_capacitance(h=1e-3):
+    from paper_2609_15043_b300 import phasorpic as pp
+    from oracle import verification as v
+    nsrc = int(round(v.T3_ELL / h))
+    nz, nr = nsrc + 1, int(round(v.T3_B / h))
+    R = np.arange(nr + 1) * h
+    cols = [int(round(a / h)) for a in v.T3_A]
+    bnd = np.zeros((5, nz + 1, nr + 1))
+    for l in range(5):
+        V = np.zeros(5)
+        V[l] = 1.0
+        prof = v.t3_potential_analytic(R, V)
+        bnd[l, 0, :] = prof
+        bnd[l, -1, :] = prof
+        bnd[l, :, -1] = 0.0                      # the grounded outer radius
+    return pp.vacuum_capacitance(nr, nz, v.T3_B, nz * h, cols, v.T3_EPS, np.eye(5), bnd)
+
+
+def test_test3_capacitance_and_state_on_the_gpu():
+    """C_h of Test 3 from five Laplace solves on the GPU: its relative
+    Frobenius error against the continuous C of Eq. t7C (Sec. 3.3: 1.21e-4),
+    the oracle's C_h to solver precision, zero charge for zero potentials
+    (appendix), and with the GPU's M_h the field-circuit column of Table
+    t7phasors (Eq. t7network) and its distance 1.90e-5 to the continuous state
+    (Eq. t7error)."""
+    require_gpu()
+    from paper_2609_15043_b300 import phasorpic as pp
+    from oracle import verification as v
+    Ch = _t3_capacitance()
+    C = v.t3_continuous_C()
+    ec = np.linalg.norm(Ch - C) / np.linalg.norm(C)
+    assert ec == pytest.approx(S3["Ch_err_h1"], rel=0.01)
+    five = v.FiveNode(1e-3)
+    assert np.max(np.abs(Ch - five.Ch)) <= 1e-9 * np.max(np.abs(five.Ch))
+    # zero potentials everywhere give zero charge
+    h = 1e-3
+    nz, nr = int(round(v.T3_ELL / h)) + 1, int(round(v.T3_B / h))
+    cols = [int(round(a / h)) for a in v.T3_A]
+    Z0 = pp.vacuum_capacitance(nr, nz, v.T3_B, nz * h, cols, v.T3_EPS, np.zeros((5, 5)),
+                               np.zeros((5, nz + 1, nr + 1)))
+    assert np.max(np.abs(Z0)) == 0.0
+    # the semidiscrete state from the GPU's C_h and M_h
+    R = np.arange(nr + 1) * h
+    sheets, bnd = [], np.zeros((5, nz + 1, nr + 1))
+    for k, a in enumerate(v.T3_A):
+        sheets.append((int(round(a / h)), 1, nz - 1))
+        prof = v.t3_unit_analytic(R, a)
+        bnd[k, 0, :] = prof
+        bnd[k, -1, :] = prof
+    Z, _ = pp.vacuum_impedance(nr, nz, v.T3_B, nz * h, F_RF, sheets, boundary=bnd)
+    xh, _ = v.t3_network(Ch, Z.imag / OMEGA)
+    x_calc = np.array([float(r[2]) + 1j * float(r[3]) for r in G3 if r[0] == "x"])
+    x_cont = np.array([float(r[4]) + 1j * float(r[5]) for r in G3 if r[0] == "x"])
+    assert np.max(np.abs(xh - x_calc)) < 6e-8
+    assert v.t3_error(xh, x_cont) == pytest.approx(S3["state_err_cont_h1"], rel=0.01)
