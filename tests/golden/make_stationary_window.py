@@ -1,7 +1,9 @@
 """Writes tests/golden/stationary_window_small.txt: the oracle's per-period
-records of the small cell (32 x 48 cells, 2e4 macroparticles per species,
-fixed 300 V source) in the direct-implicit form, for the GPU's stationary-
-window parity test (period-averaged circuit phasors and absorbed powers).
+records of a small cell (the small workload's geometry, gas, 2e4
+macroparticles per species and fixed 300 V source, on 64 x 96 cells at an
+initial density of 3e15 m^-3, where its population levels off) in the
+direct-implicit form, for the GPU's stationary-window parity test
+(period-averaged circuit phasors and absorbed powers).
 
 Calls only the oracle (and the shared seeded input generators).  The run is
 the oracle's float32 instantiation, the one whose arithmetic the fused GPU
@@ -26,9 +28,13 @@ from paper_2609_15043_b300 import workloads            # noqa: E402
 OUT = os.path.join(ROOT, "tests", "golden", "stationary_window_small.txt")
 
 
+def window_cell():
+    return workloads.small().replace(nr=64, nz=96, density=3e15, implicit_es=1)
+
+
 def main():
     periods = int(sys.argv[1]) if len(sys.argv) > 1 else 80
-    cfg = workloads.small().replace(implicit_es=1)
+    cfg = window_cell()
     w = workloads.macro_weight(cfg)
     oc = OracleCell(cfg, [w, w])
     for sp in (0, 1):
@@ -41,8 +47,8 @@ def main():
     # the file grows by one row per completed period, so a long run can be
     # stopped and its rows used
     with open(OUT, "w") as f:
-        f.write("# Oracle records of the small cell (32x48 cells, 2e4 macroparticles per species, fixed 300 V\n")
-        f.write("# source, direct-implicit electrostatics, float32 instantiation, seeded populations), one row\n")
+        f.write("# Oracle records of a small cell (64x96 cells, 2e4 macroparticles per species, n0 = 3e15 m^-3,\n")
+        f.write("# fixed 300 V source, direct-implicit electrostatics, float32 instantiation, seeded populations), one row\n")
         f.write("# per completed RF period (Sec. 2.5): period p_port p_ind p_cap p_cu |x_1| .. |x_%d| (W, A, V)\n"
                 % (2 * n + 1))
         f.write("# written by tests/golden/make_stationary_window.py %d\n" % periods)
