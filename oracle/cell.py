@@ -16,6 +16,18 @@ powers (Eqs. pind, pcap, pcap_phasor, pport), the controller, the target
 network solve, relaxation (Eq. relaxation), residuals, and the composed field
 for the next cycle (Eq. compose).  phi at the cycle boundary is then re-solved
 with the new turn potentials so the first step of the next cycle sees them.
+
+Multiharmonic extension (Sec. 4, with n_harmonics = M > 1): every retained
+frequency m w, m = 2..M, has its own Helmholtz operator (the eps_r (m w)^2/c^2
+term), unit fields, Z_vac, skin resistance, source impedance and network.  The
+per-step accumulation projects J and Q on cos m theta, sin m theta as on the
+fundamental (Eq. fourier), the period end turns them into V_p^(m) and
+I_cap^(m) = i m w Q^(m), and the network at m w is solved and relaxed with no
+source (the generator is sinusoidal: V_g drives the fundamental only).  The
+turn potentials and E_theta, B used by the next period's steps are the sums of
+all retained harmonics (waveform reconstruction, exp(+i m w t) peak phasors);
+the powers of the record are the sums over the harmonics (the time-domain
+P_ind and P_cap carry them by construction).
 """
 import math
 import numpy as np
@@ -68,6 +80,28 @@ class OracleCell:
         self.Ecp = np.zeros((g.NZ, g.NR))
         self.Essp = np.zeros((g.NZ, g.NR))
         self._compose()
+        # --- retained harmonics m = 2..M (zero state: no source at m w) ------
+        self.M = max(1, int(getattr(cfg, "n_harmonics", 1)))
+        self.harm = []
+        for m in range(2, self.M + 1):
+            wm = m * self.omega
+            k2m = None if k2 is None else MU0 * EPS0 * wm ** 2 * self.geo.eps_node
+            hm = fields.HelmholtzSolver(g, k2m)
+            Um = fields.unit_fields(hm, self.geo.gk, wm)
+            zvm, _ = fields.vacuum_impedance(g, self.geo.gk, Um)
+            if cfg.r_rf_override >= 0:
+                rrf = np.full(self.N, cfg.r_rf_override)
+            else:
+                rrf = circuit.skin_resistance(cfg.turn_r, cfg.wire_radius, wm, cfg.rho20, cfg.alpha_cu,
+                                              cfg.t_coil_c)
+            zsm = circuit.z_source(cfg.r_g, cfg.r_m, cfg.l_m, cfg.c_m, wm)
+            ztm = zvm + np.diag(rrf)
+            h = dict(m=m, omega=wm, helm=hm, U=Um, zvac=zvm, r_rf=rrf, zs=zsm, zturn=ztm,
+                     A=circuit.network_matrix(zsm, ztm, self.c_stray, wm),
+                     x=np.zeros(2 * self.N + 1, complex),
+                     Ecp=np.zeros((g.NZ, g.NR)), Essp=np.zeros((g.NZ, g.NR)))
+            self._compose_h(h)
+            self.harm.append(h)
         # --- particles ----------------------------------------------------------
         self.weights = weights
         self._species = {}
@@ -101,7 +135,20 @@ class OracleCell:
 
     def turn_potentials(self, th):
         V = self.x[1 + self.N:]
-        return V.real * math.cos(th) + (-V.imag) * math.sin(th)      # Eq. dirichlet
+        out = V.real * math.cos(th) + (-V.imag) * math.sin(th)       # Eq. dirichlet
+        for h in self.harm:
+            Vm, mt = h["x"][1 + self.N:], h["m"] * th
+            out = out + (Vm.real * math.cos(mt) + (-Vm.imag) * math.sin(mt))
+        return out
+
+    def etheta(self, th):
+        """E_theta at phase th (Eq. et_reconstruct, summed over the retained
+        harmonics)."""
+        Et = self.Ec * math.cos(th) - self.Ess * math.sin(th)
+        for h in self.harm:
+            mt = h["m"] * th
+            Et = Et + (h["Ec"] * math.cos(mt) - h["Ess"] * math.sin(mt))
+        return Et
 
     def dirichlet_values(self, th):
         vals = np.zeros((self.g.NZ, self.g.NR))
@@ -166,6 +213,11 @@ class OracleCell:
         Et = self.Ec * c - self.Ess * s
         Br = self.Brc * c + self.Brs * s
         Bz = self.Bzc * c + self.Bzs * s
+        for h in self.harm:
+            cm, sm = math.cos(h["m"] * th), math.sin(h["m"] * th)
+            Et = Et + (h["Ec"] * cm - h["Ess"] * sm)
+            Br = Br + (h["Brc"] * cm + h["Brs"] * sm)
+            Bz = Bz + (h["Bzc"] * cm + h["Bzs"] * sm)
         if not self.cfg.magnetic_force:
             Br = np.zeros_like(Br)
             Bz = np.zeros_like(Bz)
@@ -205,7 +257,7 @@ class OracleCell:
             events.extend(ev)
         Q = Qs[0] + Qs[1]
         if drive is not None:
-            Et = self.Ec * math.cos(th_old) - self.Ess * math.sin(th_old)   # Eq. et_reconstruct
+            Et = self.etheta(th_old)                                        # Eq. et_reconstruct
             Jd = np.asarray(drive(th_old, Et), dtype=np.float64)
             J += Jd
             stats['p_ind'] += float(np.sum(Jd * Et))
@@ -225,6 +277,12 @@ class OracleCell:
         self.Js += (2.0 / N) * Jd * math.sin(th_old)
         self.Qc += (2.0 / N) * Qk * math.cos(th_new)
         self.Qs += (2.0 / N) * Qk * math.sin(th_new)
+        for h in self.harm:
+            m = h["m"]
+            h["Jc"] += (2.0 / N) * Jd * math.cos(m * th_old)
+            h["Js"] += (2.0 / N) * Jd * math.sin(m * th_old)
+            h["Qc"] += (2.0 / N) * Qk * math.cos(m * th_new)
+            h["Qs"] += (2.0 / N) * Qk * math.sin(m * th_new)
         self.p_ind += stats['p_ind'] / N
         self.p_es += stats['p_es'] / N
         self.samples_V.append(Vk)
@@ -276,6 +334,18 @@ class OracleCell:
         self.coll = np.zeros((2, 3), np.int64)
         self.absorbed = 0
         self.created = 0
+        for h in getattr(self, "harm", []):
+            h["Jc"] = np.zeros((g.NZ, g.NR))
+            h["Js"] = np.zeros((g.NZ, g.NR))
+            h["Qc"] = np.zeros(self.N)
+            h["Qs"] = np.zeros(self.N)
+
+    def _compose_h(self, h):
+        """Eq. compose and the B phasors at harmonic m (Faraday's law at m w)."""
+        I = h["x"][1:1 + self.N]
+        h["Ec"] = h["Ecp"] + np.tensordot(-I.imag, h["U"], axes=1)
+        h["Ess"] = h["Essp"] + np.tensordot(I.real, h["U"], axes=1)
+        h["Brc"], h["Brs"], h["Bzc"], h["Bzs"] = fields.b_phasors(self.g, h["Ec"], h["Ess"], h["omega"])
 
     def _compose(self):
         """Eq. compose with I_k = I_c - i I_s, and the B phasors."""
@@ -303,6 +373,23 @@ class OracleCell:
         p_cap, W = circuit.cap_power_trapezoid(np.array(self.samples_V), np.array(self.samples_Q),
                                                cfg.freq)
         p_cap_ph = circuit.cap_power_phasor(x_app, N, icap)
+        # the retained harmonics: V_p^(m), I_cap^(m) = i m w Q^(m), and their
+        # port, copper and capacitive powers
+        hrec = []
+        for h in self.harm:
+            wm = h["omega"]
+            Ecp_m = h["helm"].solve(MU0 * wm * h["Js"])
+            Essp_m = h["helm"].solve(MU0 * wm * h["Jc"])
+            vp_m = -(fields.project(self.g, self.geo.gk, Ecp_m) +
+                     1j * fields.project(self.g, self.geo.gk, Essp_m))
+            qhat_m = h["Qc"] - 1j * h["Qs"]
+            icap_m = 1j * wm * qhat_m
+            xa = h["x"].copy()
+            p_port += circuit.port_power(xa, N)
+            p_cu += circuit.copper_power(xa, N, h["r_rf"])
+            p_cap_ph += circuit.cap_power_phasor(xa, N, icap_m)
+            hrec.append(dict(m=h["m"], vp=vp_m, icap=icap_m, qhat=qhat_m, x_applied=xa,
+                             Ecp=Ecp_m, Essp=Essp_m))
         vg_applied = self.vg_amp
         rec = dict(period=self.s // self.n_rf - 1, n_samples=self.n_samples, accepted=accepted,
                    vp=vp, icap=icap, qhat=qhat, x_applied=x_app, vg=vg_applied,
@@ -320,10 +407,22 @@ class OracleCell:
             rec['x_target'] = xt
             self.Ecp, self.Essp = Ecp, Essp
             self._compose()
+            for h, hr in zip(self.harm, hrec):
+                xt_m = circuit.solve_target(h["A"], 0.0, hr["icap"], hr["vp"])   # no source at m w
+                h["x"] = (1.0 - cfg.alpha) * h["x"] + cfg.alpha * xt_m
+                h["Ecp"], h["Essp"] = hr["Ecp"], hr["Essp"]
+                self._compose_h(h)
         rec['x_next'] = self.x.copy()
         rec['vg_next'] = self.vg_amp
         rec['r_kcl'], rec['r_kvl'] = circuit.residuals(self.x, self.zs, self.zturn, self.c_stray,
                                                        self.omega, self.vg, icap, vp)
+        for h, hr in zip(self.harm, hrec):
+            hr['x_next'] = h["x"].copy()
+            hr['r_kcl'], hr['r_kvl'] = circuit.residuals(h["x"], h["zs"], h["zturn"], self.c_stray, h["omega"],
+                                                         0.0, hr["icap"], hr["vp"],
+                                                         v_scale=float(np.max(np.abs(h["x"][1 + N:]))))
+            del hr['Ecp'], hr['Essp']
+        rec['harmonics'] = hrec
         self._reset_accumulators()
         # phi at the cycle boundary with the new turn potentials
         self.phi = self.solve_potential(self.Q_last + self.window_q, self.theta(self.s), self.chi_last)

@@ -60,9 +60,10 @@ def solve_target(A, vg, icap, vp):
     return np.linalg.solve(A, b)
 
 
-def residuals(x, zs, zturn, c_stray, omega, vg, icap, vp):
+def residuals(x, zs, zturn, c_stray, omega, vg, icap, vp, v_scale=None):
     """Eqs. kclres, kvlres, normalised by |I_f| and |V_g| (the scales the
-    paper uses for Test 3); returns (max KCL, max KVL)."""
+    paper uses for Test 3; v_scale replaces |V_g| where the source is zero,
+    as at a harmonic); returns (max KCL, max KVL)."""
     N = zturn.shape[0]
     If, I, V = x[0], x[1:1 + N], x[1 + N:]
     Iin = np.concatenate([[If], I[:-1]])
@@ -71,7 +72,7 @@ def residuals(x, zs, zturn, c_stray, omega, vg, icap, vp):
     rV = V - Vnext - zturn @ I - vp
     rV0 = vg - zs * If - V[0]
     si = max(abs(If), 1e-300)
-    sv = max(abs(vg), 1e-300)
+    sv = max(abs(vg) if v_scale is None else v_scale, 1e-300)
     return np.max(np.abs(rI)) / si, max(np.max(np.abs(rV)), abs(rV0)) / sv
 
 

@@ -86,6 +86,7 @@ class CellConfig:
     seed: int = 20260915
     plain_fp64: int = 0            # 1: the plain FP64 particle form (comparison baseline)
     implicit_es: int = 0           # 1: direct-implicit electrostatics (susceptibility chi in the Poisson solve)
+    n_harmonics: int = 1           # retained circuit harmonics m = 1..M (Sec. 4 extension); 1: fundamental only
     capacity_factor: float = 1.5
     sort_every_e: int = 8
     sort_every_i: int = 50
