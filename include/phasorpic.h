@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 #define PP_MAX_TURNS 8
+#define PP_MAX_HARM 4            /* retained circuit harmonics m = 1..PP_MAX_HARM */
 #define PP_NSPECIES 2            /* 0 = electrons, 1 = Ar+ */
 
 #define PP_OK 0
@@ -107,6 +108,15 @@ typedef struct pp_config {
                                         by the next step's pass with the field solved with the
                                         susceptibility chi of the predicted populations; 0: explicit
                                         leapfrog (chi = 0) */
+    int32_t n_harmonics;             /* retained circuit harmonics M (1..PP_MAX_HARM; 0 means 1): the
+                                        multiharmonic extension of Sec. 4.  Each m = 2..M has its own
+                                        Helmholtz operator, unit fields, Z_vac, skin resistance, source
+                                        impedance and network at m w; J and Q are projected on
+                                        cos m theta, sin m theta (Eq. fourier), I_cap^(m) = i m w Q^(m),
+                                        the network at m w has no source (the generator drives the
+                                        fundamental), and the turn potentials, E_theta and B of every
+                                        step are the sums over the harmonics.  The learned proposal
+                                        requires M = 1. */
 } pp_config;
 
 /* Completed-period record (Sec. 2.4 diagnostics; Eqs. vpind, icap, pport,
@@ -134,6 +144,17 @@ typedef struct pp_period_record {
        prediction for the next period was applied, whether a model is active */
     double ml_err, ml_tau;
     int32_t ml_used, ml_active;
+    /* retained harmonics m = 2..n_harm (row h = m - 2; zero when n_harm = 1):
+       applied and next states, V_p^(m), I_cap^(m) = i m w Q^(m), Q^(m), and
+       the KCL / KVL residuals of the network at m w (KVL over max |V^(m)|).
+       The powers above are sums over all retained harmonics. */
+    int32_t n_harm, pad1;
+    double xh_applied[PP_MAX_HARM - 1][2 * (2 * PP_MAX_TURNS + 1)];
+    double xh_next[PP_MAX_HARM - 1][2 * (2 * PP_MAX_TURNS + 1)];
+    double vph[PP_MAX_HARM - 1][2 * PP_MAX_TURNS];
+    double icaph[PP_MAX_HARM - 1][2 * PP_MAX_TURNS];
+    double qhath[PP_MAX_HARM - 1][2 * PP_MAX_TURNS];
+    double rh_kcl[PP_MAX_HARM - 1], rh_kvl[PP_MAX_HARM - 1];
 } pp_period_record;
 
 typedef struct pp_cell pp_cell;
@@ -373,6 +394,17 @@ int pp_set_circuit_state(pp_cell* cell, const double* x, double vg);
 
 /* pp_get_circuit_state -- reads x (2(2N+1) doubles) and vg; synchronises `stream`. */
 int pp_get_circuit_state(pp_cell* cell, double* x, double* vg, void* stream);
+
+/*
+ * pp_set_harmonic_state / pp_get_harmonic_state -- the applied circuit state
+ * of retained harmonic m (2 <= m <= n_harmonics; same layout as x: I_f, I_k,
+ * V_k peak phasors at m w, 2(2N+1) doubles) and the composed field of that
+ * harmonic (Eq. compose at m w).  set: host pointer, synchronous, re-composes
+ * the harmonic's E_theta and B; get synchronises `stream`.  PP_E_ARG for m out
+ * of range.
+ */
+int pp_set_harmonic_state(pp_cell* cell, int m, const double* x);
+int pp_get_harmonic_state(pp_cell* cell, int m, double* x, void* stream);
 
 /*
  * pp_get_turn_phasors -- the record of the most recently completed period

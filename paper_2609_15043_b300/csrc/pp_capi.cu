@@ -92,7 +92,7 @@ static void one_step(Cell* c, cudaStream_t st) {
     double th = theta(c, s), th1 = theta(c, s + 1);
     phase_mark(c, PH_OTHER, true, st);
     // also clears rho and jm and imposes the turn potentials of theta_{s+1}
-    launch_field_prep(c, std::cos(th), std::sin(th), std::cos(th1), std::sin(th1), st);
+    launch_field_prep(c, th, th1, st);
     phase_mark(c, PH_OTHER, false, st);
     phase_mark(c, PH_PUSH, true, st);
     if (c->fp64)
@@ -127,8 +127,7 @@ static void one_step(Cell* c, cudaStream_t st) {
     poisson_refine(c, std::cos(th1), std::sin(th1), st, false, nullptr, true);
     phase_mark(c, PH_POISSON, false, st);
     phase_mark(c, PH_OTHER, true, st);
-    double two_n = 2.0 / c->n_rf;
-    launch_sample_accumulate(c, std::cos(th1), std::sin(th1), two_n * std::cos(th), two_n * std::sin(th), st);
+    launch_sample_accumulate(c, th, th1, st);
     phase_mark(c, PH_OTHER, false, st);
     if (ss != st) {
         cudaEventRecord(c->ev_join, ss);
@@ -467,13 +466,25 @@ struct CkHeader {
     int64_t s;
 };
 static const uint32_t kCkMagic = 0x4b435050u;   // "PPCK"
-static const uint32_t kCkVersion = 1;
+static const uint32_t kCkVersion = 2;
 
 static std::vector<std::pair<double*, size_t>> ck_grids(Cell* c) {
     size_t n = (size_t)c->nnodes;
-    return {{c->d_phi, n},  {c->d_win, n},  {c->d_Ec, n},   {c->d_Ess, n},        {c->d_Ecp, n},
-            {c->d_Essp, n}, {c->d_Ecp_new, n}, {c->d_Essp_new, n}, {c->d_Br, 4 * n}, {c->d_Jc, n},
-            {c->d_Js, n},   {c->d_Jc_c, n}, {c->d_Js_c, n}};
+    std::vector<std::pair<double*, size_t>> g = {
+        {c->d_phi, n},  {c->d_win, n},  {c->d_Ec, n},   {c->d_Ess, n},        {c->d_Ecp, n},
+        {c->d_Essp, n}, {c->d_Ecp_new, n}, {c->d_Essp_new, n}, {c->d_Br, 4 * n}, {c->d_Jc, n},
+        {c->d_Js, n},   {c->d_Jc_c, n}, {c->d_Js_c, n}};
+    // the CG solve's previous potential (its initial-guess extrapolation)
+    if (c->use_pcg) g.push_back({c->d_phi_prev, n});
+    // the retained harmonics' fields and accumulators
+    if (c->nharm > 1) {
+        const size_t nh = (size_t)(c->nharm - 1);
+        g.push_back({c->d_Ech, 2 * nh * n});
+        g.push_back({c->d_Ecph, 4 * nh * n});
+        g.push_back({c->d_Bh, 4 * nh * n});
+        g.push_back({c->d_Jh, 4 * nh * n});
+    }
+    return g;
 }
 
 // member-wise (the struct has padding whose bytes are unspecified)
@@ -487,7 +498,8 @@ static bool cfg_equal(const pp_config& a, const pp_config& b) {
            PP_EQ(v_g) && PP_EQ(phase_g) && PP_EQ(power_control) && PP_EQ(p_target) && PP_EQ(gamma) &&
            PP_EQ(n_trend) && PP_EQ(eps_p) && PP_EQ(alpha_v) && PP_EQ(f_step) && PP_EQ(v_min) && PP_EQ(v_max) &&
            PP_EQ(alpha) && PP_EQ(weight) && PP_EQ(capacity) && PP_EQ(seed) && PP_EQ(sort_every) &&
-           PP_EQ(poisson_max_iter) && PP_EQ(poisson_tol) && PP_EQ(plain_fp64);
+           PP_EQ(poisson_max_iter) && PP_EQ(poisson_tol) && PP_EQ(plain_fp64) && PP_EQ(implicit_es) &&
+           PP_EQ(n_harmonics);
 #undef PP_EQ
 }
 
@@ -957,6 +969,36 @@ int pp_set_circuit_state(pp_cell* h, const double* x, double vg) {
     cudaMemcpy(&c->d_st->vg_amp, &vg, sizeof(double), cudaMemcpyHostToDevice);
     launch_compose(c, false, 0);
     return cuda_check(cudaDeviceSynchronize(), "pp_set_circuit_state");
+}
+
+int pp_set_harmonic_state(pp_cell* h, int m, const double* x) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !x || m < 2 || m > c->nharm) {
+        set_error("bad argument to pp_set_harmonic_state (2 <= m <= n_harmonics)");
+        return PP_E_ARG;
+    }
+    int NX = 2 * c->nturns + 1;
+    for (int q = 0; q < 2 * NX; ++q)
+        if (!std::isfinite(x[q])) {
+            set_error("non-finite circuit state");
+            return PP_E_NAN;
+        }
+    cudaDeviceSynchronize();
+    cudaMemcpy(c->d_st->xh[m - 2], x, sizeof(double) * 2 * NX, cudaMemcpyHostToDevice);
+    launch_compose(c, false, 0);
+    return cuda_check(cudaDeviceSynchronize(), "pp_set_harmonic_state");
+}
+
+int pp_get_harmonic_state(pp_cell* h, int m, double* x, void* stream) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !x || m < 2 || m > c->nharm) {
+        set_error("bad argument to pp_get_harmonic_state (2 <= m <= n_harmonics)");
+        return PP_E_ARG;
+    }
+    int rc = read_state(c, (cudaStream_t)stream);
+    if (rc) return rc;
+    memcpy(x, c->h_st->xh[m - 2], sizeof(double) * 2 * (2 * c->nturns + 1));
+    return PP_OK;
 }
 
 int pp_get_circuit_state(pp_cell* h, double* x, double* vg, void* stream) {

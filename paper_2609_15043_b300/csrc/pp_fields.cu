@@ -261,9 +261,11 @@ template void sep_solve<double>(const SepSolver<double>&, const double*, double*
 __device__ __forceinline__ double turn_target(const DevState* st, const double* ext, int k, int nt,
                                               double cs, double sn) {
     if (ext) return ext[k];
-    // Eq. dirichlet: phi_k = V_c cos + V_s sin with V = V_c - i V_s
+    // Eq. dirichlet: phi_k = V_c cos + V_s sin with V = V_c - i V_s, plus the
+    // retained harmonics
     double vr = st->x[2 * (1 + nt + k)], vi = st->x[2 * (1 + nt + k) + 1];
-    return vr * cs + (-vi) * sn;
+    const double v1 = vr * cs + (-vi) * sn;
+    return st->nharm > 1 ? v1 + harm_turn_sum(st, k, nt, cs, sn) : v1;
 }
 
 struct PoisArgs {
@@ -475,6 +477,13 @@ struct TurnSet {
     double cs, sn;
 };
 
+// the retained harmonics' composed fields at the step's phase
+struct HarmFields {
+    const double* Ech;      // (nh) x 2 x nodes: E_c, E_ss
+    const double* Bh;       // (nh) x 4 x nodes
+    HarmPhase ph;           // cos m theta, sin m theta
+};
+
 // Per plasma cell 5 x 4 values (Er, Ez, Etheta, Br, Bz at corners 00, 01, 10,
 // 11).  A block takes a tile of 8 x 32 cells: its 9 x 33 nodes are evaluated
 // once into shared memory, then every thread writes its cell's 20 values
@@ -498,7 +507,7 @@ __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi
                                                   const double* __restrict__ Ess, const double* __restrict__ B, T* F,
                                                   T* rho, T* jm, int* sched, int NR, int nr, int i_win, int nnodes,
                                                   double dz, double dr, double cs, double sn, int magnetic,
-                                                  TurnSet ts) {
+                                                  TurnSet ts, HarmFields hf) {
     __shared__ T s_v[(kFpRows + 1) * (kFpCols + 1)][5];
     const int ci0 = blockIdx.y * kFpRows, cj0 = blockIdx.x * kFpCols;
     const int t = threadIdx.x;
@@ -537,6 +546,17 @@ __global__ void __launch_bounds__(256) field_prep(const double* __restrict__ phi
         if (magnetic) {
             Br = __dadd_rn(__dmul_rn(B[n], cs), __dmul_rn(B[nnodes + n], sn));
             Bz = __dadd_rn(__dmul_rn(B[2 * nnodes + n], cs), __dmul_rn(B[3 * nnodes + n], sn));
+        }
+        // the retained harmonics, added in the order m = 2, 3, ...
+        for (int h = 0; h < hf.ph.nh; ++h) {
+            const double cm = hf.ph.c[h], sm = hf.ph.s[h];
+            const double* E2 = hf.Ech + (size_t)h * 2 * nnodes;
+            Et = __dadd_rn(Et, __dsub_rn(__dmul_rn(E2[n], cm), __dmul_rn(E2[nnodes + n], sm)));
+            if (magnetic) {
+                const double* B2 = hf.Bh + (size_t)h * 4 * nnodes;
+                Br = __dadd_rn(Br, __dadd_rn(__dmul_rn(B2[n], cm), __dmul_rn(B2[nnodes + n], sm)));
+                Bz = __dadd_rn(Bz, __dadd_rn(__dmul_rn(B2[2 * nnodes + n], cm), __dmul_rn(B2[3 * nnodes + n], sm)));
+            }
         }
         s_v[q][0] = (T)Er;
         s_v[q][1] = (T)Ez;
@@ -581,6 +601,12 @@ struct SampleArgs {
     int* done;                          // the step's Poisson solve: final convergence decision
     int sweep;
     double tol;
+    // retained harmonics: J harmonics (nh x 4 x nodes, with Kahan terms),
+    // (2/N) cos m theta_old, (2/N) sin m theta_old, and cos m theta_new,
+    // sin m theta_new of the charge sample
+    double* Jh;
+    int nnodes;
+    HarmPhase wh, qh;
 };
 
 template <typename T>
@@ -593,6 +619,11 @@ __global__ void sample_accumulate(SampleArgs a, const T* jm) {
             double J = (double)jm[n] / a.vol[n];
             kahan_add(a.Jc[n], a.Jcc[n], a.wc * J);
             kahan_add(a.Js[n], a.Jsc[n], a.ws * J);
+            for (int h = 0; h < a.wh.nh; ++h) {
+                double* J4 = a.Jh + (size_t)h * 4 * a.nnodes;
+                kahan_add(J4[n], J4[2 * a.nnodes + n], a.wh.c[h] * J);
+                kahan_add(J4[a.nnodes + n], J4[3 * a.nnodes + n], a.wh.s[h] * J);
+            }
         }
         return;
     }
@@ -619,6 +650,10 @@ __global__ void sample_accumulate(SampleArgs a, const T* jm) {
         double Q = q[k];
         kahan_add(st->qc[k], st->qc_c[k], a.two_over_n * Q * a.cs);
         kahan_add(st->qs[k], st->qs_c[k], a.two_over_n * Q * a.sn);
+        for (int h = 0; h < a.qh.nh; ++h) {
+            kahan_add(st->qch[h][k], st->qchc[h][k], a.two_over_n * Q * a.qh.c[h]);
+            kahan_add(st->qsh[h][k], st->qshc[h][k], a.two_over_n * Q * a.qh.s[h]);
+        }
         if (st->n_samples == 0) {
             st->v_first[k] = V;
             st->q_first[k] = Q;
@@ -655,23 +690,28 @@ __global__ void interior_to_nodes(const double* src, double* dst, int NZ, int NR
     dst[n] = v;
 }
 
-void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
-                         cudaStream_t st) {
-    int rows = c->hs.rows, M = c->hs.M;
+void helmholtz_solve_sep(Cell* c, const SepSolver<double>& hs, const double* rhs_nodes, double* out_nodes,
+                         double scale, cudaStream_t st) {
+    int rows = hs.rows, M = hs.M;
     int nint = rows * M;
     double* stage = c->d_hstage;
     nodes_to_interior<<<(nint + 255) / 256, 256, 0, st>>>(rhs_nodes, stage, c->NZ, c->NR, 1, M, scale,
                                                            nullptr);
-    sep_solve<double>(c->hs, stage, stage + nint, st, nullptr);
+    sep_solve<double>(hs, stage, stage + nint, st, nullptr);
     interior_to_nodes<<<(c->nnodes + 255) / 256, 256, 0, st>>>(stage + nint, out_nodes, c->NZ, c->NR, 1, M);
     count_launch(2);
+}
+
+void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
+                         cudaStream_t st) {
+    helmholtz_solve_sep(c, c->hs, rhs_nodes, out_nodes, scale, st);
 }
 
 // ---------------------------------------------------------------- compose and B
 // Eq. compose: E_c = E_c^(p) + sum I_s,k U_k, E_ss = E_ss^(p) + sum I_c,k U_k
 // with I_k = I_c - i I_s (so I_s = -Im I_k, I_c = Re I_k).
-__global__ void compose_kernel(const DevState* st, double* Ec, double* Ess, double* Ecp, double* Essp,
-                               const double* Ecp_new, const double* Essp_new, const double* U, int nn,
+__global__ void compose_kernel(const DevState* st, const double* x, double* Ec, double* Ess, double* Ecp,
+                               double* Essp, const double* Ecp_new, const double* Essp_new, const double* U, int nn,
                                int nt, int use_new) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
@@ -681,7 +721,7 @@ __global__ void compose_kernel(const DevState* st, double* Ec, double* Ess, doub
     }
     double ec = Ecp[n], es = Essp[n];
     for (int k = 0; k < nt; ++k) {
-        double ire = st->x[2 * (1 + k)], iim = st->x[2 * (1 + k) + 1];
+        double ire = x[2 * (1 + k)], iim = x[2 * (1 + k) + 1];
         double u = U[(size_t)k * nn + n];
         ec += (-iim) * u;
         es += ire * u;
@@ -718,16 +758,41 @@ __global__ void bphasor_kernel(const double* Ec, const double* Ess, double* B, i
 
 void launch_compose(Cell* c, bool from_new, cudaStream_t st) {
     int nn = c->nnodes;
-    compose_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_st, c->d_Ec, c->d_Ess, c->d_Ecp, c->d_Essp,
+    compose_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_st, c->d_st->x, c->d_Ec, c->d_Ess, c->d_Ecp, c->d_Essp,
                                                      c->d_Ecp_new, c->d_Essp_new, c->d_U, nn, c->nturns,
                                                      from_new ? 1 : 0);
     bphasor_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_Ec, c->d_Ess, c->d_Br, c->NZ, c->NR, c->dz, c->dr,
                                                      c->omega);
     count_launch(2);
+    // the retained harmonics (Eq. compose and Faraday's law at m w)
+    for (int h = 0; h + 1 < c->nharm; ++h) {
+        double* E2 = c->d_Ech + (size_t)h * 2 * nn;
+        double* P4 = c->d_Ecph + (size_t)h * 4 * nn;
+        compose_kernel<<<(nn + 255) / 256, 256, 0, st>>>(c->d_st, c->d_st->xh[h], E2, E2 + nn, P4, P4 + nn,
+                                                         P4 + 2 * nn, P4 + 3 * nn,
+                                                         c->d_Uh + (size_t)h * c->nturns * nn, nn, c->nturns,
+                                                         from_new ? 1 : 0);
+        bphasor_kernel<<<(nn + 255) / 256, 256, 0, st>>>(E2, E2 + nn, c->d_Bh + (size_t)h * 4 * nn, c->NZ, c->NR,
+                                                         c->dz, c->dr, (h + 2) * c->omega);
+        count_launch(2);
+    }
+}
+
+HarmPhase harm_phase(const Cell* c, double th) {
+    HarmPhase p;
+    p.nh = c->nharm - 1;
+    for (int h = 0; h < kMaxHarm - 1; ++h) {
+        p.c[h] = h < p.nh ? std::cos((h + 2) * th) : 0.0;
+        p.s[h] = h < p.nh ? std::sin((h + 2) * th) : 0.0;
+    }
+    return p;
 }
 
 // ---------------------------------------------------------------- launchers
-void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, double ws, cudaStream_t st) {
+void launch_sample_accumulate(Cell* c, double th_old, double th_new, cudaStream_t st) {
+    const double two_n = 2.0 / c->n_rf;
+    const double cs_new = std::cos(th_new), sn_new = std::sin(th_new);
+    const double wc = two_n * std::cos(th_old), ws = two_n * std::sin(th_old);
     SampleArgs a;
     a.st = c->d_st;
     a.phi = c->d_phi;
@@ -753,6 +818,14 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
     a.done = &c->d_st->pdone;
     a.sweep = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
     a.tol = c->cfg.poisson_tol;
+    a.Jh = c->d_Jh;
+    a.nnodes = c->nnodes;
+    a.wh = harm_phase(c, th_old);
+    for (int h = 0; h < a.wh.nh; ++h) {
+        a.wh.c[h] *= two_n;
+        a.wh.s[h] *= two_n;
+    }
+    a.qh = harm_phase(c, th_new);
     const unsigned nb = (unsigned)((a.nn + 255) / 256) + 1;     // + the sample block
     if (c->fp64)
         sample_accumulate<double><<<nb, 256, 0, st>>>(a, c->d_jm64);
@@ -761,17 +834,19 @@ void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, 
     count_launch();
 }
 
-void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_next, cudaStream_t st) {
+void launch_field_prep(Cell* c, double th, double th_next, cudaStream_t st) {
+    const double cs = std::cos(th), sn = std::sin(th), cs_next = std::cos(th_next), sn_next = std::sin(th_next);
     dim3 grid((c->nr + kFpCols - 1) / kFpCols, (c->i_win + kFpRows - 1) / kFpRows);
     TurnSet ts{c->d_phi, c->d_tn_node, c->d_tn_k, c->ntn, c->nturns, c->d_st, cs_next, sn_next};
+    HarmFields hf{c->d_Ech, c->d_Bh, harm_phase(c, th)};
     if (c->fp64)
         field_prep<double><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F64, c->d_rho64, c->d_jm64,
                                                  &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
-                                                 cs, sn, c->cfg.magnetic_force, ts);
+                                                 cs, sn, c->cfg.magnetic_force, ts, hf);
     else
         field_prep<float><<<grid, 256, 0, st>>>(c->d_phi, c->d_Ec, c->d_Ess, c->d_Br, c->d_F, c->d_rho, c->d_jm,
                                                 &c->d_st->push_chunk, c->NR, c->nr, c->i_win, c->nnodes, c->dz, c->dr,
-                                                cs, sn, c->cfg.magnetic_force, ts);
+                                                cs, sn, c->cfg.magnetic_force, ts, hf);
     count_launch();
 }
 

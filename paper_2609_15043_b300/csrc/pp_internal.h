@@ -87,6 +87,9 @@ struct PcgPlan {
     long long gvec_stride = 0;              // floats of one CTA's private global region (vectors not in shared memory)
 };
 
+constexpr int kMaxHarm = PP_MAX_HARM;             // retained circuit harmonics
+constexpr int kNX2 = 2 * (2 * PP_MAX_TURNS + 1);    // doubles of one circuit state
+
 struct DevState {
     double x[2 * (2 * PP_MAX_TURNS + 1)];    // applied circuit state
     double vg_amp;
@@ -122,6 +125,39 @@ struct DevState {
     int phi_prev_ok;                         // the previous step's potential is stored (CG initial guess)
     int piters;
     double prel;
+    // retained harmonics m = 2..nharm (row h = m - 2): applied states, turn
+    // charge harmonics with Kahan terms, the period's loads and powers
+    int nharm;
+    double xh[kMaxHarm - 1][kNX2];
+    double qch[kMaxHarm - 1][PP_MAX_TURNS], qsh[kMaxHarm - 1][PP_MAX_TURNS];
+    double qchc[kMaxHarm - 1][PP_MAX_TURNS], qshc[kMaxHarm - 1][PP_MAX_TURNS];
+    double hvp[kMaxHarm - 1][2 * PP_MAX_TURNS], hicap[kMaxHarm - 1][2 * PP_MAX_TURNS];
+    double hp_port, hp_cu, hp_capph;         // the harmonics' port, copper and phasor-capacitive powers
+};
+
+// The retained harmonics' part of turn k's potential at phase theta (Eq.
+// dirichlet at m w, summed over m = 2..nharm): V^(m) = V_c - i V_s gives
+// V_c cos m theta + V_s sin m theta, with cos m theta, sin m theta from the
+// fundamental's by the Chebyshev recurrence.
+__device__ __forceinline__ double harm_turn_sum(const DevState* st, int k, int nt, double cs, double sn) {
+    double v = 0.0;
+    double c1 = cs, s1 = sn, c0 = 1.0, s0 = 0.0;
+    for (int m = 2; m <= st->nharm; ++m) {
+        const double c2 = 2.0 * cs * c1 - c0, s2 = 2.0 * cs * s1 - s0;
+        const double* xh = st->xh[m - 2];
+        v += xh[2 * (1 + nt + k)] * c2 + (-xh[2 * (1 + nt + k) + 1]) * s2;
+        c0 = c1;
+        s0 = s1;
+        c1 = c2;
+        s1 = s2;
+    }
+    return v;
+}
+
+// phase factors cos m theta, sin m theta of the retained harmonics (host)
+struct HarmPhase {
+    int nh;                                  // harmonics m = 2..nh + 1
+    double c[kMaxHarm - 1], s[kMaxHarm - 1];
 };
 
 // FP32 or FP64 separable solver: radial generalised eigenbasis x tridiagonal in z
@@ -254,6 +290,20 @@ struct Cell {
     DevState* h_st = nullptr;               // pinned host mirror for reads
 
     // circuit constants (device)
+    // retained harmonics m = 2..nharm (index h = m - 2): Helmholtz solvers at
+    // m w, unit fields, composed and plasma-only fields, B phasors, J
+    // harmonics with Kahan terms, and the network constants at m w
+    int nharm = 1;
+    SepSolver<double> hsh[kMaxHarm - 1];
+    double* d_Uh = nullptr;                 // (nharm-1) x N x nodes
+    double* d_Ech = nullptr;                // (nharm-1) x 2 x nodes: E_c, E_ss
+    double* d_Ecph = nullptr;               // (nharm-1) x 4 x nodes: E_c^p, E_ss^p, and the period's new ones
+    double* d_Bh = nullptr;                 // (nharm-1) x 4 x nodes
+    double* d_Jh = nullptr;                 // (nharm-1) x 4 x nodes: J_c, J_s, their Kahan terms
+    double* d_Ainvh = nullptr;              // (nharm-1) x (2N+1)^2 complex
+    double* d_zturnh = nullptr;             // (nharm-1) x N^2 complex
+    double* d_circh = nullptr;              // (nharm-1) x (2 + 2N): zs, r_rf, c_stray at m w
+    std::vector<double> zvach;              // host copies of Z_vac(m w), (nharm-1) x N^2 complex
     double* d_Ainv = nullptr;               // (2N+1)^2 complex inverse of the network matrix
     double* d_zturn = nullptr;              // N^2 complex
     double* d_circ = nullptr;               // misc: zs(2), r_rf[N], c_stray[N]
@@ -324,7 +374,8 @@ int vacuum_capacitance(const pp_vacuum_problem* p, double eps_r, const double* s
                        double* C, double* phis);
 
 // ---------------------------------------------------------------- launchers
-void launch_field_prep(Cell* c, double cs, double sn, double cs_next, double sn_next, cudaStream_t st);
+void launch_field_prep(Cell* c, double th, double th_next, cudaStream_t st);
+HarmPhase harm_phase(const Cell* c, double th);
 void launch_push(Cell* c, cudaStream_t st);
 void launch_push_plain(Cell* c, cudaStream_t st);
 void push_prepare(Cell* c);
@@ -337,10 +388,12 @@ void launch_deposit_only(Cell* c, cudaStream_t st);
 int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external_targets,
                    const double* d_targets, bool in_step = false);
 void poisson_fast_solve(Cell* c, const float* rhs, float* out, cudaStream_t st);
-void launch_sample_accumulate(Cell* c, double cs_new, double sn_new, double wc, double ws, cudaStream_t st);
+void launch_sample_accumulate(Cell* c, double th_old, double th_new, cudaStream_t st);
 void period_end(Cell* c, cudaStream_t st);
 template <typename T>
 void sep_solve(const SepSolver<T>& s, const T* rhs, T* out, cudaStream_t st, const int* skip);
+void helmholtz_solve_sep(Cell* c, const SepSolver<double>& hs, const double* rhs_nodes, double* out_nodes,
+                         double scale, cudaStream_t st);
 void helmholtz_solve_dev(Cell* c, const double* rhs_nodes, double* out_nodes, double scale,
                          cudaStream_t st);
 void launch_compose(Cell* c, bool from_new, cudaStream_t st);

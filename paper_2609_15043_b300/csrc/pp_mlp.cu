@@ -441,6 +441,10 @@ int pp_ml_configure(pp_cell* h, const pp_mlp* m, double alpha_ml, int collect) {
         set_error("bad argument to pp_ml_configure (alpha_ml in (0, 1])");
         return PP_E_ARG;
     }
+    if (c->nharm > 1) {
+        set_error("pp_ml_configure: the proposal predicts the fundamental's loads; the cell retains harmonics");
+        return PP_E_CONFIG;
+    }
     return ml_configure(c, m, alpha_ml, collect);
 }
 

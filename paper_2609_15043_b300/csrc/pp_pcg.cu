@@ -97,9 +97,11 @@ struct PcgArgs {
 __device__ __forceinline__ double tgt_of(const DevState* st, const double* ext, int k, int nt, double cs,
                                          double sn) {
     if (ext) return ext[k];
-    // Eq. dirichlet: phi_k = V_c cos + V_s sin with V = V_c - i V_s
+    // Eq. dirichlet: phi_k = V_c cos + V_s sin with V = V_c - i V_s, plus the
+    // retained harmonics
     double vr = st->x[2 * (1 + nt + k)], vi = st->x[2 * (1 + nt + k) + 1];
-    return vr * cs + (-vi) * sn;
+    const double v1 = vr * cs + (-vi) * sn;
+    return st->nharm > 1 ? v1 + harm_turn_sum(st, k, nt, cs, sn) : v1;
 }
 
 // chi = (q_e/m_e rho_e + q_i/m_i rho_i) dt^2 / (eps0 V eps_r) (weights from set-up)

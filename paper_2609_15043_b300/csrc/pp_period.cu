@@ -83,6 +83,13 @@ __global__ void period_circuit(PeriodArgs a) {
         wsum += st->w[k] + 0.5 * (st->v_first[k] + st->v_prev[k]) * (st->q_first[k] - st->q_prev[k]);
     double p_cap = a.freq * wsum;
     double p_ind = st->p_ind, p_es = st->p_es;
+    // the retained harmonics' port, copper and phasor-capacitive powers
+    // (harmonic_loads ran first); P_ind and P_cap are time-domain sums
+    if (st->nharm > 1) {
+        p_port += st->hp_port;
+        p_cu += st->hp_cu;
+        p_cap_ph += st->hp_capph;
+    }
     pp_period_record& rec = st->rec;
     rec.period = st->period;
     rec.n_samples = st->n_samples;
@@ -249,6 +256,159 @@ __global__ void period_circuit(PeriodArgs a) {
     for (int q = 0; q < C_NCOUNT; ++q) st->per[q] = 0;
 }
 
+// ---------------------------------------------------------------- retained harmonics
+struct HarmArgs {
+    DevState* st;
+    int nh, N, NR, ntn, nnodes;
+    const int* tn_node;
+    const int* tn_k;
+    const double* gk_val;
+    double dr, dz, omega, alpha;
+    const double* Ecph;       // nh x 4 x nodes: (E_c^p, E_ss^p, new E_c^p, new E_ss^p)
+    const double* Ainvh;      // nh x (2N+1)^2 complex
+    const double* zturnh;     // nh x N^2 complex
+    const double* circh;      // nh x (2 + 2N)
+};
+
+// Loads of the completed period at every retained harmonic m w (Eq. vpind on
+// the plasma-only field at m w, I_cap^(m) = i m w Q^(m)) and the powers of
+// the applied harmonic states; one thread.  Runs before period_circuit,
+// which adds the powers to the fundamental's.
+__global__ void harmonic_loads(HarmArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    DevState* st = a.st;
+    const int N = a.N, NX = 2 * N + 1;
+    const double two_pi = 6.283185307179586;
+    pp_period_record& rec = st->rec;
+    double pp = 0, pc = 0, pcap = 0;
+    for (int h = 0; h < a.nh; ++h) {
+        const double wm = (h + 2) * a.omega;
+        const double* Ecp = a.Ecph + ((size_t)h * 4 + 2) * a.nnodes;
+        const double* Essp = a.Ecph + ((size_t)h * 4 + 3) * a.nnodes;
+        Cx vp[PP_MAX_TURNS], icap[PP_MAX_TURNS];
+        for (int k = 0; k < N; ++k) vp[k] = Cx{0, 0};
+        for (int t = 0; t < a.ntn; ++t) {
+            int n = a.tn_node[t], k = a.tn_k[t];
+            double R = (n % a.NR) * a.dr;
+            double w = a.gk_val[t] * two_pi * R * a.dz * a.dr;
+            vp[k].r -= w * Ecp[n];
+            vp[k].i -= w * Essp[n];
+        }
+        for (int k = 0; k < N; ++k) {
+            icap[k] = Cx{wm * st->qsh[h][k], wm * st->qch[h][k]};
+            st->hvp[h][2 * k] = vp[k].r;
+            st->hvp[h][2 * k + 1] = vp[k].i;
+            st->hicap[h][2 * k] = icap[k].r;
+            st->hicap[h][2 * k + 1] = icap[k].i;
+            rec.vph[h][2 * k] = vp[k].r;
+            rec.vph[h][2 * k + 1] = vp[k].i;
+            rec.icaph[h][2 * k] = icap[k].r;
+            rec.icaph[h][2 * k + 1] = icap[k].i;
+            rec.qhath[h][2 * k] = st->qch[h][k];
+            rec.qhath[h][2 * k + 1] = -st->qsh[h][k];
+        }
+        const double* x = st->xh[h];
+        const double* rrf = a.circh + (size_t)h * (2 + 2 * N) + 2;
+        pp += 0.5 * (x[2 * (1 + N)] * x[0] + x[2 * (1 + N) + 1] * x[1]);
+        for (int k = 0; k < N; ++k) {
+            pc += 0.5 * rrf[k] * (x[2 * (1 + k)] * x[2 * (1 + k)] + x[2 * (1 + k) + 1] * x[2 * (1 + k) + 1]);
+            pcap += 0.5 * (x[2 * (1 + N + k)] * icap[k].r + x[2 * (1 + N + k) + 1] * icap[k].i);
+        }
+        for (int q = 0; q < 2 * NX; ++q) rec.xh_applied[h][q] = x[q];
+    }
+    st->hp_port = pp;
+    st->hp_cu = pc;
+    st->hp_capph = pcap;
+    rec.n_harm = a.nh + 1;
+}
+
+// After period_circuit: with an accepted period, each harmonic network at m w
+// (no source) is solved for the period's loads and relaxed (Eqs. target,
+// relaxation); its KCL / KVL residuals go to the record; the harmonic charge
+// accumulators are reset.  One thread.
+__global__ void harmonic_relax(HarmArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    DevState* st = a.st;
+    const int N = a.N, NX = 2 * N + 1;
+    pp_period_record& rec = st->rec;
+    for (int h = 0; h < a.nh; ++h) {
+        const double wm = (h + 2) * a.omega;
+        const double* Ainv = a.Ainvh + (size_t)h * 2 * NX * NX;
+        const double* zturn = a.zturnh + (size_t)h * 2 * N * N;
+        const double* circ = a.circh + (size_t)h * (2 + 2 * N);
+        Cx x[2 * PP_MAX_TURNS + 1], vp[PP_MAX_TURNS], icap[PP_MAX_TURNS];
+        for (int q = 0; q < NX; ++q) x[q] = Cx{st->xh[h][2 * q], st->xh[h][2 * q + 1]};
+        for (int k = 0; k < N; ++k) {
+            vp[k] = Cx{st->hvp[h][2 * k], st->hvp[h][2 * k + 1]};
+            icap[k] = Cx{st->hicap[h][2 * k], st->hicap[h][2 * k + 1]};
+        }
+        if (st->accepted) {
+            Cx b[2 * PP_MAX_TURNS + 1];
+            b[0] = Cx{0, 0};
+            for (int k = 0; k < N; ++k) {
+                b[1 + k] = icap[k];
+                b[1 + N + k] = vp[k];
+            }
+            for (int r = 0; r < NX; ++r) {
+                Cx s = Cx{0, 0};
+                for (int q = 0; q < NX; ++q)
+                    s = cadd(s, cmul(Cx{Ainv[2 * (r * NX + q)], Ainv[2 * (r * NX + q) + 1]}, b[q]));
+                x[r] = cadd(cscale(x[r], 1.0 - a.alpha), cscale(s, a.alpha));
+            }
+            for (int q = 0; q < NX; ++q) {
+                st->xh[h][2 * q] = x[q].r;
+                st->xh[h][2 * q + 1] = x[q].i;
+            }
+        }
+        // residuals (KCL over |I_f|, KVL over max |V|)
+        double si = sqrt(cabs2(x[0])), sv = 0;
+        for (int k = 0; k < N; ++k) sv = fmax(sv, sqrt(cabs2(x[1 + N + k])));
+        si = si > 1e-300 ? si : 1e-300;
+        sv = sv > 1e-300 ? sv : 1e-300;
+        double rkcl = 0, rkvl = 0;
+        for (int k = 0; k < N; ++k) {
+            Cx iin = (k == 0) ? x[0] : x[k];
+            Cx r = csub(csub(iin, x[1 + k]), icap[k]);
+            r = csub(r, cmul(Cx{0, wm * circ[2 + N + k]}, x[1 + N + k]));
+            rkcl = fmax(rkcl, sqrt(cabs2(r)) / si);
+            Cx vnext = (k + 1 < N) ? x[1 + N + k + 1] : Cx{0, 0};
+            Cx rv = csub(x[1 + N + k], vnext);
+            for (int l = 0; l < N; ++l)
+                rv = csub(rv, cmul(Cx{zturn[2 * (k * N + l)], zturn[2 * (k * N + l) + 1]}, x[1 + l]));
+            rv = csub(rv, vp[k]);
+            rkvl = fmax(rkvl, sqrt(cabs2(rv)) / sv);
+        }
+        Cx r0 = csub(csub(Cx{0, 0}, cmul(Cx{circ[0], circ[1]}, x[0])), x[1 + N]);
+        rkvl = fmax(rkvl, sqrt(cabs2(r0)) / sv);
+        rec.rh_kcl[h] = rkcl;
+        rec.rh_kvl[h] = rkvl;
+        for (int q = 0; q < 2 * NX; ++q) rec.xh_next[h][q] = st->xh[h][q];
+        for (int k = 0; k < PP_MAX_TURNS; ++k) st->qch[h][k] = st->qsh[h][k] = st->qchc[h][k] = st->qshc[h][k] = 0;
+    }
+}
+
+static HarmArgs harm_args(Cell* c) {
+    HarmArgs a;
+    a.st = c->d_st;
+    a.nh = c->nharm - 1;
+    a.N = c->nturns;
+    a.NR = c->NR;
+    a.ntn = c->ntn;
+    a.nnodes = c->nnodes;
+    a.tn_node = c->d_tn_node;
+    a.tn_k = c->d_tn_k;
+    a.gk_val = c->d_gk_val;
+    a.dr = c->dr;
+    a.dz = c->dz;
+    a.omega = c->omega;
+    a.alpha = c->cfg.alpha;
+    a.Ecph = c->d_Ecph;
+    a.Ainvh = c->d_Ainvh;
+    a.zturnh = c->d_zturnh;
+    a.circh = c->d_circh;
+    return a;
+}
+
 void period_end(Cell* c, cudaStream_t st) {
     double scale = kMu0 * c->omega;
     // features of the completed period (electrons and current harmonics as
@@ -258,6 +418,19 @@ void period_end(Cell* c, cudaStream_t st) {
     // Eq. helmholtz_two_real: L E_c^p = mu0 w J_s, L E_ss^p = mu0 w J_c
     helmholtz_solve_dev(c, c->d_Js, c->d_Ecp_new, scale, st);
     helmholtz_solve_dev(c, c->d_Jc, c->d_Essp_new, scale, st);
+    // the same at every retained harmonic m w, then its loads and powers
+    const size_t nn = (size_t)c->nnodes;
+    for (int h = 0; h + 1 < c->nharm; ++h) {
+        const double* J4 = c->d_Jh + (size_t)h * 4 * nn;
+        double* P4 = c->d_Ecph + (size_t)h * 4 * nn;
+        const double sm = kMu0 * (h + 2) * c->omega;
+        helmholtz_solve_sep(c, c->hsh[h], J4 + nn, P4 + 2 * nn, sm, st);
+        helmholtz_solve_sep(c, c->hsh[h], J4, P4 + 3 * nn, sm, st);
+    }
+    if (c->nharm > 1) {
+        harmonic_loads<<<1, 32, 0, st>>>(harm_args(c));
+        count_launch();
+    }
     PeriodArgs a;
     a.st = c->d_st;
     a.Ecp = c->d_Ecp_new;
@@ -293,12 +466,17 @@ void period_end(Cell* c, cudaStream_t st) {
     a.ml_pred = c->d_ml_pred;
     period_circuit<<<1, 32, 0, st>>>(a);
     count_launch();
+    if (c->nharm > 1) {
+        harmonic_relax<<<1, 32, 0, st>>>(harm_args(c));
+        count_launch();
+    }
     launch_compose(c, true, st);
     size_t nb = sizeof(double) * c->nnodes;
     cudaMemsetAsync(c->d_Jc, 0, nb, st);
     cudaMemsetAsync(c->d_Js, 0, nb, st);
     cudaMemsetAsync(c->d_Jc_c, 0, nb, st);
     cudaMemsetAsync(c->d_Js_c, 0, nb, st);
+    if (c->nharm > 1) cudaMemsetAsync(c->d_Jh, 0, nb * 4 * (c->nharm - 1), st);
 }
 
 }  // namespace pp

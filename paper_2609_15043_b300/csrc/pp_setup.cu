@@ -209,7 +209,7 @@ static int on_grid(double x, double h, int* k) {
 // the outer boundaries): the radial generalised eigenbasis T v = mu D v
 // (D = R) and per-mode Thomas factors in z; k2base = mu0 eps0 w^2 (0: MQS)
 // times the node-row average of eps_row.
-static void build_helmholtz(Cell* c, double k2base) {
+static void build_helmholtz_into(Cell* c, SepSolver<double>& s, double k2base) {
     const int NR = c->NR, rows = c->NZ - 2, MH = NR - 2;
     const double dr = c->dr, dz = c->dz;
     std::vector<double> T((size_t)MH * MH, 0.0), D(MH);
@@ -238,7 +238,6 @@ static void build_helmholtz(Cell* c, double k2base) {
         for (int m = 0; m < MH; ++m) diag[(size_t)ii * MH + m] = -2.0 / (dz * dz) + mu[m] + k2base * epsn;
     }
     thomas_factors(lo, up, diag, rows, MH, cp, invd);
-    SepSolver<double>& s = c->hs;
     s.rows = rows;
     s.M = MH;
     s.Vf = upload<double>(c, Vf);
@@ -248,7 +247,72 @@ static void build_helmholtz(Cell* c, double k2base) {
     s.lo = upload<double>(c, lo);
     s.t0 = c->alloc<double>((size_t)rows * MH);
     s.t1 = c->alloc<double>((size_t)rows * MH);
-    c->d_hstage = c->alloc<double>((size_t)2 * rows * MH);
+}
+
+static void build_helmholtz(Cell* c, double k2base) {
+    build_helmholtz_into(c, c->hs, k2base);
+    c->d_hstage = c->alloc<double>((size_t)2 * (c->NZ - 2) * (c->NR - 2));
+}
+
+// Network constants at angular frequency w (Eqs. skin, zsource, blockmatrix):
+// R_rf per turn, Z_source, Z_turn = Z_vac + diag(R_rf), the inverse of the
+// (2N+1) network matrix, and the circ vector (zs, r_rf, c_stray).  false when
+// the matrix is singular.
+static bool network_constants(const Cell* c, double w, const std::vector<double>& zvac, std::vector<double>& r_rf,
+                              std::vector<std::complex<double>>& Ainv, std::vector<double>& ainv,
+                              std::vector<double>& ztv, std::vector<double>& circ) {
+    const pp_config& f = c->cfg;
+    const int N = c->nturns, NX = 2 * N + 1;
+    r_rf.assign(N, 0.0);
+    if (f.r_rf_override >= 0) {
+        for (int k = 0; k < N; ++k) r_rf[k] = f.r_rf_override;
+    } else {
+        double rho = f.rho20 * (1.0 + f.alpha_cu * (f.t_coil_c - 20.0));
+        double delta = std::sqrt(2.0 * rho / (w * kMu0));
+        double inner = std::max(f.wire_radius - delta, 0.0);
+        for (int k = 0; k < N; ++k)
+            r_rf[k] = rho * 2 * kPi * f.turn_r[k] / (kPi * (f.wire_radius * f.wire_radius - inner * inner));
+    }
+    double xs = w * f.l_m;
+    if (f.c_m > 0) xs -= 1.0 / (w * f.c_m);
+    cd zs(f.r_g + f.r_m, xs);
+    std::vector<cd> A((size_t)NX * NX, cd(0, 0));
+    std::vector<cd> zt((size_t)N * N);
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l < N; ++l)
+            zt[(size_t)k * N + l] = cd(zvac[2 * (k * N + l)], zvac[2 * (k * N + l) + 1]) + (k == l ? r_rf[k] : 0.0);
+    A[0] = zs;
+    A[1 + N] = 1.0;
+    for (int k = 0; k < N; ++k) {
+        int r = 1 + k;
+        A[(size_t)r * NX + (k == 0 ? 0 : k)] = 1.0;          // I_in,k
+        A[(size_t)r * NX + 1 + k] = -1.0;
+        A[(size_t)r * NX + 1 + N + k] = cd(0, -w * f.c_stray[k]);
+        int r2 = 1 + N + k;
+        for (int l = 0; l < N; ++l) A[(size_t)r2 * NX + 1 + l] = -zt[(size_t)k * N + l];
+        A[(size_t)r2 * NX + 1 + N + k] = 1.0;
+        if (k + 1 < N) A[(size_t)r2 * NX + 1 + N + k + 1] = -1.0;
+    }
+    Ainv = A;
+    if (!invert(Ainv, NX)) return false;
+    ainv.assign(2 * NX * NX, 0.0);
+    ztv.assign(2 * N * N, 0.0);
+    circ.assign(2 + 2 * N, 0.0);
+    for (int q = 0; q < NX * NX; ++q) {
+        ainv[2 * q] = Ainv[q].real();
+        ainv[2 * q + 1] = Ainv[q].imag();
+    }
+    for (int q = 0; q < N * N; ++q) {
+        ztv[2 * q] = zt[q].real();
+        ztv[2 * q + 1] = zt[q].imag();
+    }
+    circ[0] = zs.real();
+    circ[1] = zs.imag();
+    for (int k = 0; k < N; ++k) {
+        circ[2 + k] = r_rf[k];
+        circ[2 + N + k] = f.c_stray[k];
+    }
+    return true;
 }
 
 static int fail(const char* msg) {
@@ -266,6 +330,7 @@ int setup_cell(Cell* c) {
     if (f.freq <= 0 || f.dt <= 0) return fail("freq and dt must be positive");
     if (f.plain_fp64 != 0 && f.plain_fp64 != 1) return fail("plain_fp64 must be 0 or 1");
     if (f.implicit_es != 0 && f.implicit_es != 1) return fail("implicit_es must be 0 or 1");
+    if (f.n_harmonics < 0 || f.n_harmonics > PP_MAX_HARM) return fail("n_harmonics must be in 1..PP_MAX_HARM");
     c->implicit = f.implicit_es == 1;
     c->nr = f.nr;
     c->nz = f.nz;
@@ -655,57 +720,64 @@ int setup_cell(Cell* c) {
     c->eps_rec = zmax > 0 ? dmax / zmax : 0.0;
 
     // ---- R_rf (Eq. skin), Z_source (Eq. zsource), network (Eq. blockmatrix)
-    c->r_rf.assign(N, 0.0);
-    if (f.r_rf_override >= 0) {
-        for (int k = 0; k < N; ++k) c->r_rf[k] = f.r_rf_override;
-    } else {
-        double rho = f.rho20 * (1.0 + f.alpha_cu * (f.t_coil_c - 20.0));
-        double delta = std::sqrt(2.0 * rho / (c->omega * kMu0));
-        double inner = std::max(f.wire_radius - delta, 0.0);
-        for (int k = 0; k < N; ++k)
-            c->r_rf[k] = rho * 2 * kPi * f.turn_r[k] / (kPi * (f.wire_radius * f.wire_radius - inner * inner));
-    }
-    double xs = c->omega * f.l_m;
-    if (f.c_m > 0) xs -= 1.0 / (c->omega * f.c_m);
-    cd zs(f.r_g + f.r_m, xs);
     const int NX = 2 * N + 1;
-    std::vector<cd> A((size_t)NX * NX, cd(0, 0));
-    std::vector<cd> zt((size_t)N * N);
-    for (int k = 0; k < N; ++k)
-        for (int l = 0; l < N; ++l)
-            zt[(size_t)k * N + l] = cd(c->zvac[2 * (k * N + l)], c->zvac[2 * (k * N + l) + 1]) + (k == l ? c->r_rf[k] : 0.0);
-    A[0] = zs;
-    A[1 + N] = 1.0;
-    for (int k = 0; k < N; ++k) {
-        int r = 1 + k;
-        A[(size_t)r * NX + (k == 0 ? 0 : k)] = 1.0;          // I_in,k
-        A[(size_t)r * NX + 1 + k] = -1.0;
-        A[(size_t)r * NX + 1 + N + k] = cd(0, -c->omega * f.c_stray[k]);
-        int r2 = 1 + N + k;
-        for (int l = 0; l < N; ++l) A[(size_t)r2 * NX + 1 + l] = -zt[(size_t)k * N + l];
-        A[(size_t)r2 * NX + 1 + N + k] = 1.0;
-        if (k + 1 < N) A[(size_t)r2 * NX + 1 + N + k + 1] = -1.0;
-    }
-    std::vector<cd> Ainv = A;
-    if (!invert(Ainv, NX)) return fail("network matrix is singular");
-    std::vector<double> ainv(2 * NX * NX), ztv(2 * N * N), circ(2 + 2 * N);
-    for (int q = 0; q < NX * NX; ++q) {
-        ainv[2 * q] = Ainv[q].real();
-        ainv[2 * q + 1] = Ainv[q].imag();
-    }
-    for (int q = 0; q < N * N; ++q) {
-        ztv[2 * q] = zt[q].real();
-        ztv[2 * q + 1] = zt[q].imag();
-    }
-    circ[0] = zs.real();
-    circ[1] = zs.imag();
-    for (int k = 0; k < N; ++k) {
-        circ[2 + k] = c->r_rf[k];
-        circ[2 + N + k] = f.c_stray[k];
-    }
+    std::vector<cd> Ainv;
+    std::vector<double> ainv, ztv, circ;
+    if (!network_constants(c, c->omega, c->zvac, c->r_rf, Ainv, ainv, ztv, circ))
+        return fail("network matrix is singular");
     c->d_Ainv = upload<double>(c, ainv);
     c->d_zturn = upload<double>(c, ztv);
     c->d_circ = upload<double>(c, circ);
+
+    // ---- retained harmonics m = 2..M (the multiharmonic extension of
+    // Sec. 4): Helmholtz operator (k^2 m^2), unit fields, Z_vac and network at
+    // m w, field and accumulator storage; the harmonic states start at zero
+    // (no source at m w)
+    c->nharm = f.n_harmonics < 1 ? 1 : f.n_harmonics;
+    if (c->nharm > 1) {
+        const int nh = c->nharm - 1;
+        const size_t nn = (size_t)c->nnodes;
+        c->d_Uh = c->alloc<double>((size_t)nh * N * nn);
+        c->d_Ech = c->alloc<double>((size_t)nh * 2 * nn);
+        c->d_Ecph = c->alloc<double>((size_t)nh * 4 * nn);
+        c->d_Bh = c->alloc<double>((size_t)nh * 4 * nn);
+        c->d_Jh = c->alloc<double>((size_t)nh * 4 * nn);
+        std::vector<double> ainvh, zth, circh;
+        c->zvach.assign((size_t)nh * 2 * N * N, 0.0);
+        std::vector<double> Uhh((size_t)N * nn);
+        for (int h = 0; h < nh; ++h) {
+            const int m = h + 2;
+            const double wm = m * c->omega;
+            build_helmholtz_into(c, c->hsh[h], f.full_helmholtz ? kMu0 * kEps0 * wm * wm : 0.0);
+            double* Uh = c->d_Uh + (size_t)h * N * nn;
+            for (int k = 0; k < N; ++k) {
+                std::fill(gk.begin(), gk.end(), 0.0);
+                double gv = f.winding[k] / (c->turn_nodes[k].size() * dz * dr);
+                for (int n : c->turn_nodes[k]) gk[n] = gv;
+                cudaMemcpy(d_g, gk.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+                helmholtz_solve_sep(c, c->hsh[h], d_g, Uh + (size_t)k * nn, kMu0 * wm, 0);
+            }
+            cudaMemcpy(Uhh.data(), Uh, sizeof(double) * N * nn, cudaMemcpyDeviceToHost);
+            std::vector<double> zv(2 * N * N, 0.0);
+            for (int k = 0; k < N; ++k)
+                for (int l = 0; l < N; ++l) {
+                    double sum = 0;
+                    double gv = f.winding[k] / (c->turn_nodes[k].size() * dz * dr);
+                    for (int n : c->turn_nodes[k]) sum += gv * Uhh[(size_t)l * nn + n] * 2 * kPi * ((n % NR) * dr) * dz * dr;
+                    zv[2 * (k * N + l) + 1] = -sum;
+                }
+            std::copy(zv.begin(), zv.end(), c->zvach.begin() + (size_t)h * 2 * N * N);
+            std::vector<cd> Ah;
+            std::vector<double> rr, ai, zt, ci;
+            if (!network_constants(c, wm, zv, rr, Ah, ai, zt, ci)) return fail("harmonic network matrix is singular");
+            ainvh.insert(ainvh.end(), ai.begin(), ai.end());
+            zth.insert(zth.end(), zt.begin(), zt.end());
+            circh.insert(circh.end(), ci.begin(), ci.end());
+        }
+        c->d_Ainvh = upload<double>(c, ainvh);
+        c->d_zturnh = upload<double>(c, zth);
+        c->d_circh = upload<double>(c, circh);
+    }
 
     // ---- x^1: zero-load network solution
     cd vg(f.v_g * std::cos(f.phase_g), f.v_g * std::sin(f.phase_g));
@@ -716,6 +788,7 @@ int setup_cell(Cell* c) {
         h->x[2 * q + 1] = x.imag();
     }
     h->vg_amp = f.v_g;
+    h->nharm = c->nharm;
     cudaMemcpy(c->d_st, h, sizeof(DevState), cudaMemcpyHostToDevice);
     launch_compose(c, false, 0);
 

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PHASORPIC_LIB") or os.path.join(_HERE, "libphasorpic.so")
 
 MAX_TURNS = 8
+MAX_HARM = 4
 NSPECIES = 2
 
 PP_OK = 0
@@ -40,7 +41,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_mlp_forward", "pp_ml_configure", "pp_get_ml_features", "pp_ml_features_now",
            "pp_trainer_create", "pp_trainer_load", "pp_trainer_gradients", "pp_trainer_epoch",
            "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy",
-           "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune"]
+           "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune", "pp_set_harmonic_state",
+           "pp_get_harmonic_state"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -73,6 +75,7 @@ class PPConfig(C.Structure):
         ("poisson_tol", C.c_double),
         ("plain_fp64", C.c_int32),
         ("implicit_es", C.c_int32),
+        ("n_harmonics", C.c_int32),
     ]
 
 
@@ -93,6 +96,13 @@ class PPRecord(C.Structure):
         ("coll", (C.c_int64 * 3) * NSPECIES),
         ("absorbed", C.c_int64), ("created", C.c_int64), ("nu_violations", C.c_int64),
         ("ml_err", C.c_double), ("ml_tau", C.c_double), ("ml_used", C.c_int32), ("ml_active", C.c_int32),
+        ("n_harm", C.c_int32), ("pad1", C.c_int32),
+        ("xh_applied", (C.c_double * (2 * (2 * MAX_TURNS + 1))) * (MAX_HARM - 1)),
+        ("xh_next", (C.c_double * (2 * (2 * MAX_TURNS + 1))) * (MAX_HARM - 1)),
+        ("vph", (C.c_double * (2 * MAX_TURNS)) * (MAX_HARM - 1)),
+        ("icaph", (C.c_double * (2 * MAX_TURNS)) * (MAX_HARM - 1)),
+        ("qhath", (C.c_double * (2 * MAX_TURNS)) * (MAX_HARM - 1)),
+        ("rh_kcl", C.c_double * (MAX_HARM - 1)), ("rh_kvl", C.c_double * (MAX_HARM - 1)),
     ]
 
 
@@ -133,6 +143,8 @@ def _load():
         "pp_get_circuit_state": (I, [V, V, P(D), V]),
         "pp_get_turn_phasors": (I, [V, P(PPRecord), V]),
         "pp_get_vacuum_impedance": (I, [V, V, P(D), V]),
+        "pp_set_harmonic_state": (I, [V, I, V]),
+        "pp_get_harmonic_state": (I, [V, I, V, V]),
         "pp_vacuum_impedance": (I, [P(PPVacuumProblem), V, V, P(D), V]),
         "pp_vacuum_capacitance": (I, [P(PPVacuumProblem), D, V, V, V, V]),
         "pp_get_grid": (I, [V, I, V, C.c_int64, V]),
@@ -279,6 +291,7 @@ def make_config(cfg, capacity=None, weight=None, poisson_max_iter=2, poisson_tol
     c.poisson_tol = poisson_tol
     c.plain_fp64 = int(getattr(cfg, "plain_fp64", 0))
     c.implicit_es = int(getattr(cfg, "implicit_es", 0))
+    c.n_harmonics = int(getattr(cfg, "n_harmonics", 1))
     return c
 
 
@@ -482,6 +495,16 @@ class Cell:
         r = PPRecord()
         _check(lib.pp_get_turn_phasors(self.h, C.byref(r), C.c_void_p(stream)), "pp_get_turn_phasors")
         return record_dict(r, self.n_turns)
+
+    def set_harmonic_state(self, m, x):
+        """Applied circuit state of retained harmonic m (complex, 2N+1)."""
+        xv = np.ascontiguousarray(np.asarray(x, dtype=complex)).view(np.float64)
+        _check(lib.pp_set_harmonic_state(self.h, int(m), _ptr(xv)), "pp_set_harmonic_state")
+
+    def harmonic_state(self, m, stream=0):
+        x = np.zeros(2 * (2 * self.n_turns + 1))
+        _check(lib.pp_get_harmonic_state(self.h, int(m), _ptr(x), C.c_void_p(stream)), "pp_get_harmonic_state")
+        return x.view(complex)
 
     def vacuum_impedance(self):
         z = np.zeros(2 * self.n_turns * self.n_turns)
@@ -689,4 +712,9 @@ def record_dict(r, n):
                 r_kcl=r.r_kcl, r_kvl=r.r_kvl, particle_steps=r.particle_steps,
                 n_live=list(r.n_live), coll=np.array([list(r.coll[0]), list(r.coll[1])]),
                 absorbed=r.absorbed, created=r.created, nu_violations=r.nu_violations,
-                ml_err=r.ml_err, ml_tau=r.ml_tau, ml_used=bool(r.ml_used), ml_active=bool(r.ml_active))
+                ml_err=r.ml_err, ml_tau=r.ml_tau, ml_used=bool(r.ml_used), ml_active=bool(r.ml_active),
+                harmonics=[dict(m=h + 2, x_applied=cplx(r.xh_applied[h], 2 * n + 1),
+                                x_next=cplx(r.xh_next[h], 2 * n + 1), vp=cplx(r.vph[h], n),
+                                icap=cplx(r.icaph[h], n), qhat=cplx(r.qhath[h], n),
+                                r_kcl=r.rh_kcl[h], r_kvl=r.rh_kvl[h])
+                           for h in range(max(r.n_harm, 1) - 1)])

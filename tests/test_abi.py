@@ -75,6 +75,8 @@ def test_config_validation_phase_closure():
     (dict(nr=600), "nr exceeds"),
     (dict(nz=1200, n_init=10), "nz exceeds"),
     (dict(plain_fp64=2), "plain_fp64"),
+    (dict(n_harmonics=5), "n_harmonics"),
+    (dict(n_harmonics=-1), "n_harmonics"),
     (dict(z_coil=0.128), "coil turn nodes must lie above"),
     (dict(nr=128, nz=192, turn_r=[0.05], winding=[1], wire_radius=0.008), "too many turn nodes"),
 ])
