@@ -28,13 +28,22 @@ turn potentials and E_theta, B used by the next period's steps are the sums of
 all retained harmonics (waveform reconstruction, exp(+i m w t) peak phasors);
 the powers of the record are the sums over the harmonics (the time-domain
 P_ind and P_cap carry them by construction).
+
+Particle control (oracle.particles, oracle.control): with see_gamma > 0 the
+ions absorbed on the electrode, wall or window emit secondary electrons; with
+particle_weights (or sm_every > 0) every particle carries a relative weight,
+and with sm_every > 0 a split-merge pass follows the append of every
+sm_every-th step.  Creation events are appended ionisations first (electron
+and ion, ordered by the parent electron's uid), then secondary electrons
+(ordered by the parent ion's uid); both species number their new particles
+in that order.
 """
 import math
 import numpy as np
 
 from .constants import EPS0, MU0, QE, ME, M_AR, KB
 from .grid import CellGeometry
-from . import fields, circuit, particles
+from . import fields, circuit, particles, control
 
 
 class OracleCell:
@@ -110,15 +119,25 @@ class OracleCell:
         self.P = [None, None]
         self.next_uid = [0, 0]
         self.window_q = np.zeros((g.NZ, g.NR))
+        self.see_gamma = float(getattr(cfg, "see_gamma", 0.0))
+        self.see_t_ev = float(getattr(cfg, "see_t_ev", 2.0))
+        self.sm_every = int(getattr(cfg, "sm_every", 0))
+        self.sm = (int(getattr(cfg, "sm_target", 0)), int(getattr(cfg, "sm_min", 0)),
+                   int(getattr(cfg, "sm_max", 0)))
+        self.see_emitted = 0
+        self.sm_stats = dict(split=0, merged=0, skipped=0)
         self.s = 0
         self.phi = np.zeros((g.NZ, g.NR))
         self._reset_accumulators()
         self.records = []
 
     # ------------------------------------------------------------------------
-    def set_particles(self, sp, cell, dr, dz, vr, vt, vz, uid):
-        self.P[sp] = dict(cell=np.asarray(cell, np.int64).copy(), dr=np.array(dr), dz=np.array(dz),
+    def set_particles(self, sp, cell, dr, dz, vr, vt, vz, uid, w=None):
+        """w: relative weights (default 1, in the state's dtype)."""
+        dr = np.array(dr)
+        self.P[sp] = dict(cell=np.asarray(cell, np.int64).copy(), dr=dr, dz=np.array(dz),
                           vr=np.array(vr), vt=np.array(vt), vz=np.array(vz),
+                          w=(np.ones(dr.shape, dr.dtype) if w is None else np.array(w, dr.dtype)),
                           uid=np.asarray(uid, np.int64).copy())
         self.next_uid[sp] = int(np.max(uid)) + 1 if len(uid) else 0
 
@@ -168,8 +187,9 @@ class OracleCell:
             cell = P['cell'][live]
             ir, iz = cell % self.cfg.nr, cell // self.cfg.nr
             w = particles.bilinear(P['dr'][live].astype(T), P['dz'][live].astype(T), T)
+            qwp = (sc.qw * P['w'][live].astype(T)).astype(T)
             for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), w):
-                np.add.at(Qs[sp], (iz + di, ir + dj), (sc.qw * wk).astype(np.float64))
+                np.add.at(Qs[sp], (iz + di, ir + dj), (qwp * wk).astype(np.float64))
         return Qs
 
     def deposit_charge(self, T):
@@ -248,12 +268,15 @@ class OracleCell:
         stats = dict(p_ind=0.0, p_es=0.0, absorbed=0, pushed=0, nu_viol=0,
                      coll=np.zeros((2, 3), np.int64))
         events = []
+        see = None
+        if self.see_gamma > 0:
+            see = (T(self.see_gamma), T(math.sqrt(QE * self.see_t_ev / ME)))
         for sp in (0, 1):
             if self.P[sp] is None:
                 continue
             sc = self.species(sp, T)
             ev = particles.push_species(self.P[sp], F, sc, self.geo, s, cfg.seed, T,
-                                        Qs[sp], J, self.window_q, stats, implicit=self.implicit)
+                                        Qs[sp], J, self.window_q, stats, implicit=self.implicit, see=see)
             events.extend(ev)
         Q = Qs[0] + Qs[1]
         if drive is not None:
@@ -262,6 +285,15 @@ class OracleCell:
             J += Jd
             stats['p_ind'] += float(np.sum(Jd * Et))
         self._append(events, T)
+        if self.sm_every > 0 and (s + 1) % self.sm_every == 0:
+            ncell = self.geo.i_win * cfg.nr
+            for sp in (0, 1):
+                if self.P[sp] is None:
+                    continue
+                st_sm, self.next_uid[sp] = control.split_merge(self.P[sp], sp, s, cfg.seed, ncell, *self.sm,
+                                                               self.next_uid[sp], T)
+                for key in st_sm:
+                    self.sm_stats[key] += st_sm[key]
         # Poisson at t_{s+1}
         th_new = self.theta(s + 1)
         chi = self.susceptibility(Qs, T) if self.implicit else None
@@ -291,28 +323,37 @@ class OracleCell:
         self.pushed += stats['pushed']
         self.coll += stats['coll']
         self.absorbed += stats['absorbed']
-        self.created += len(events)
+        n_see = sum(1 for e in events if e['kind'] == 1)
+        self.created += len(events) - n_see
+        self.see_emitted += n_see
         self.s += 1
         self.Q_last = Q
-        info = dict(stats=stats, events=len(events), Q=Q, J=J, Qk=Qk, Qs=Qs)
+        info = dict(stats=stats, events=len(events), see=n_see, Q=Q, J=J, Qk=Qk, Qs=Qs)
         if self.s % N == 0:
             info['record'] = self.period_end()
         return info
 
     def _append(self, events, T):
-        events = sorted(events, key=lambda e: e['parent'])
+        """Creation events: ionisations (kind 0) give an electron and an ion,
+        secondary emissions (kind 1) an electron; ordered by (kind, parent
+        uid), numbered in that order per species."""
+        events = sorted(events, key=lambda e: (e['kind'], e['parent']))
         if not events:
             return
-        n = len(events)
         for sp in (0, 1):
+            evs = events if sp == 0 else [e for e in events if e['kind'] == 0]
+            n = len(evs)
+            if n == 0:
+                continue
             P = self.P[sp]
             uid0 = self.next_uid[sp]
-            new = dict(cell=np.array([e['cell'] for e in events], np.int64),
-                       dr=np.array([e['dr'] for e in events], T),
-                       dz=np.array([e['dz'] for e in events], T),
-                       vr=np.array([(e['ve'] if sp == 0 else e['vi'])[0] for e in events], T),
-                       vt=np.array([(e['ve'] if sp == 0 else e['vi'])[1] for e in events], T),
-                       vz=np.array([(e['ve'] if sp == 0 else e['vi'])[2] for e in events], T),
+            new = dict(cell=np.array([e['cell'] for e in evs], np.int64),
+                       dr=np.array([e['dr'] for e in evs], T),
+                       dz=np.array([e['dz'] for e in evs], T),
+                       vr=np.array([(e['ve'] if sp == 0 else e['vi'])[0] for e in evs], T),
+                       vt=np.array([(e['ve'] if sp == 0 else e['vi'])[1] for e in evs], T),
+                       vz=np.array([(e['ve'] if sp == 0 else e['vi'])[2] for e in evs], T),
+                       w=np.array([e['w'] for e in evs], T),
                        uid=np.arange(uid0, uid0 + n, dtype=np.int64))
             for key in P:
                 P[key] = np.concatenate([P[key], new[key].astype(P[key].dtype)])

@@ -35,6 +35,25 @@ values, never a decision of the same step.
 Cross sections are this project's analytic rational functions of energy (a
 reading: the paper gives none): thresholds 11.55 and 15.76 eV, magnitudes of
 the right order for argon; they are not database fits.
+
+Particle control (the GEC application of Sec. 3.4 runs with secondary-electron
+emission and weighted split-merge, which the paper inherits and does not
+define; readings):
+  * per-particle relative weights w (P['w'], 1 when absent): a particle
+    carries the charge q W_s w, with W_s the species' macro weight; every
+    deposit, current moment and power sum uses (q W_s) w, rounded once in T,
+    which equals q W_s exactly when w = 1;
+  * ion-induced secondary emission: an Ar+ absorbed on the electrode, the side
+    wall or the window emits one electron with probability gamma, decided by
+    the first uniform of draw call 3 (keyed by the ion's uid and the step).
+    The electron starts at the ion's last position inside the plasma (before
+    the move or correction that took it out, at most one ion step from the
+    surface), carries the ion's relative weight, and leaves with a half-space
+    Maxwellian flux at temperature T_see: the normal speed is Rayleigh,
+    v_s sqrt(-2 ln u_b), directed into the plasma, and the two tangential
+    components are Gaussian, v_s sqrt(-2 ln u_c) (cos, sin)(2 pi u_d), with
+    v_s = sqrt(e T_see / m_e).  On the window the departing electron leaves
+    its positive charge on the surface as well (twice the ion's charge).
 """
 import math
 import numpy as np
@@ -164,25 +183,83 @@ def _carry(i, f, T):
     return i + fix, f
 
 
-def _window_charge(window_q, ir2, drn, qw, i_win, nr, T):
+def _window_charge(window_q, ir2, drn, qd, i_win, nr, T):
     """Permanent window charge of particles absorbed on the window surface:
-    linear weights in R on the surface nodes."""
+    linear weights in R on the surface nodes; qd is the charge each one
+    leaves (T)."""
     one = T(1.0)
     rpos = ir2.astype(T) + drn
     j0 = np.floor(rpos).astype(np.int64)
     f = (rpos - j0.astype(T)).astype(T)
-    qd = np.full(j0.shape, qw, T)
+    qd = np.asarray(qd, T)
     np.add.at(window_q, (np.full(j0.shape, i_win), j0), (qd * (one - f)).astype(np.float64))
     np.add.at(window_q, (np.full(j0.shape, i_win), np.minimum(j0 + 1, nr)), (qd * f).astype(np.float64))
 
 
-def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, window_q, stats):
+def secondary_electrons(uid, surface, ir, iz, dr, dz, w, step, seed, see, T, nr):
+    """Ion-induced secondary emission (module docstring) for absorbed ions:
+    uid, surface (0 electrode, 1 side wall, 2 window), the ions' last
+    positions inside the plasma (ir, iz, dr, dz), their relative weights w;
+    see = (gamma, v_s) in T.  Returns the mask of ions that emit and the
+    emission events (kind 1: an electron only)."""
+    gamma, vs = see
+    a, b, c, d = philox.draws(uid, step, 3, 1, seed, T)
+    emit = a < gamma
+    events = []
+    if np.any(emit):
+        rn = np.sqrt(-2.0 * np.log(b.astype(np.float64))).astype(T)
+        rt = np.sqrt(-2.0 * np.log(c.astype(np.float64)))
+        ang = 2.0 * np.pi * d.astype(np.float64)
+        vn = (vs * rn).astype(T)
+        t1 = (vs * (rt * np.cos(ang)).astype(T)).astype(T)
+        t2 = (vs * (rt * np.sin(ang)).astype(T)).astype(T)
+        for q in np.nonzero(emit)[0]:
+            if surface[q] == 0:          # electrode z = 0: into +z
+                ve = (t1[q], t2[q], vn[q])
+            elif surface[q] == 1:        # side wall r = R: into -r
+                ve = (-vn[q], t1[q], t2[q])
+            else:                        # window z = z_win: into -z
+                ve = (t1[q], t2[q], -vn[q])
+            events.append(dict(kind=1, parent=int(uid[q]), cell=int(iz[q] * nr + ir[q]), dr=dr[q], dz=dz[q],
+                               ve=ve, vi=None, w=w[q]))
+    return emit, events
+
+
+def _absorb(window_q, hit_e, hit_w, hit_d, ir_in, iz_in, dr_in, dz_in, ir_out, dr_out, uid, wrel, qwp, sc,
+            geo, step, seed, see, T):
+    """Boundary bookkeeping of the particles that left the plasma region:
+    secondary emission for ions (positions _in: the last ones inside), and the
+    window charge at the surface crossing (positions _out), doubled where the
+    ion emitted.  Returns the emission events."""
+    nr, i_win = geo.cfg.nr, geo.i_win
+    hit = hit_e | hit_w | hit_d
+    emit = np.zeros(hit.shape, bool)
+    events = []
+    if see is not None and sc.sp == 1 and np.any(hit):
+        hi = np.nonzero(hit)[0]
+        surf = np.where(hit_e[hi], 0, np.where(hit_w[hi], 1, 2))
+        em, events = secondary_electrons(uid[hi], surf, ir_in[hi], iz_in[hi], dr_in[hi], dz_in[hi], wrel[hi],
+                                         step, seed, see, T, nr)
+        emit[hi] = em
+    if np.any(hit_d):
+        qd = np.where(emit, qwp * T(2.0), qwp).astype(T)[hit_d]
+        _window_charge(window_q, ir_out[hit_d], dr_out[hit_d], qd, i_win, nr, T)
+    return events
+
+
+def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, window_q, stats, wrel=None,
+                         qwp=None, step=0, seed=0, see=None):
     """The implicit electrostatic kick of the previous step at the predicted
     position (v += (q/m) dt E, x += (q/m) dt^2 E).  A correction through the
     axis reflects (r -> -r, v_r -> -v_r); a correction out of the plasma region
-    absorbs the particle there (window charge on the window surface).
-    Returns the corrected arrays and the mask of particles still alive."""
+    absorbs the particle there (window charge on the window surface, secondary
+    emission from the position before the correction).
+    Returns the corrected arrays, the mask of particles still alive and the
+    emission events."""
     nr, i_win = geo.cfg.nr, geo.i_win
+    if wrel is None:
+        wrel = np.ones(idx.size, T)
+        qwp = np.full(idx.size, sc.qw, T)
     vr_c = (vr + sc.qmd * Er).astype(T)
     vz_c = (vz + sc.qmd * Ez).astype(T)
     # electrostatic work of the kick with the mean of the pre- and post-kick velocities
@@ -202,18 +279,18 @@ def _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo, T, win
     hit_w = (~hit_e) & (irc >= nr)
     hit_d = (~hit_e) & (~hit_w) & (izc >= i_win)
     stats['absorbed'] += int(np.count_nonzero(hit_e | hit_w | hit_d))
-    if np.any(hit_d):
-        _window_charge(window_q, irc[hit_d], drc[hit_d], sc.qw, i_win, nr, T)
+    events = _absorb(window_q, hit_e, hit_w, hit_d, ir, iz, dr, dz, irc, drc, P['uid'][idx], wrel, qwp, sc,
+                     geo, step, seed, see, T)
     alive = ~(hit_e | hit_w | hit_d)
-    stats['p_es'] += float(np.sum(float(sc.qw) * (vbr[alive] * Er[alive].astype(np.float64) +
-                                                  vbz[alive] * Ez[alive].astype(np.float64))))
+    stats['p_es'] += float(np.sum(qwp[alive].astype(np.float64) * (vbr[alive] * Er[alive].astype(np.float64) +
+                                                                   vbz[alive] * Ez[alive].astype(np.float64))))
     P['cell'][idx[~alive]] = DEAD
     P['dr'][idx[~alive]] = T(0.0)
     P['dz'][idx[~alive]] = T(0.0)
-    return irc, izc, drc, dzc, vr_c, vz_c, alive
+    return irc, izc, drc, dzc, vr_c, vz_c, alive, events
 
 
-def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=False):
+def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=False, see=None):
     """Advance one species one step in place.
 
     P: dict with int64 'cell' (DEAD when absorbed), T arrays 'dr','dz','vr',
@@ -227,7 +304,11 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
        the predicted one; the gathered E_r, E_z are applied as the previous
        step's implicit kick, the Boris step carries E_theta and B only, J is
        taken at the corrected position and Q at the next predicted one.
-    Returns the list of ionisation events (electrons only).
+    see: (gamma, v_s) in T to let absorbed ions emit secondary electrons, or
+       None.
+    P may carry relative weights 'w' (module docstring; 1 when absent).
+    Returns the list of creation events: ionisations (kind 0, from electrons)
+    and secondary emissions (kind 1, from ions).
     """
     nr = geo.cfg.nr
     i_win = geo.i_win
@@ -239,6 +320,9 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     dr, dz = P['dr'][idx], P['dz'][idx]
     vr, vt, vz = P['vr'][idx], P['vt'][idx], P['vz'][idx]
     one, half, zero = T(1.0), T(0.5), T(0.0)
+    wrel = P['w'][idx].astype(T) if 'w' in P else np.ones(idx.size, T)
+    qwp = (sc.qw * wrel).astype(T)          # = sc.qw exactly when w = 1
+    events = []
 
     # --- gather at the old position ------------------------------------------
     w = bilinear(dr, dz, T)
@@ -250,9 +334,11 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     n_entry = int(idx.size)
 
     if implicit:
-        ir, iz, dr, dz, vr, vz, ok = _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo,
-                                                         T, window_q, stats)
+        ir, iz, dr, dz, vr, vz, ok, ev = _implicit_correction(P, idx, ir, iz, dr, dz, vr, vz, Er, Ez, sc, geo,
+                                                             T, window_q, stats, wrel, qwp, step, seed, see)
+        events.extend(ev)
         idx, ir, iz, dr, dz, vr, vt, vz = (a[ok] for a in (idx, ir, iz, dr, dz, vr, vt, vz))
+        wrel, qwp = wrel[ok], qwp[ok]
         Et, Br, Bz = Et[ok], Br[ok], Bz[ok]
         cell = iz * nr + ir
         w = bilinear(dr, dz, T)             # current moment at the corrected position
@@ -278,12 +364,12 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     vbt = (vt + vny) * half
     vbr = (vr + vnx) * half
     vbz = (vz + vnz) * half
-    jm = sc.qw * vbt
+    jm = qwp * vbt
     for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), w):
         np.add.at(J, (iz + di, ir + dj), (jm * wk).astype(np.float64))
     stats['p_ind'] += float(np.sum(jm.astype(np.float64) * Et.astype(np.float64)))
     if not implicit:
-        stats['p_es'] += float(np.sum(sc.qw.astype(np.float64) *
+        stats['p_es'] += float(np.sum(qwp.astype(np.float64) *
                                       (vbr.astype(np.float64) * Er.astype(np.float64) +
                                        vbz.astype(np.float64) * Ez.astype(np.float64))))
 
@@ -325,14 +411,8 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     hit_w = (~hit_e) & (ir2 >= nr)
     hit_d = (~hit_e) & (~hit_w) & (iz2 >= i_win)
     stats['absorbed'] += int(np.count_nonzero(hit_e | hit_w | hit_d))
-    if np.any(hit_d):
-        rpos = ir2[hit_d].astype(T) + drn[hit_d]
-        j0 = np.floor(rpos).astype(np.int64)
-        f = (rpos - j0.astype(T)).astype(T)
-        qd = np.full(j0.shape, sc.qw, T)
-        np.add.at(window_q, (np.full(j0.shape, i_win), j0), (qd * (one - f)).astype(np.float64))
-        np.add.at(window_q, (np.full(j0.shape, i_win), np.minimum(j0 + 1, nr)),
-                  (qd * f).astype(np.float64))
+    events.extend(_absorb(window_q, hit_e, hit_w, hit_d, ir, iz, dr, dz, ir2, drn, P['uid'][idx], wrel, qwp,
+                          sc, geo, step, seed, see, T))
     alive = ~(hit_e | hit_w | hit_d)
 
     # --- null-collision MCC at the new position -------------------------------
@@ -340,12 +420,11 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     u0 = philox.null_draw(uid, step, sc.sp, seed, T)
     _, u1, u2, u3 = philox.draws(uid, step, 0, sc.sp, seed, T)
     cand = alive & (u0 < sc.pnull)
-    events = []
     ci = np.nonzero(cand)[0]
     if ci.size:
         if sc.sp == 0:
-            events = _collide_electrons(ci, vr2, vt2, vnz, u1, u2, u3, uid, step, seed,
-                                        sc, T, stats, ir2, iz2, drn, dzn, nr)
+            events.extend(_collide_electrons(ci, vr2, vt2, vnz, u1, u2, u3, uid, step, seed,
+                                             sc, T, stats, ir2, iz2, drn, dzn, nr, wrel))
         else:
             _collide_ions(ci, vr2, vt2, vnz, u1, u2, u3, uid, step, seed, sc, T, stats)
 
@@ -353,7 +432,7 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
     ai = np.nonzero(alive)[0]
     wn = bilinear(drn[ai], dzn[ai], T)
     for (di, dj), wk in zip(((0, 0), (0, 1), (1, 0), (1, 1)), wn):
-        np.add.at(Q, (iz2[ai] + di, ir2[ai] + dj), (sc.qw * wk).astype(np.float64))
+        np.add.at(Q, (iz2[ai] + di, ir2[ai] + dj), (qwp[ai] * wk).astype(np.float64))
 
     # --- write back ------------------------------------------------------------
     newcell = np.where(alive, iz2 * nr + ir2, DEAD)
@@ -368,7 +447,7 @@ def push_species(P, F, sc, geo, step, seed, T, Q, J, window_q, stats, implicit=F
 
 
 def _collide_electrons(ci, vr, vt, vz, u1, u2, u3, uid, step, seed, sc, T, stats,
-                       ir2, iz2, drn, dzn, nr):
+                       ir2, iz2, drn, dzn, nr, wrel):
     x, y, z = vr[ci], vt[ci], vz[ci]
     v2 = x * x + y * y + z * z
     g = np.sqrt(v2)
@@ -414,10 +493,11 @@ def _collide_electrons(ci, vr, vt, vz, u1, u2, u3, uid, step, seed, sc, T, stats
         n0, n1, n2 = _gauss3(a2, a3, b0, b1, T)
         for q in range(ii.size):
             k = p[q]
-            events.append(dict(parent=int(uid[k]), cell=int(iz2[k] * nr + ir2[k]),
+            events.append(dict(kind=0, parent=int(uid[k]), cell=int(iz2[k] * nr + ir2[k]),
                                dr=drn[k], dz=dzn[k],
                                ve=(ge[q] * ex_[q], ge[q] * ey_[q], ge[q] * ez_[q]),
-                               vi=(sc.vth_gas * n0[q], sc.vth_gas * n1[q], sc.vth_gas * n2[q])))
+                               vi=(sc.vth_gas * n0[q], sc.vth_gas * n1[q], sc.vth_gas * n2[q]),
+                               w=wrel[k]))
     return events
 
 

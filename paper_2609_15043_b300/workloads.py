@@ -87,6 +87,16 @@ class CellConfig:
     plain_fp64: int = 0            # 1: the plain FP64 particle form (comparison baseline)
     implicit_es: int = 0           # 1: direct-implicit electrostatics (susceptibility chi in the Poisson solve)
     n_harmonics: int = 1           # retained circuit harmonics m = 1..M (Sec. 4 extension); 1: fundamental only
+    # particle control (off by default): ion-induced secondary emission, per-particle relative
+    # weights and the split-merge pass (every sm_every steps: merge above sm_max particles per
+    # cell, split below sm_min, towards sm_target)
+    see_gamma: float = 0.0
+    see_t_ev: float = 2.0
+    particle_weights: int = 0
+    sm_every: int = 0
+    sm_target: int = 0
+    sm_min: int = 0
+    sm_max: int = 0
     capacity_factor: float = 1.5
     sort_every_e: int = 8
     sort_every_i: int = 50

@@ -251,7 +251,7 @@ def test_chi_potential_is_the_potential_of_the_corrected_charge():
         Ez = particles._gather(F, cell, w, 1)
         sc = oc.species(sp, np.float64)
         stats = dict(absorbed=0, p_es=0.0)
-        irc, izc, drc, dzc, _, _, ok = particles._implicit_correction(
+        irc, izc, drc, dzc, _, _, ok, _ = particles._implicit_correction(
             P, idx, ir, iz, P["dr"][idx], P["dz"][idx], P["vr"][idx], P["vz"][idx], Er, Ez, sc, oc.geo,
             np.float64, np.zeros((g.NZ, g.NR)), stats)
         wc = particles.bilinear(drc[ok], dzc[ok], np.float64)
