@@ -117,6 +117,23 @@ typedef struct pp_config {
                                         fundamental), and the turn potentials, E_theta and B of every
                                         step are the sums over the harmonics.  The learned proposal
                                         requires M = 1. */
+    /* particle control of the GEC-type runs (Sec. 3.4 runs them with secondary emission and
+       weighted split-merge; the paper inherits both and defines neither, so these are readings):
+       see_gamma: probability that an Ar+ absorbed on the electrode, the side wall or the window
+       emits one electron (0: off; requires weight[0] == weight[1]).  The electron starts at the
+       ion's last position inside the plasma with the ion's relative weight and a half-space
+       Maxwellian flux at see_t_ev (eV): Rayleigh normal speed into the plasma, Gaussian tangential
+       components; on the window the departing electron's charge stays on the surface.
+       particle_weights: 1 gives every particle a relative weight w (charge q W_s w; default 1).
+       sm_every > 0 (implies particle_weights): after the append of every sm_every-th step, per
+       species and per cell in increasing uid order, a cell with n > sm_max merges
+       min(n - sm_target, n / 2) disjoint consecutive pairs (one member survives with the summed
+       weight, chosen with probability proportional to its weight), a cell with 0 < n < sm_min
+       splits its first min(sm_target - n, n) particles into two halves of the same state;
+       cells above 4096 particles are left alone.  Requires 1 <= sm_min <= sm_target <= sm_max. */
+    double see_gamma, see_t_ev;
+    int32_t particle_weights;
+    int32_t sm_every, sm_target, sm_min, sm_max;
 } pp_config;
 
 /* Completed-period record (Sec. 2.4 diagnostics; Eqs. vpind, icap, pport,
@@ -194,8 +211,35 @@ int pp_set_particles(pp_cell* cell, int species, int64_t n, const uint32_t* cell
                      const float* vz, const uint32_t* uid);
 
 /*
+ * pp_set_particles_weighted -- pp_set_particles with relative weights w (> 0,
+ * finite; stored in the particle state's type).  PP_E_CONFIG if the cell has
+ * no per-particle weights (pp_config.particle_weights / sm_every).  With
+ * pp_set_particles a weighted cell gives every particle w = 1.
+ */
+int pp_set_particles_weighted(pp_cell* cell, int species, int64_t n, const uint32_t* cell_idx,
+                              const float* dr, const float* dz, const float* vr, const float* vt,
+                              const float* vz, const uint32_t* uid, const double* w);
+
+/*
+ * pp_get_particle_weights -- the relative weights of the live macroparticles of
+ * one species, in the order pp_get_particles reports them (storage order) when
+ * no step runs between the two calls; *n gets the count.  PP_E_CONFIG for a
+ * cell without per-particle weights, PP_E_CAPACITY if cap is too small.
+ * Synchronises `stream`.
+ */
+int pp_get_particle_weights(pp_cell* cell, int species, int64_t cap, int64_t* n, double* w, void* stream);
+
+/*
+ * pp_get_control_counters -- cumulative particle-control counters (out[4]):
+ * [0] secondary electrons emitted, [1] particles split, [2] pairs merged,
+ * [3] cells a split-merge pass left alone (above 4096 particles).
+ * Synchronises `stream`.
+ */
+int pp_get_control_counters(pp_cell* cell, int64_t* out, void* stream);
+
+/*
  * pp_get_particles -- copies the live macroparticles of one species (absorbed
- * ones dropped, order unspecified) to host arrays of length `cap`; *n gets the
+ * ones dropped, in storage order) to host arrays of length `cap`; *n gets the
  * count.  PP_E_CAPACITY if cap is too small.  Synchronises `stream`.
  */
 int pp_get_particles(pp_cell* cell, int species, int64_t cap, int64_t* n, uint32_t* cell_idx,

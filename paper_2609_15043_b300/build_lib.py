@@ -1,8 +1,8 @@
 """Builds libphasorpic.so in-tree for sm_103a with nvcc.
 
-Flags: -gencode arch=compute_103a,code=sm_103a -lineinfo -O3.  The two
-particle-step sources (the fused FP32 kernel and the plain FP64 form) are
-compiled with --fmad=false: their cell crossings, absorptions and collision
+Flags: -gencode arch=compute_103a,code=sm_103a -lineinfo -O3.  The
+particle-step sources (the fused FP32 kernel, the plain FP64 form and the
+split-merge pass) are compiled with --fmad=false: their cell crossings, absorptions and collision
 decisions then round exactly like the oracle's float32 / float64
 instantiations, and the arithmetic that decides nothing (deposit weights,
 moments, power tallies) is fused explicitly with fma intrinsics.  Every other
@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasorpic.so")
 SOURCES = ["pp_capi.cu", "pp_setup.cu", "pp_fields.cu", "pp_pcg.cu", "pp_particles.cu", "pp_plain.cu", "pp_mlp.cu",
-           "pp_mlp_train.cu", "pp_period.cu"]
-NO_CONTRACT = {"pp_particles.cu", "pp_plain.cu"}
+           "pp_mlp_train.cu", "pp_period.cu", "pp_control.cu"]
+NO_CONTRACT = {"pp_particles.cu", "pp_plain.cu", "pp_control.cu"}
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -102,6 +102,8 @@ static void one_step(Cell* c, cudaStream_t st) {
     phase_mark(c, PH_PUSH, false, st);
     phase_mark(c, PH_OTHER, true, st);
     launch_append(c, st);
+    // the split-merge pass after every sm_every-th step's append
+    if (c->sm_every > 0 && (s + 1) % c->sm_every == 0) launch_split_merge(c, st);
     phase_mark(c, PH_OTHER, false, st);
     // The step's counting sorts touch only the particle store, its slot counts
     // and the sort bins; the Poisson solve and the sample touch node grids and
@@ -151,6 +153,7 @@ static void one_step(Cell* c, cudaStream_t st) {
 // counter make the captured kernels valid for every period.
 static bool graph_eligible(const Cell* c) {
     if (!c->use_graphs || c->s % c->n_rf != 0) return false;
+    if (c->sm_every > 0 && c->n_rf % c->sm_every != 0) return false;
     for (int sp = 0; sp < 2; ++sp) {
         int e = c->sort_every[sp];
         if (c->sort_count[sp] != 0 || c->n_rf % e != 0 || (c->n_rf / e) % 2 != 0) return false;
@@ -386,13 +389,24 @@ int pp_destroy(pp_cell* h) {
     return PP_OK;
 }
 
-int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, const float* dr, const float* dz,
-                     const float* vr, const float* vt, const float* vz, const uint32_t* uid) {
+static int set_particles_impl(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, const float* dr,
+                              const float* dz, const float* vr, const float* vt, const float* vz,
+                              const uint32_t* uid, const double* w) {
     Cell* c = reinterpret_cast<Cell*>(h);
     if (!c || sp < 0 || sp > 1 || n < 0 || (n > 0 && (!cell_idx || !dr || !dz || !vr || !vt || !vz || !uid))) {
         set_error("bad argument to pp_set_particles");
         return PP_E_ARG;
     }
+    if (w && !c->weighted) {
+        set_error("the cell has no per-particle weights (pp_config.particle_weights, sm_every)");
+        return PP_E_CONFIG;
+    }
+    if (w)
+        for (int64_t q = 0; q < n; ++q)
+            if (!(w[q] > 0.0 && std::isfinite(w[q]))) {
+                set_error("weights must be positive and finite");
+                return PP_E_ARG;
+            }
     if (n > c->cap[sp]) {
         set_error("population exceeds the species capacity");
         return PP_E_CAPACITY;
@@ -427,6 +441,10 @@ int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, co
         }
         cudaMemcpy(p.cell, cell_idx, b4, cudaMemcpyHostToDevice);
         cudaMemcpy(p.uid, uid, b4, cudaMemcpyHostToDevice);
+        if (p.w) {
+            for (int64_t q = 0; q < n; ++q) tmp[q] = w ? w[q] : 1.0;
+            cudaMemcpy(p.w, tmp.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+        }
     } else {
         ParticleBuf& p = c->pb[sp][c->cur[sp]];
         cudaMemcpy(p.cell, cell_idx, b4, cudaMemcpyHostToDevice);
@@ -436,6 +454,11 @@ int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, co
         cudaMemcpy(p.vt, vt, b4, cudaMemcpyHostToDevice);
         cudaMemcpy(p.vz, vz, b4, cudaMemcpyHostToDevice);
         cudaMemcpy(p.uid, uid, b4, cudaMemcpyHostToDevice);
+        if (p.w) {
+            std::vector<float> tw((size_t)n);
+            for (int64_t q = 0; q < n; ++q) tw[q] = w ? (float)w[q] : 1.0f;
+            cudaMemcpy(p.w, tw.data(), b4, cudaMemcpyHostToDevice);
+        }
     }
     int ni = (int)n;
     cudaMemcpy(c->d_nslot + sp, &ni, sizeof(int), cudaMemcpyHostToDevice);
@@ -446,6 +469,68 @@ int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, co
     c->sort_count[sp] = 0;
     c->primed = false;
     return cuda_check(cudaDeviceSynchronize(), "pp_set_particles");
+}
+
+int pp_set_particles(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, const float* dr, const float* dz,
+                     const float* vr, const float* vt, const float* vz, const uint32_t* uid) {
+    return set_particles_impl(h, sp, n, cell_idx, dr, dz, vr, vt, vz, uid, nullptr);
+}
+
+int pp_set_particles_weighted(pp_cell* h, int sp, int64_t n, const uint32_t* cell_idx, const float* dr,
+                              const float* dz, const float* vr, const float* vt, const float* vz,
+                              const uint32_t* uid, const double* w) {
+    if (n > 0 && !w) {
+        set_error("bad argument to pp_set_particles_weighted");
+        return PP_E_ARG;
+    }
+    return set_particles_impl(h, sp, n, cell_idx, dr, dz, vr, vt, vz, uid, w);
+}
+
+int pp_get_particle_weights(pp_cell* h, int sp, int64_t cap, int64_t* n, double* w, void* stream) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || sp < 0 || sp > 1 || !n) {
+        set_error("bad argument to pp_get_particle_weights");
+        return PP_E_ARG;
+    }
+    if (!c->weighted) {
+        set_error("the cell has no per-particle weights");
+        return PP_E_CONFIG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int ns = 0;
+    cudaMemcpyAsync(&ns, c->d_nslot + sp, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int rc = cuda_check(cudaStreamSynchronize(st), "reading the particle count");
+    if (rc) return rc;
+    std::vector<uint32_t> cl((size_t)ns);
+    std::vector<double> wv((size_t)ns);
+    if (c->fp64) {
+        PBuf<double>& p = c->pd[sp][c->cur[sp]];
+        cudaMemcpy(cl.data(), p.cell, sizeof(uint32_t) * (size_t)ns, cudaMemcpyDeviceToHost);
+        cudaMemcpy(wv.data(), p.w, sizeof(double) * (size_t)ns, cudaMemcpyDeviceToHost);
+    } else {
+        ParticleBuf& p = c->pb[sp][c->cur[sp]];
+        std::vector<float> tw((size_t)ns);
+        cudaMemcpy(cl.data(), p.cell, sizeof(uint32_t) * (size_t)ns, cudaMemcpyDeviceToHost);
+        cudaMemcpy(tw.data(), p.w, sizeof(float) * (size_t)ns, cudaMemcpyDeviceToHost);
+        for (int q = 0; q < ns; ++q) wv[q] = tw[q];
+    }
+    rc = cuda_check(cudaGetLastError(), "reading weights");
+    if (rc) return rc;
+    int64_t m = 0;
+    for (uint32_t x : cl)
+        if (x != kDead) ++m;
+    *n = m;
+    if (m > cap) {
+        set_error("output array too small");
+        return PP_E_CAPACITY;
+    }
+    int64_t o = 0;
+    for (int q = 0; q < ns; ++q)
+        if (cl[q] != kDead) {
+            if (w) w[o] = wv[q];
+            ++o;
+        }
+    return PP_OK;
 }
 
 int pp_get_particles(pp_cell* h, int sp, int64_t cap, int64_t* n, uint32_t* cell_idx, float* dr, float* dz,
@@ -466,7 +551,7 @@ struct CkHeader {
     int64_t s;
 };
 static const uint32_t kCkMagic = 0x4b435050u;   // "PPCK"
-static const uint32_t kCkVersion = 2;
+static const uint32_t kCkVersion = 3;
 
 static std::vector<std::pair<double*, size_t>> ck_grids(Cell* c) {
     size_t n = (size_t)c->nnodes;
@@ -499,33 +584,40 @@ static bool cfg_equal(const pp_config& a, const pp_config& b) {
            PP_EQ(n_trend) && PP_EQ(eps_p) && PP_EQ(alpha_v) && PP_EQ(f_step) && PP_EQ(v_min) && PP_EQ(v_max) &&
            PP_EQ(alpha) && PP_EQ(weight) && PP_EQ(capacity) && PP_EQ(seed) && PP_EQ(sort_every) &&
            PP_EQ(poisson_max_iter) && PP_EQ(poisson_tol) && PP_EQ(plain_fp64) && PP_EQ(implicit_es) &&
-           PP_EQ(n_harmonics);
+           PP_EQ(n_harmonics) && PP_EQ(see_gamma) && PP_EQ(see_t_ev) && PP_EQ(particle_weights) &&
+           PP_EQ(sm_every) && PP_EQ(sm_target) && PP_EQ(sm_min) && PP_EQ(sm_max);
 #undef PP_EQ
 }
 
-// the seven particle arrays of the current buffer and their element sizes
-static void ck_arrays(Cell* c, int sp, void** arr, size_t* es) {
+// the particle arrays of the current buffer (seven, and the weights in a
+// weighted cell) and their element sizes; returns their count
+static int ck_arrays(Cell* c, int sp, void** arr, size_t* es) {
     if (c->fp64) {
         PBuf<double>& p = c->pd[sp][c->cur[sp]];
-        void* a[7] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid};
-        for (int f = 0; f < 7; ++f) {
+        void* a[8] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid, p.w};
+        for (int f = 0; f < 8; ++f) {
             arr[f] = a[f];
             es[f] = (f == 0 || f == 6) ? 4 : 8;
         }
     } else {
         ParticleBuf& p = c->pb[sp][c->cur[sp]];
-        void* a[7] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid};
-        for (int f = 0; f < 7; ++f) {
+        void* a[8] = {p.cell, p.dr, p.dz, p.vr, p.vt, p.vz, p.uid, p.w};
+        for (int f = 0; f < 8; ++f) {
             arr[f] = a[f];
             es[f] = 4;
         }
     }
+    return c->weighted ? 8 : 7;
 }
 
 static uint64_t ck_size(Cell* c, const int* nslot) {
     uint64_t b = sizeof(CkHeader) + sizeof(pp_config) + sizeof(DevState) + 2 * sizeof(uint32_t);
     for (auto& g : ck_grids(c)) b += sizeof(double) * g.second;
-    const uint64_t per = c->fp64 ? 2 * 4 + 5 * 8 : 7 * 4;
+    void* arr[8];
+    size_t es[8];
+    const int na = ck_arrays(c, 0, arr, es);
+    uint64_t per = 0;
+    for (int f = 0; f < na; ++f) per += es[f];
     for (int sp = 0; sp < 2; ++sp) b += per * (uint64_t)nslot[sp];
     return b;
 }
@@ -566,10 +658,10 @@ int pp_checkpoint(pp_cell* h, void* host_buf, uint64_t* bytes) {
         o += sizeof(double) * g.second;
     }
     for (int sp = 0; sp < 2; ++sp) {
-        void* arr[7];
-        size_t es[7];
-        ck_arrays(c, sp, arr, es);
-        for (int f = 0; f < 7; ++f) {
+        void* arr[8];
+        size_t es[8];
+        const int na = ck_arrays(c, sp, arr, es);
+        for (int f = 0; f < na; ++f) {
             size_t nb = es[f] * (size_t)nslot[sp];
             cudaMemcpy(o, arr[f], nb, cudaMemcpyDeviceToHost);
             o += nb;
@@ -619,10 +711,10 @@ int pp_restore(pp_cell* h, const void* host_buf, uint64_t bytes) {
         o += sizeof(double) * g.second;
     }
     for (int sp = 0; sp < 2; ++sp) {
-        void* arr[7];
-        size_t es[7];
-        ck_arrays(c, sp, arr, es);
-        for (int f = 0; f < 7; ++f) {
+        void* arr[8];
+        size_t es[8];
+        const int na = ck_arrays(c, sp, arr, es);
+        for (int f = 0; f < na; ++f) {
             size_t nb = es[f] * (size_t)hd.nslot[sp];
             cudaMemcpy(arr[f], o, nb, cudaMemcpyHostToDevice);
             o += nb;
@@ -1225,6 +1317,18 @@ int pp_get_counters(pp_cell* h, int64_t* out, void* stream) {
     out[9] = c->s;
     out[10] = (int64_t)c->h_st->live[0];
     out[11] = (int64_t)c->h_st->live[1];
+    return PP_OK;
+}
+
+int pp_get_control_counters(pp_cell* h, int64_t* out, void* stream) {
+    Cell* c = reinterpret_cast<Cell*>(h);
+    if (!c || !out) {
+        set_error("bad argument to pp_get_control_counters");
+        return PP_E_ARG;
+    }
+    int rc = read_state(c, (cudaStream_t)stream);
+    if (rc) return rc;
+    for (int q = 0; q < 4; ++q) out[q] = (int64_t)c->h_st->ctl[q];
     return PP_OK;
 }
 

@@ -52,6 +52,7 @@ struct PBuf {
     T* vt;
     T* vz;
     uint32_t* uid;
+    T* w;           // relative weights; nullptr in a cell without per-particle weights
 };
 using ParticleBuf = PBuf<float>;
 
@@ -59,14 +60,17 @@ template <typename T>
 struct SpecT {          // constants of one species in T (rounded once from FP64)
     T qmh, dtr, dtz, qw, numax, pnull, ng, ce, inv_ce, loss, vth_gas;
     T qmd, kres, kzes;  // direct-implicit kick: (q/m) dt, (q/m) dt^2 / dr, (q/m) dt^2 / dz
+    T see_g, see_vs;    // ions: secondary-emission yield (0: off) and sqrt(e T_see / m_e)
 };
 using SpeciesConst = SpecT<float>;
 
 template <typename T>
-struct EventT {         // one ionisation: new e- and Ar+ at the parent's position
-    uint32_t parent, cell;
+struct EventT {         // kind 0: ionisation (new e- and Ar+ at the parent electron's position);
+    uint32_t parent, cell;  // kind 1: secondary emission (new e- at the parent ion's last position)
     T dr, dz;
     T ve[3], vi[3];
+    T w;                // the parent's relative weight (1 without per-particle weights)
+    uint32_t kind;
 };
 using Event = EventT<float>;
 
@@ -107,6 +111,7 @@ struct DevState {
     unsigned long long step;                 // PIC steps completed (drives the RNG counters)
     unsigned int status;
     int n_events;                            // events recorded this step
+    int n_see;                               // of which secondary emissions
     int append_done;                         // blocks of the append kernel that finished ranking
     int accepted;                            // last period end accepted
     long long period;
@@ -133,6 +138,11 @@ struct DevState {
     double qchc[kMaxHarm - 1][PP_MAX_TURNS], qshc[kMaxHarm - 1][PP_MAX_TURNS];
     double hvp[kMaxHarm - 1][2 * PP_MAX_TURNS], hicap[kMaxHarm - 1][2 * PP_MAX_TURNS];
     double hp_port, hp_cu, hp_capph;         // the harmonics' port, copper and phasor-capacitive powers
+    // particle control: cumulative secondary emissions, splits, merges,
+    // skipped cells; the current split-merge pass's split total and whether
+    // its splits fit the store
+    unsigned long long ctl[4];
+    int sm_split_total, sm_nlist, sm_split_ok;
 };
 
 // The retained harmonics' part of turn k's potential at phase theta (Eq.
@@ -213,8 +223,18 @@ struct Cell {
     uint32_t* d_next_uid = nullptr;         // [2]
     uint32_t* d_hist = nullptr;             // counting-sort bins (ncell + 2)
     Event* d_events = nullptr;
-    int event_cap = 0;                      // ionisation events one step can record
-    uint32_t* d_ev_perm = nullptr;          // events in parent-uid order (append kernel)
+    int event_cap = 0;                      // creation events one step can record
+    uint32_t* d_ev_perm = nullptr;          // events in (kind, parent uid) order (append kernel)
+    // particle control
+    bool weighted = false;                  // per-particle relative weights
+    bool see = false;                       // ion-induced secondary emission
+    int sm_every = 0, sm_target = 0, sm_min = 0, sm_max = 0;
+    uint32_t* d_sm_cnt = nullptr;           // per cell: live particles (ncell + 2)
+    uint32_t* d_sm_start = nullptr;         // per cell: first slot of its run in d_sm_perm (ncell + 1)
+    uint32_t* d_sm_cursor = nullptr;        // per cell: scatter cursor
+    uint32_t* d_sm_soff = nullptr;          // per cell: first new slot of its splits (ncell + 1)
+    int* d_sm_list = nullptr;               // cells the pass acts on
+    uint32_t* d_sm_perm = nullptr;          // slots of the acting cells' particles, grouped by cell
 
     // direct-implicit electrostatics: susceptibility from the species charges
     bool implicit = false;
@@ -382,6 +402,7 @@ void push_prepare(Cell* c);
 void launch_append(Cell* c, cudaStream_t st);
 void launch_sort(Cell* c, int sp, cudaStream_t st);
 void launch_deposit_only(Cell* c, cudaStream_t st);
+void launch_split_merge(Cell* c, cudaStream_t st);
 // in_step: the step's field preparation already imposed the turn potentials
 // and cleared the bookkeeping, and the step's sample kernel takes the final
 // convergence decision

@@ -133,7 +133,7 @@ struct CollCtx {
 template <typename T>
 __device__ __forceinline__ void electron_collision(const CollCtx<T>& a, uint32_t step, const SpecT<T>& S,
                                                    uint32_t uid, T& vx, T& vy, T& vz, uint32_t cell, T drn,
-                                                   T dzn, unsigned* cnt) {
+                                                   T dzn, unsigned* cnt, T w = T(1.0)) {
     U4 u = draw4(uid, step, 0u, 0u, a.key0, a.key1);
     T x = vx, y = vy, z = vz;
     T v2 = x * x + y * y + z * z;
@@ -182,6 +182,8 @@ __device__ __forceinline__ void electron_collision(const CollCtx<T>& a, uint32_t
             e.vi[0] = a.vth_gas_ion * g0;
             e.vi[1] = a.vth_gas_ion * g1;
             e.vi[2] = a.vth_gas_ion * g2;
+            e.w = w;
+            e.kind = 0u;
             a.ev[slot] = e;
         } else {
             atomicOr(&a.st->status, (unsigned)PP_ST_EVENTS);
@@ -190,6 +192,55 @@ __device__ __forceinline__ void electron_collision(const CollCtx<T>& a, uint32_t
     vx = gn * dx;
     vy = gn * dy;
     vz = gn * dzz;
+}
+
+// Ion-induced secondary emission of an Ar+ absorbed on a surface (0
+// electrode, 1 side wall, 2 window): with probability see_g (first uniform of
+// draw call 3) one electron starts at the ion's last position inside the
+// plasma (cell, dr, dz) with the ion's weight, its normal speed Rayleigh,
+// v_s sqrt(-2 ln u_b), into the plasma, its tangential components
+// v_s sqrt(-2 ln u_c) (cos, sin)(2 pi u_d).  Recorded as a kind-1 event.
+// Returns whether the ion emitted.
+template <typename T>
+__device__ __forceinline__ bool see_emit(const CollCtx<T>& a, uint32_t step, const SpecT<T>& S, uint32_t uid,
+                                         int surface, uint32_t cell, T dr, T dz, T w) {
+    U4 u = draw4(uid, step, 3u, 1u, a.key0, a.key1);
+    if (!(T(u.a) < S.see_g)) return false;
+    const T rn = sqrt_t(T(-2.0) * log_t(T(u.b)));
+    const T rt = sqrt_t(T(-2.0) * log_t(T(u.c)));
+    T sd, cd;
+    sincospi_t(T(2.0) * T(u.d), &sd, &cd);
+    const T vn = S.see_vs * rn;
+    const T t1 = S.see_vs * (rt * cd), t2 = S.see_vs * (rt * sd);
+    EventT<T> e;
+    e.parent = uid;
+    e.cell = cell;
+    e.dr = dr;
+    e.dz = dz;
+    if (surface == 0) {
+        e.ve[0] = t1;
+        e.ve[1] = t2;
+        e.ve[2] = vn;
+    } else if (surface == 1) {
+        e.ve[0] = -vn;
+        e.ve[1] = t1;
+        e.ve[2] = t2;
+    } else {
+        e.ve[0] = t1;
+        e.ve[1] = t2;
+        e.ve[2] = -vn;
+    }
+    e.vi[0] = e.vi[1] = e.vi[2] = T(0.0);
+    e.w = w;
+    e.kind = 1u;
+    int slot = atomicAdd(&a.st->n_events, 1);
+    if (slot < a.ev_cap) {
+        a.ev[slot] = e;
+        atomicAdd(&a.st->n_see, 1);
+    } else {
+        atomicOr(&a.st->status, (unsigned)PP_ST_EVENTS);
+    }
+    return true;
 }
 
 // Ar+-Ar against a gas partner drawn from the 300 K Maxwellian: charge

@@ -445,6 +445,10 @@ int pp_ml_configure(pp_cell* h, const pp_mlp* m, double alpha_ml, int collect) {
         set_error("pp_ml_configure: the proposal predicts the fundamental's loads; the cell retains harmonics");
         return PP_E_CONFIG;
     }
+    if (c->weighted) {
+        set_error("pp_ml_configure: the summaries count unweighted macroparticles; the cell has per-particle weights");
+        return PP_E_CONFIG;
+    }
     return ml_configure(c, m, alpha_ml, collect);
 }
 

@@ -207,9 +207,10 @@ static_assert(kTileRows <= kPushThreads / 32, "one warp clears and flushes each 
 
 // shared-memory layout of one block (dynamic)
 struct PushSmem {
-    static constexpr int kArrays = 7;        // cell, dr, dz, vr, vt, vz, uid
-    static size_t bytes(int NR) {
-        return sizeof(float) * kChunk * kArrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
+    // cell, dr, dz, vr, vt, vz, uid, and the weights w with per-particle weights
+    static size_t bytes(int NR, bool weighted) {
+        const int arrays = weighted ? 8 : 7;
+        return sizeof(float) * kChunk * arrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
                256;
     }
 };
@@ -219,7 +220,10 @@ struct PushSmem {
 // thread advances kPPT consecutive particles (gather, Boris, current and
 // charge deposits accumulated in registers, move, boundaries, null test), the
 // few collision candidates are then processed densely, and bulk copies write
-// the six updated slices back.
+// the six updated slices back.  W: per-particle relative weights (staged as
+// an eighth slice, read only); each particle's charge is then (q W_s) w.
+// Ions absorbed on a surface may emit a secondary electron (see_emit).
+template <bool W>
 __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t* s_cell = reinterpret_cast<uint32_t*>(smem);
@@ -229,7 +233,8 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     float* s_vt = s_vr + kChunk;
     float* s_vz = s_vt + kChunk;
     uint32_t* s_uid = reinterpret_cast<uint32_t*>(s_vz + kChunk);
-    float* t_rho = reinterpret_cast<float*>(s_uid + kChunk);
+    float* s_w = reinterpret_cast<float*>(s_uid + kChunk);          // used when W
+    float* t_rho = s_w + (W ? kChunk : 0);
     float* t_jm = t_rho + kTileRows * a.NR;
     uint16_t* s_cand = reinterpret_cast<uint16_t*>(t_jm + kTileRows * a.NR);
     __shared__ __align__(8) uint64_t s_bar;
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x;
     const uint32_t step = (uint32_t)(*a.step);
+    const CollCtx<float> cc{a.key0, a.key1, a.ev, a.ev_cap, a.st, a.sp[1].vth_gas};
 
     if (t == 0) {
         mbar_init(&s_bar, 1);
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         // ---- stage the chunk (previous bulk stores must have read their smem)
         if (t == 0) {
             bulk_wait_read();
-            mbar_expect_tx(&s_bar, 7u * bytes);
+            mbar_expect_tx(&s_bar, (W ? 8u : 7u) * bytes);
             bulk_g2s(s_cell, P.cell + base, bytes, &s_bar);
             bulk_g2s(s_dr, P.dr + base, bytes, &s_bar);
             bulk_g2s(s_dz, P.dz + base, bytes, &s_bar);
@@ -292,6 +298,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bulk_g2s(s_vt, P.vt + base, bytes, &s_bar);
             bulk_g2s(s_vz, P.vz + base, bytes, &s_bar);
             bulk_g2s(s_uid, P.uid + base, bytes, &s_bar);
+            if (W) bulk_g2s(s_w, P.w + base, bytes, &s_bar);
             s_ncand = 0;
         }
         bool ok = mbar_wait(&s_bar, parity);
@@ -367,6 +374,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             const int ir0 = (int)cell - iz0 * nr;
             const float dr0 = s_dr[p], dz0 = s_dz[p];
             const float vr0 = s_vr[p], vt = s_vt[p], vz0 = s_vz[p];
+            const float wq = W ? S.qw * s_w[p] : S.qw;          // the particle's charge
             if (cell != fcell) {
                 const float4* f = reinterpret_cast<const float4*>(a.F) + (size_t)cell * 5;
                 f0 = __ldg(f);
@@ -419,12 +427,17 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                 const bool cw = !ce && irc >= nr;
                 const bool cd = !ce && !cw && izc >= a.i_win;
                 if (ce || cw || cd) {
+                    bool emit = false;
+                    if (sp == 1 && S.see_g > 0.0f)
+                        emit = see_emit(cc, step, S, s_uid[p], ce ? 0 : (cw ? 1 : 2), cell, dr0, dz0,
+                                        W ? s_w[p] : 1.0f);
                     if (cd) {
+                        const float qd = emit ? wq * 2.0f : wq;
                         float rpos = (float)irc + tr;
                         int j0 = (int)floorf(rpos);
                         float fr = rpos - (float)j0;
-                        atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
-                        atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+                        atomicAdd(&a.win[a.i_win * NR + j0], (double)(qd * (one - fr)));
+                        atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(qd * fr));
                     }
                     ++cnt[0];
                     ++cnt[1 + sp];
@@ -434,7 +447,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                     continue;
                 }
                 // electrostatic work of the kick (mean of the pre- and post-kick velocities)
-                acc_es = __fmaf_rn(S.qw, __fmaf_rn((vr + vrc) * 0.5f, Er, ((vz + vzc) * 0.5f) * Ez), acc_es);
+                acc_es = __fmaf_rn(wq, __fmaf_rn((vr + vrc) * 0.5f, Er, ((vz + vzc) * 0.5f) * Ez), acc_es);
                 ir = irc;
                 iz = izc;
                 dr = tr;
@@ -469,9 +482,9 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             float vbt = (vt + vny) * 0.5f;
             float vbr = (vr + vnx) * 0.5f;
             float vbz = (vz + vnz) * 0.5f;
-            float jmv = S.qw * vbt;
+            float jmv = wq * vbt;
             acc_ind = __fmaf_rn(jmv, Et, acc_ind);
-            if (!a.implicit) acc_es = __fmaf_rn(S.qw, __fmaf_rn(vbr, Er, vbz * Ez), acc_es);
+            if (!a.implicit) acc_es = __fmaf_rn(wq, __fmaf_rn(vbr, Er, vbz * Ez), acc_es);
             ++cnt[0];
             dep_run(dj, tj, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
             // move (cell units): r' = |(r + a, b)| written as r + delta
@@ -514,20 +527,25 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bool he = iz2 < 0;
             bool hw = !he && ir2 >= nr;
             bool hd = !he && !hw && iz2 >= a.i_win;
+            bool emit = false;
+            if (sp == 1 && S.see_g > 0.0f && (he || hw || hd))
+                emit = see_emit(cc, step, S, s_uid[p], he ? 0 : (hw ? 1 : 2), (uint32_t)(iz * nr + ir), dr, dz,
+                                W ? s_w[p] : 1.0f);
             if (hd) {
+                const float qd = emit ? wq * 2.0f : wq;
                 float rpos = (float)ir2 + drn;
                 int j0 = (int)floorf(rpos);
                 float fr = rpos - (float)j0;
-                atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
-                atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+                atomicAdd(&a.win[a.i_win * NR + j0], (double)(qd * (one - fr)));
+                atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(qd * fr));
             }
             const bool alive = !(he || hw || hd);
             uint32_t ncell = kDead;
             if (alive) {
                 ncell = (uint32_t)(iz2 * nr + ir2);
                 float wa2 = one - drn, wb2 = one - dzn;
-                dep_home(dq, dq2, tq, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
-                         S.qw * (drn * dzn));
+                dep_home(dq, dq2, tq, iz2, ir2, wq * (wa2 * wb2), wq * (drn * wb2), wq * (wa2 * dzn),
+                         wq * (drn * dzn));
                 // null-collision test; candidates are processed densely below
                 uint32_t r = philox2x32_10(s_uid[p], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
                                            a.key0 ^ a.key1);
@@ -551,14 +569,14 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         __syncthreads();
         // ---- phase B: collisions of the candidates
         const int nc = s_ncand;
-        const CollCtx<float> cc{a.key0, a.key1, a.ev, a.ev_cap, a.st, a.sp[1].vth_gas};
         if (t < nc) {
             unsigned pc[6] = {0, 0, 0, 0, 0, 0};
             for (int c = t; c < nc; c += kPushThreads) {
                 const int p = s_cand[c];
                 float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
                 if (sp == 0)
-                    electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], pc);
+                    electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], pc,
+                                       W ? s_w[p] : 1.0f);
                 else
                     ion_collision(cc, step, S, s_uid[p], vx, vy, vzz, pc);
                 s_vr[p] = vx;
@@ -640,12 +658,16 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
 
 void push_prepare(Cell* c) {
     if (c->push_blocks) return;
-    size_t shm = PushSmem::bytes(c->NR);
-    cudaFuncSetAttribute(push_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    size_t shm = PushSmem::bytes(c->NR, c->weighted);
+    cudaFuncSetAttribute(push_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(push_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     int dev = 0, nsm = 148, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel, kPushThreads, shm);
+    if (c->weighted)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel<true>, kPushThreads, shm);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel<false>, kPushThreads, shm);
     per = per < 1 ? 1 : per;
     c->push_per_sm_max = per;
     c->push_blocks = nsm * ((c->push_per_sm > 0 && c->push_per_sm < per) ? c->push_per_sm : per);
@@ -675,9 +697,12 @@ void launch_push(Cell* c, cudaStream_t st) {
     a.ev = c->d_events;
     a.ev_cap = c->event_cap;
     a.st = c->d_st;
-    size_t shm = PushSmem::bytes(c->NR);
+    size_t shm = PushSmem::bytes(c->NR, c->weighted);
     push_prepare(c);
-    push_kernel<<<c->push_blocks, kPushThreads, shm, st>>>(a);
+    if (c->weighted)
+        push_kernel<true><<<c->push_blocks, kPushThreads, shm, st>>>(a);
+    else
+        push_kernel<false><<<c->push_blocks, kPushThreads, shm, st>>>(a);
     count_launch();
 }
 
@@ -691,11 +716,12 @@ __global__ void deposit_only(PBuf<T> P, const int* nslot, int sp, T qw, T* rho, 
     int iz = (int)(cell / (uint32_t)nr), ir = (int)(cell - (uint32_t)iz * (uint32_t)nr);
     T dr = P.dr[idx], dz = P.dz[idx];
     T wa = T(1.0) - dr, wb = T(1.0) - dz;
+    const T q = P.w ? qw * P.w[idx] : qw;
     T* p = rho + iz * NR + ir;
-    atomicAdd(p, qw * (wa * wb));
-    atomicAdd(p + 1, qw * (dr * wb));
-    atomicAdd(p + NR, qw * (wa * dz));
-    atomicAdd(p + NR + 1, qw * (dr * dz));
+    atomicAdd(p, q * (wa * wb));
+    atomicAdd(p + 1, q * (dr * wb));
+    atomicAdd(p + NR, q * (wa * dz));
+    atomicAdd(p + NR + 1, q * (dr * dz));
 }
 
 void launch_deposit_only(Cell* c, cudaStream_t st) {
@@ -715,34 +741,38 @@ void launch_deposit_only(Cell* c, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- append events
-// The step's ionisation events are appended as e- / Ar+ pairs with uid =
-// next_uid + rank, rank = the event's position in parent-uid order (a parent
-// ionises at most once per step, so the parent uids are distinct and the rank
-// of an event is the number of events with a smaller parent uid).  Block b
-// ranks events [b*kAppendThreads, (b+1)*kAppendThreads) against all events,
-// staged through shared memory in tiles, and scatters their indices into
-// `perm`; the last block to finish (arrival counter, no waiting) writes the
-// pairs and updates the slot counts, uids and counters.  The grid covers the
-// event capacity; blocks beyond the step's event count return at once.
+// The step's creation events are appended in (kind, parent uid) order:
+// ionisations (kind 0) as e- / Ar+ pairs, then secondary emissions (kind 1)
+// as electrons.  A new particle's uid is next_uid + its rank among its
+// species' new particles (a parent ionises at most once per step and an ion
+// is absorbed once, so the keys are distinct and an event's rank is the
+// number of events with a smaller key).  Block b ranks events
+// [b*kAppendThreads, (b+1)*kAppendThreads) against all events, staged through
+// shared memory in tiles, and scatters their indices into `perm`; the last
+// block to finish (arrival counter, no waiting) writes the particles and
+// updates the slot counts, uids and counters.  The grid covers the event
+// capacity; blocks beyond the step's event count return at once.
 template <typename T>
 __global__ void __launch_bounds__(kAppendThreads) append_kernel(PBuf<T> pe, PBuf<T> pi, int* nslot,
                                                                 uint32_t* next_uid, const EventT<T>* ev,
                                                                 uint32_t* perm, int ev_cap, DevState* st,
                                                                 int64_t cap_e, int64_t cap_i) {
     constexpr int kTile = 4096;
-    __shared__ uint32_t tile[kTile];
+    __shared__ unsigned long long tile[kTile];
     __shared__ int s_last;
     const int n_ev = min(st->n_events, ev_cap);
     const int first = blockIdx.x * kAppendThreads;
     if (n_ev == 0 || first >= n_ev) return;
     const int nblk = (n_ev + kAppendThreads - 1) / kAppendThreads;
     const int q = first + (int)threadIdx.x;
-    const uint32_t kq = (q < n_ev) ? ev[q].parent : 0u;
+    const unsigned long long kq =
+        (q < n_ev) ? (((unsigned long long)ev[q].kind << 32) | (unsigned long long)ev[q].parent) : 0ull;
     int rank = 0;
     for (int base = 0; base < n_ev; base += kTile) {
         const int m = min(kTile, n_ev - base);
         __syncthreads();
-        for (int j = threadIdx.x; j < m; j += kAppendThreads) tile[j] = ev[base + j].parent;
+        for (int j = threadIdx.x; j < m; j += kAppendThreads)
+            tile[j] = ((unsigned long long)ev[base + j].kind << 32) | (unsigned long long)ev[base + j].parent;
         __syncthreads();
         if (q < n_ev)
             for (int j = 0; j < m; ++j) rank += tile[j] < kq ? 1 : 0;
@@ -756,12 +786,21 @@ __global__ void __launch_bounds__(kAppendThreads) append_kernel(PBuf<T> pe, PBuf
     if (!s_last) return;
     __threadfence();
     const int ne = nslot[0], ni = nslot[1];
-    int n_add = n_ev;
-    if ((int64_t)ne + n_add > cap_e) n_add = (int)(cap_e - ne);
-    if ((int64_t)ni + n_add > cap_i) n_add = (int)(cap_i - ni);
-    if (n_add < 0) n_add = 0;
+    const int n_see = min(((volatile int*)&st->n_see)[0], n_ev);
+    const int n_pair = n_ev - n_see;
+    int n_pair_add = n_pair;
+    if ((int64_t)ne + n_pair_add > cap_e) n_pair_add = (int)(cap_e - ne);
+    if ((int64_t)ni + n_pair_add > cap_i) n_pair_add = (int)(cap_i - ni);
+    if (n_pair_add < 0) n_pair_add = 0;
+    int n_see_add = 0;
+    if (n_pair_add == n_pair) {
+        n_see_add = n_see;
+        if ((int64_t)ne + n_pair + n_see_add > cap_e) n_see_add = (int)(cap_e - ne - n_pair);
+        if (n_see_add < 0) n_see_add = 0;
+    }
+    const int n_e_add = n_pair_add + n_see_add;
     const uint32_t ue = next_uid[0], ui = next_uid[1];
-    for (int r = threadIdx.x; r < n_add; r += kAppendThreads) {
+    for (int r = threadIdx.x; r < n_e_add; r += kAppendThreads) {
         const EventT<T> e = ev[((volatile uint32_t*)perm)[r]];
         pe.cell[ne + r] = e.cell;
         pe.dr[ne + r] = e.dr;
@@ -770,26 +809,32 @@ __global__ void __launch_bounds__(kAppendThreads) append_kernel(PBuf<T> pe, PBuf
         pe.vt[ne + r] = e.ve[1];
         pe.vz[ne + r] = e.ve[2];
         pe.uid[ne + r] = ue + (uint32_t)r;
-        pi.cell[ni + r] = e.cell;
-        pi.dr[ni + r] = e.dr;
-        pi.dz[ni + r] = e.dz;
-        pi.vr[ni + r] = e.vi[0];
-        pi.vt[ni + r] = e.vi[1];
-        pi.vz[ni + r] = e.vi[2];
-        pi.uid[ni + r] = ui + (uint32_t)r;
+        if (pe.w) pe.w[ne + r] = e.w;
+        if (r < n_pair_add) {
+            pi.cell[ni + r] = e.cell;
+            pi.dr[ni + r] = e.dr;
+            pi.dz[ni + r] = e.dz;
+            pi.vr[ni + r] = e.vi[0];
+            pi.vt[ni + r] = e.vi[1];
+            pi.vz[ni + r] = e.vi[2];
+            pi.uid[ni + r] = ui + (uint32_t)r;
+            if (pi.w) pi.w[ni + r] = e.w;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        nslot[0] = ne + n_add;
-        nslot[1] = ni + n_add;
-        next_uid[0] = ue + (uint32_t)n_add;
-        next_uid[1] = ui + (uint32_t)n_add;
-        st->cnt[C_CREATED] += (unsigned long long)n_add;
-        st->live[0] += (unsigned long long)n_add;
-        st->live[1] += (unsigned long long)n_add;
-        st->per[C_CREATED] += (unsigned long long)n_add;
-        if (n_add < n_ev) st->status |= PP_ST_CAPACITY;
+        nslot[0] = ne + n_e_add;
+        nslot[1] = ni + n_pair_add;
+        next_uid[0] = ue + (uint32_t)n_e_add;
+        next_uid[1] = ui + (uint32_t)n_pair_add;
+        st->cnt[C_CREATED] += (unsigned long long)n_pair_add;
+        st->live[0] += (unsigned long long)n_e_add;
+        st->live[1] += (unsigned long long)n_pair_add;
+        st->per[C_CREATED] += (unsigned long long)n_pair_add;
+        st->ctl[0] += (unsigned long long)n_see_add;
+        if (n_e_add < n_ev) st->status |= PP_ST_CAPACITY;
         st->n_events = 0;
+        st->n_see = 0;
         st->append_done = 0;
     }
 }
@@ -865,6 +910,7 @@ __global__ void sort_scatter(PBuf<T> src, PBuf<T> dst, const int* nslot, int sp,
     dst.vt[pos] = src.vt[idx];
     dst.vz[pos] = src.vz[idx];
     dst.uid[pos] = src.uid[idx];
+    if (src.w) dst.w[pos] = src.w[idx];
 }
 
 // the new slot count, then the bins are cleared for the next sort

@@ -4,7 +4,8 @@
 // corner table, current and charge deposited with global atomics, collisions
 // handled inline by the thread that found them.  Instantiated with double it
 // is the plain FP64 PIC step; every arithmetic expression is the fused
-// kernel's (and the oracle's) in the same order, evaluated in T.
+// kernel's (and the oracle's) in the same order, evaluated in T, including the
+// per-particle weights and the secondary emission of absorbed ions.
 #include "pp_internal.h"
 #include "pp_mcc.cuh"
 
@@ -61,6 +62,8 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         T dr = P.dr[q], dz = P.dz[q];
         T vr = P.vr[q], vz = P.vz[q];
         const T vt = P.vt[q];
+        const T wrel = P.w ? P.w[q] : one;
+        const T wq = P.w ? S.qw * wrel : S.qw;               // the particle's charge
         const T* f = a.F + (size_t)cell * 20;
         // gather (bilinear weights at the old position)
         T wa = one - dr, wb = one - dz;
@@ -102,12 +105,16 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
             const bool cw = !ce && irc >= nr;
             const bool cd = !ce && !cw && izc >= a.i_win;
             if (ce || cw || cd) {
+                bool emit = false;
+                if (sp == 1 && S.see_g > T(0.0))
+                    emit = see_emit(cc, step, S, P.uid[q], ce ? 0 : (cw ? 1 : 2), cell, dr, dz, wrel);
                 if (cd) {
+                    const T qd = emit ? wq * T(2.0) : wq;
                     T rpos = (T)irc + tr;
                     int j0 = (int)floor_t(rpos);
                     T fr = rpos - (T)j0;
-                    atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
-                    atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+                    atomicAdd(&a.win[a.i_win * NR + j0], (double)(qd * (one - fr)));
+                    atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(qd * fr));
                 }
                 ++cnt[7 + sp];
                 P.cell[q] = kDead;
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
                 P.dz[q] = T(0.0);
                 continue;
             }
-            acc_es += (double)(S.qw * (((vr + vrc) * T(0.5)) * Er + ((vz + vzc) * T(0.5)) * Ez));
+            acc_es += (double)(wq * (((vr + vrc) * T(0.5)) * Er + ((vz + vzc) * T(0.5)) * Ez));
             ir = irc;
             iz = izc;
             dr = tr;
@@ -149,9 +156,9 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         T vbt = (vt + vny) * T(0.5);
         T vbr = (vr + vnx) * T(0.5);
         T vbz = (vz + vnz) * T(0.5);
-        T jmv = S.qw * vbt;
+        T jmv = wq * vbt;
         acc_ind += (double)(jmv * Et);
-        if (!a.implicit) acc_es += (double)(S.qw * (vbr * Er + vbz * Ez));
+        if (!a.implicit) acc_es += (double)(wq * (vbr * Er + vbz * Ez));
         add4(a.jm, NR, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
         // move (cell units): r' = |(r + a, b)| written as r + delta
         T am = vnx * S.dtr, bm = vny * S.dtr, cm = vnz * S.dtz;
@@ -191,24 +198,28 @@ __global__ void __launch_bounds__(256, 2) push_plain(PlainArgs<T> a) {
         bool he = iz2 < 0;
         bool hw = !he && ir2 >= nr;
         bool hd = !he && !hw && iz2 >= a.i_win;
+        bool emit = false;
+        if (sp == 1 && S.see_g > T(0.0) && (he || hw || hd))
+            emit = see_emit(cc, step, S, P.uid[q], he ? 0 : (hw ? 1 : 2), (uint32_t)(iz * nr + ir), dr, dz, wrel);
         if (hd) {
+            const T qd = emit ? wq * T(2.0) : wq;
             T rpos = (T)ir2 + drn;
             int j0 = (int)floor_t(rpos);
             T fr = rpos - (T)j0;
-            atomicAdd(&a.win[a.i_win * NR + j0], (double)(S.qw * (one - fr)));
-            atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(S.qw * fr));
+            atomicAdd(&a.win[a.i_win * NR + j0], (double)(qd * (one - fr)));
+            atomicAdd(&a.win[a.i_win * NR + min(j0 + 1, nr)], (double)(qd * fr));
         }
         const bool alive = !(he || hw || hd);
         uint32_t ncell = kDead;
         if (alive) {
             ncell = (uint32_t)(iz2 * nr + ir2);
             T wa2 = one - drn, wb2 = one - dzn;
-            add4(a.rho[sp], NR, iz2, ir2, S.qw * (wa2 * wb2), S.qw * (drn * wb2), S.qw * (wa2 * dzn),
-                 S.qw * (drn * dzn));
+            add4(a.rho[sp], NR, iz2, ir2, wq * (wa2 * wb2), wq * (drn * wb2), wq * (wa2 * dzn),
+                 wq * (drn * dzn));
             uint32_t r = philox2x32_10(P.uid[q], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31), a.key0 ^ a.key1);
             if (T(u01(r)) < S.pnull) {
                 if (sp == 0)
-                    electron_collision(cc, step, S, P.uid[q], vr2, vt2, vnz, ncell, drn, dzn, cnt);
+                    electron_collision(cc, step, S, P.uid[q], vr2, vt2, vnz, ncell, drn, dzn, cnt, wrel);
                 else
                     ion_collision(cc, step, S, P.uid[q], vr2, vt2, vnz, cnt);
             }

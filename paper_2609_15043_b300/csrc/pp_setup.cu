@@ -178,6 +178,8 @@ static void species_constants(Cell* c) {
         d.qmd = q / m * f.dt;
         d.kres = q / m * f.dt * f.dt / c->dr;
         d.kzes = q / m * f.dt * f.dt / c->dz;
+        d.see_g = sp == 1 ? f.see_gamma : 0.0;
+        d.see_vs = sp == 1 && f.see_gamma > 0.0 ? std::sqrt(kQe * f.see_t_ev / kMe) : 0.0;
         c->chi_qm[sp] = q / m;
         SpeciesConst& s = c->sc[sp];
         s.qmh = (float)d.qmh;
@@ -194,6 +196,8 @@ static void species_constants(Cell* c) {
         s.qmd = (float)d.qmd;
         s.kres = (float)d.kres;
         s.kzes = (float)d.kzes;
+        s.see_g = (float)d.see_g;
+        s.see_vs = (float)d.see_vs;
     }
 }
 
@@ -331,7 +335,22 @@ int setup_cell(Cell* c) {
     if (f.plain_fp64 != 0 && f.plain_fp64 != 1) return fail("plain_fp64 must be 0 or 1");
     if (f.implicit_es != 0 && f.implicit_es != 1) return fail("implicit_es must be 0 or 1");
     if (f.n_harmonics < 0 || f.n_harmonics > PP_MAX_HARM) return fail("n_harmonics must be in 1..PP_MAX_HARM");
+    if (!(f.see_gamma >= 0.0 && f.see_gamma <= 1.0)) return fail("see_gamma must lie in [0, 1]");
+    if (f.see_gamma > 0.0 && !(f.see_t_ev > 0.0 && std::isfinite(f.see_t_ev)))
+        return fail("see_t_ev must be positive");
+    if (f.see_gamma > 0.0 && f.weight[0] != f.weight[1])
+        return fail("secondary emission needs equal macro weights of electrons and ions");
+    if (f.particle_weights != 0 && f.particle_weights != 1) return fail("particle_weights must be 0 or 1");
+    if (f.sm_every < 0) return fail("sm_every must be >= 0");
+    if (f.sm_every > 0 && !(f.sm_min >= 1 && f.sm_min <= f.sm_target && f.sm_target <= f.sm_max))
+        return fail("split-merge needs 1 <= sm_min <= sm_target <= sm_max");
     c->implicit = f.implicit_es == 1;
+    c->see = f.see_gamma > 0.0;
+    c->sm_every = f.sm_every;
+    c->sm_target = f.sm_target;
+    c->sm_min = f.sm_min;
+    c->sm_max = f.sm_max;
+    c->weighted = f.particle_weights == 1 || f.sm_every > 0;
     c->nr = f.nr;
     c->nz = f.nz;
     c->NR = f.nr + 1;
@@ -497,8 +516,9 @@ int setup_cell(Cell* c) {
                 p.vt = c->alloc<double>(n);
                 p.vz = c->alloc<double>(n);
                 p.uid = c->alloc<uint32_t>(n);
-                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid;
-                c->pb[sp][b] = ParticleBuf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                p.w = c->weighted ? c->alloc<double>(n) : nullptr;
+                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid && (p.w || !c->weighted);
+                c->pb[sp][b] = ParticleBuf{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
             } else {
                 ParticleBuf& p = c->pb[sp][b];
                 p.cell = c->alloc<uint32_t>(n);
@@ -508,8 +528,9 @@ int setup_cell(Cell* c) {
                 p.vt = c->alloc<float>(n);
                 p.vz = c->alloc<float>(n);
                 p.uid = c->alloc<uint32_t>(n);
-                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid;
-                c->pd[sp][b] = PBuf<double>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                p.w = c->weighted ? c->alloc<float>(n) : nullptr;
+                ok = p.cell && p.dr && p.dz && p.vr && p.vt && p.vz && p.uid && (p.w || !c->weighted);
+                c->pd[sp][b] = PBuf<double>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
             }
             if (!ok) {
                 set_error("cudaMalloc failed for the particle store");
@@ -537,6 +558,20 @@ int setup_cell(Cell* c) {
     c->d_next_uid = c->alloc<uint32_t>(2);
     c->d_hist = c->alloc<uint32_t>((size_t)c->i_win * c->nr + 2);
     c->d_events = c->alloc<Event>(c->event_cap);
+    if (c->sm_every > 0) {
+        const size_t ncell = (size_t)c->i_win * c->nr;
+        const int64_t capmax = c->cap[0] > c->cap[1] ? c->cap[0] : c->cap[1];
+        c->d_sm_cnt = c->alloc<uint32_t>(ncell + 2);
+        c->d_sm_start = c->alloc<uint32_t>(ncell + 1);
+        c->d_sm_cursor = c->alloc<uint32_t>(ncell + 1);
+        c->d_sm_soff = c->alloc<uint32_t>(ncell + 1);
+        c->d_sm_list = c->alloc<int>(ncell + 1);
+        c->d_sm_perm = c->alloc<uint32_t>((size_t)capmax);
+        if (!c->d_sm_cnt || !c->d_sm_start || !c->d_sm_cursor || !c->d_sm_soff || !c->d_sm_list || !c->d_sm_perm) {
+            set_error("cudaMalloc failed for the split-merge buffers");
+            return PP_E_CUDA;
+        }
+    }
     c->d_phi = c->alloc<double>(c->nnodes);
     c->d_F = c->alloc<float>((size_t)c->i_win * c->nr * 20);
     c->d_rho = c->alloc<float>((size_t)2 * c->nnodes);

@@ -42,7 +42,8 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_trainer_create", "pp_trainer_load", "pp_trainer_gradients", "pp_trainer_epoch",
            "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy",
            "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune", "pp_set_harmonic_state",
-           "pp_get_harmonic_state"]
+           "pp_get_harmonic_state", "pp_set_particles_weighted", "pp_get_particle_weights",
+           "pp_get_control_counters"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -76,6 +77,9 @@ class PPConfig(C.Structure):
         ("plain_fp64", C.c_int32),
         ("implicit_es", C.c_int32),
         ("n_harmonics", C.c_int32),
+        ("see_gamma", C.c_double), ("see_t_ev", C.c_double),
+        ("particle_weights", C.c_int32),
+        ("sm_every", C.c_int32), ("sm_target", C.c_int32), ("sm_min", C.c_int32), ("sm_max", C.c_int32),
     ]
 
 
@@ -162,6 +166,9 @@ def _load():
         "pp_step_index": (C.c_int64, [V]),
         "pp_checkpoint": (I, [V, V, P(C.c_uint64)]),
         "pp_get_particles64": (I, [V, I, C.c_int64, P(C.c_int64), V, V, V, V, V, V, V, V]),
+        "pp_set_particles_weighted": (I, [V, I, C.c_int64, V, V, V, V, V, V, V, V]),
+        "pp_get_particle_weights": (I, [V, I, C.c_int64, P(C.c_int64), V, V]),
+        "pp_get_control_counters": (I, [V, V, V]),
         "pp_init_batch": (I, [V, I, P(V)]),
         "pp_mlp_forward": (I, [V, V, I, V]),
         "pp_ml_configure": (I, [V, V, D, I]),
@@ -292,6 +299,13 @@ def make_config(cfg, capacity=None, weight=None, poisson_max_iter=2, poisson_tol
     c.plain_fp64 = int(getattr(cfg, "plain_fp64", 0))
     c.implicit_es = int(getattr(cfg, "implicit_es", 0))
     c.n_harmonics = int(getattr(cfg, "n_harmonics", 1))
+    c.see_gamma = float(getattr(cfg, "see_gamma", 0.0))
+    c.see_t_ev = float(getattr(cfg, "see_t_ev", 2.0))
+    c.particle_weights = int(getattr(cfg, "particle_weights", 0))
+    c.sm_every = int(getattr(cfg, "sm_every", 0))
+    c.sm_target = int(getattr(cfg, "sm_target", 0))
+    c.sm_min = int(getattr(cfg, "sm_min", 0))
+    c.sm_max = int(getattr(cfg, "sm_max", 0))
     return c
 
 
@@ -450,13 +464,22 @@ class Cell:
     def step_index(self):
         return lib.pp_step_index(self.h)
 
+    @property
+    def weighted(self):
+        return bool(self.pcfg.particle_weights or self.pcfg.sm_every > 0)
+
     def set_particles(self, sp, p):
+        """p: dict of cell, dr, dz, vr, vt, vz, uid and, for a cell with
+        per-particle weights, optionally w (default 1)."""
         n = len(p["cell"])
         arr = {k: np.ascontiguousarray(p[k], dtype=np.uint32 if k in ("cell", "uid") else np.float32)
                for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")}
-        _check(lib.pp_set_particles(self.h, sp, n, *[_ptr(arr[k]) for k in
-                                                     ("cell", "dr", "dz", "vr", "vt", "vz", "uid")]),
-               "pp_set_particles")
+        args = [_ptr(arr[k]) for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")]
+        if "w" in p:
+            w = np.ascontiguousarray(p["w"], dtype=np.float64)
+            _check(lib.pp_set_particles_weighted(self.h, sp, n, *args, _ptr(w)), "pp_set_particles_weighted")
+        else:
+            _check(lib.pp_set_particles(self.h, sp, n, *args), "pp_set_particles")
 
     def get_particles(self, sp, cap=None, stream=0, dtype=np.float32):
         """Live particles of species sp; dtype float64 reads the state through
@@ -469,7 +492,14 @@ class Cell:
         fn = lib.pp_get_particles64 if dtype == np.float64 else lib.pp_get_particles
         _check(fn(self.h, sp, cap, C.byref(n), *[_ptr(out[k]) for k in ("cell", "dr", "dz", "vr", "vt", "vz", "uid")],
                   C.c_void_p(stream)), "pp_get_particles")
-        return {k: v[:n.value] for k, v in out.items()}
+        res = {k: v[:n.value] for k, v in out.items()}
+        if self.weighted:
+            w = np.empty(cap, np.float64)
+            m = C.c_int64()
+            _check(lib.pp_get_particle_weights(self.h, sp, cap, C.byref(m), _ptr(w), C.c_void_p(stream)),
+                   "pp_get_particle_weights")
+            res["w"] = w[:m.value]
+        return res
 
     def prime(self, stream=0):
         _check(lib.pp_prime(self.h, C.c_void_p(stream)), "pp_prime")
@@ -550,6 +580,13 @@ class Cell:
         keys = ["particle_steps", "absorbed", "created", "e_elastic", "e_excitation", "e_ionisation",
                 "i_cx", "i_isotropic", "nu_violations", "steps", "live_e", "live_i"]
         return dict(zip(keys, out.tolist()))
+
+    def control_counters(self, stream=0):
+        """Cumulative particle-control counters: secondary electrons emitted,
+        particles split, pairs merged, cells a pass left alone."""
+        out = np.zeros(4, np.int64)
+        _check(lib.pp_get_control_counters(self.h, _ptr(out), C.c_void_p(stream)), "pp_get_control_counters")
+        return dict(zip(["see", "split", "merged", "skipped"], out.tolist()))
 
 
 def _poisson_stats(self, stream=0):
