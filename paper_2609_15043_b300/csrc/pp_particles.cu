@@ -207,10 +207,9 @@ static_assert(kTileRows <= kPushThreads / 32, "one warp clears and flushes each 
 
 // shared-memory layout of one block (dynamic)
 struct PushSmem {
-    // cell, dr, dz, vr, vt, vz, uid, and the weights w with per-particle weights
-    static size_t bytes(int NR, bool weighted) {
-        const int arrays = weighted ? 8 : 7;
-        return sizeof(float) * kChunk * arrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
+    static constexpr int kArrays = 7;        // cell, dr, dz, vr, vt, vz, uid
+    static size_t bytes(int NR) {
+        return sizeof(float) * kChunk * kArrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
                256;
     }
 };
@@ -220,9 +219,11 @@ struct PushSmem {
 // thread advances kPPT consecutive particles (gather, Boris, current and
 // charge deposits accumulated in registers, move, boundaries, null test), the
 // few collision candidates are then processed densely, and bulk copies write
-// the six updated slices back.  W: per-particle relative weights (staged as
-// an eighth slice, read only); each particle's charge is then (q W_s) w.
-// Ions absorbed on a surface may emit a secondary electron (see_emit).
+// the six updated slices back.  W: per-particle relative weights, read
+// through the read-only cache (each thread's kPPT consecutive weights share
+// cache lines; staging them would cost the shared memory of the third block
+// per SM); each particle's charge is then (q W_s) w.  Ions absorbed on a
+// surface may emit a secondary electron (see_emit).
 template <bool W>
 __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -233,8 +234,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     float* s_vt = s_vr + kChunk;
     float* s_vz = s_vt + kChunk;
     uint32_t* s_uid = reinterpret_cast<uint32_t*>(s_vz + kChunk);
-    float* s_w = reinterpret_cast<float*>(s_uid + kChunk);          // used when W
-    float* t_rho = s_w + (W ? kChunk : 0);
+    float* t_rho = reinterpret_cast<float*>(s_uid + kChunk);
     float* t_jm = t_rho + kTileRows * a.NR;
     uint16_t* s_cand = reinterpret_cast<uint16_t*>(t_jm + kTileRows * a.NR);
     __shared__ __align__(8) uint64_t s_bar;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         // ---- stage the chunk (previous bulk stores must have read their smem)
         if (t == 0) {
             bulk_wait_read();
-            mbar_expect_tx(&s_bar, (W ? 8u : 7u) * bytes);
+            mbar_expect_tx(&s_bar, 7u * bytes);
             bulk_g2s(s_cell, P.cell + base, bytes, &s_bar);
             bulk_g2s(s_dr, P.dr + base, bytes, &s_bar);
             bulk_g2s(s_dz, P.dz + base, bytes, &s_bar);
@@ -298,7 +298,6 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bulk_g2s(s_vt, P.vt + base, bytes, &s_bar);
             bulk_g2s(s_vz, P.vz + base, bytes, &s_bar);
             bulk_g2s(s_uid, P.uid + base, bytes, &s_bar);
-            if (W) bulk_g2s(s_w, P.w + base, bytes, &s_bar);
             s_ncand = 0;
         }
         bool ok = mbar_wait(&s_bar, parity);
@@ -374,7 +373,12 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             const int ir0 = (int)cell - iz0 * nr;
             const float dr0 = s_dr[p], dz0 = s_dz[p];
             const float vr0 = s_vr[p], vt = s_vt[p], vz0 = s_vz[p];
-            const float wq = W ? S.qw * s_w[p] : S.qw;          // the particle's charge
+            const float wrel = W ? __ldg(P.w + base + p) : 1.0f;
+            const float wq = W ? S.qw * wrel : S.qw;            // the particle's charge
+            // the null-collision uniform depends only on (uid, step, species):
+            // drawn first, its integer rounds overlap the floating-point chain
+            const uint32_t rnull =
+                philox2x32_10(s_uid[p], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31), a.key0 ^ a.key1);
             if (cell != fcell) {
                 const float4* f = reinterpret_cast<const float4*>(a.F) + (size_t)cell * 5;
                 f0 = __ldg(f);
@@ -429,8 +433,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                 if (ce || cw || cd) {
                     bool emit = false;
                     if (sp == 1 && S.see_g > 0.0f)
-                        emit = see_emit(cc, step, S, s_uid[p], ce ? 0 : (cw ? 1 : 2), cell, dr0, dz0,
-                                        W ? s_w[p] : 1.0f);
+                        emit = see_emit(cc, step, S, s_uid[p], ce ? 0 : (cw ? 1 : 2), cell, dr0, dz0, wrel);
                     if (cd) {
                         const float qd = emit ? wq * 2.0f : wq;
                         float rpos = (float)irc + tr;
@@ -530,7 +533,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             bool emit = false;
             if (sp == 1 && S.see_g > 0.0f && (he || hw || hd))
                 emit = see_emit(cc, step, S, s_uid[p], he ? 0 : (hw ? 1 : 2), (uint32_t)(iz * nr + ir), dr, dz,
-                                W ? s_w[p] : 1.0f);
+                                wrel);
             if (hd) {
                 const float qd = emit ? wq * 2.0f : wq;
                 float rpos = (float)ir2 + drn;
@@ -547,9 +550,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                 dep_home(dq, dq2, tq, iz2, ir2, wq * (wa2 * wb2), wq * (drn * wb2), wq * (wa2 * dzn),
                          wq * (drn * dzn));
                 // null-collision test; candidates are processed densely below
-                uint32_t r = philox2x32_10(s_uid[p], (step & 0x7FFFFFFFu) | ((uint32_t)sp << 31),
-                                           a.key0 ^ a.key1);
-                if (u01(r) < S.pnull) {
+                if (u01(rnull) < S.pnull) {
                     int slot = atomicAdd(&s_ncand, 1);
                     s_cand[slot] = (uint16_t)p;
                 }
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
                 float vx = s_vr[p], vy = s_vt[p], vzz = s_vz[p];
                 if (sp == 0)
                     electron_collision(cc, step, S, s_uid[p], vx, vy, vzz, s_cell[p], s_dr[p], s_dz[p], pc,
-                                       W ? s_w[p] : 1.0f);
+                                       W ? __ldg(P.w + base + p) : 1.0f);
                 else
                     ion_collision(cc, step, S, s_uid[p], vx, vy, vzz, pc);
                 s_vr[p] = vx;
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
 
 void push_prepare(Cell* c) {
     if (c->push_blocks) return;
-    size_t shm = PushSmem::bytes(c->NR, c->weighted);
+    size_t shm = PushSmem::bytes(c->NR);
     cudaFuncSetAttribute(push_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(push_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     int dev = 0, nsm = 148, per = 1;
@@ -697,7 +698,7 @@ void launch_push(Cell* c, cudaStream_t st) {
     a.ev = c->d_events;
     a.ev_cap = c->event_cap;
     a.st = c->d_st;
-    size_t shm = PushSmem::bytes(c->NR, c->weighted);
+    size_t shm = PushSmem::bytes(c->NR);
     push_prepare(c);
     if (c->weighted)
         push_kernel<true><<<c->push_blocks, kPushThreads, shm, st>>>(a);
