@@ -332,7 +332,7 @@ def run_ours(args, cfg, ws, rank, local):
         tcell.prime(sh)
         tuned = tcell.autotune(args.autotune, sh)
         tcell.close()
-        cell.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"])
+        cell.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"], tuned["push_particles_per_thread"])
     if args.profile_steps:
         cell.advance_steps(args.profile_steps, sh)
         torch.cuda.synchronize()
@@ -521,7 +521,7 @@ def run_batch(args, ws, rank, local):
         tuned = tb.autotune(args.autotune, sh)
         tb.close()
         for c in batch.cells:
-            c.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"])
+            c.set_tuning(tuned["sort_every"], tuned["push_blocks_per_sm"], tuned["push_particles_per_thread"])
     for _ in range(args.warmup):
         batch.advance_period(1, sh)
     torch.cuda.synchronize()

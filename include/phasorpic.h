@@ -620,7 +620,9 @@ int pp_get_phase_times(pp_cell* cell, double* ms, int64_t* counts);
  * never the physics: the counting-sort cadence of each species (steps between
  * sorts; the store drifts out of cell order between sorts, which costs the
  * particle kernel's deposits, while a sort costs a pass over the store), and
- * the resident blocks per SM of the persistent particle kernel.  A period
+ * the resident blocks per SM of the persistent particle kernel, and its tile
+ * shape: the particles each thread advances per chunk (4, 8 or 16; a chunk is
+ * 256 times that, staged in shared memory as one unit).  A period
  * graph is replayed only when each cadence divides N_RF an even number of
  * times; other cadences run the step loop.  The tuning is not part of
  * pp_config or of a checkpoint; a new cell starts from pp_config.sort_every
@@ -629,16 +631,18 @@ int pp_get_phase_times(pp_cell* cell, double* ms, int64_t* counts);
 typedef struct pp_tuning {
     int32_t sort_every[2];           /* sort cadence (steps) of electrons, ions; >= 1 */
     int32_t push_blocks_per_sm;      /* blocks per SM of the particle kernel; 0 = as many as fit */
-    int32_t reserved0;
+    int32_t push_particles_per_thread; /* 4, 8 or 16 (0 = 8): the particle kernel's chunk shape */
 } pp_tuning;
 
 int pp_get_tuning(pp_cell* cell, pp_tuning* out);
-/* PP_E_ARG unless both cadences are >= 1 and the block count >= 0. */
+/* PP_E_ARG unless both cadences are >= 1, the block count >= 0 and the
+ * particles per thread one of 0, 4, 8, 16. */
 int pp_set_tuning(pp_cell* cell, const pp_tuning* t);
 
 /*
- * pp_autotune -- coordinate descent over the blocks per SM (1 .. as many as
- * fit; skipped for the plain FP64 form), the electron cadence (graph-capable
+ * pp_autotune -- coordinate descent over the particle kernel's tile shape
+ * (4, 8, 16 particles per thread) and its blocks per SM (1 .. as many as fit;
+ * both skipped for the plain FP64 form), the electron cadence (graph-capable
  * divisors of N_RF in [2, 40]) and the ion cadence (in [10, 200]).  Each
  * candidate runs one period, then is timed over trial_periods periods with
  * CUDA events on `stream` and ranked by time per particle-step (time per

@@ -869,6 +869,7 @@ static void apply_tuning(Cell* c, const pp_tuning& t) {
     c->sort_every[0] = t.sort_every[0];
     c->sort_every[1] = t.sort_every[1];
     c->push_per_sm = t.push_blocks_per_sm;
+    c->push_ppt = t.push_particles_per_thread;
     c->push_blocks = 0;                          // recomputed by push_prepare
     c->graph_cur[0] = c->graph_cur[1] = -1;      // re-capture the period graph
 }
@@ -898,13 +899,20 @@ static int batch_advance(Batch* b, int n_periods, cudaStream_t st) {
 static int autotune(std::vector<Cell*>& cells, const std::function<int(int)>& advance, int trial, cudaStream_t st,
                     pp_tuning* chosen, double* ms_out) {
     for (Cell* c : cells) push_prepare(c);
-    pp_tuning best{{cells[0]->sort_every[0], cells[0]->sort_every[1]}, cells[0]->push_per_sm, 0};
-    int max_per_sm = cells[0]->push_per_sm_max;
+    pp_tuning best{{cells[0]->sort_every[0], cells[0]->sort_every[1]}, cells[0]->push_per_sm,
+                   cells[0]->push_ppt > 0 ? cells[0]->push_ppt : kPPT};
     bool fp64 = true;
-    for (Cell* c : cells) {
-        max_per_sm = std::min(max_per_sm, c->push_per_sm_max);
-        fp64 = fp64 && c->fp64;
-    }
+    for (Cell* c : cells) fp64 = fp64 && c->fp64;
+    // blocks per SM that fit with the cells' current tile shape
+    auto fit_per_sm = [&]() {
+        int m = 1 << 30;
+        for (Cell* c : cells) {
+            push_prepare(c);
+            m = std::min(m, c->push_per_sm_max);
+        }
+        return m;
+    };
+    int max_per_sm = fit_per_sm();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -944,17 +952,32 @@ static int autotune(std::vector<Cell*>& cells, const std::function<int(int)>& ad
     };
     double best_ms = 0, best_cost = 0;
     int rc = measure(best, &best_ms, &best_cost);
-    std::vector<std::vector<int>> cand(3);
-    if (!fp64)
-        for (int k = 1; k <= max_per_sm; ++k) cand[0].push_back(k);
-    cand[1] = cadences(cells, 2, 40);
-    cand[2] = cadences(cells, 10, 200);
-    for (int knob = 0; knob < 3 && rc == PP_OK; ++knob) {
+    // knobs: 0 tile shape (as many blocks as fit), 1 blocks per SM, 2 and 3
+    // the sort cadences
+    std::vector<std::vector<int>> cand(4);
+    if (!fp64) cand[0] = {4, 8, 16};
+    cand[2] = cadences(cells, 2, 40);
+    cand[3] = cadences(cells, 10, 200);
+    for (int knob = 0; knob < 4 && rc == PP_OK; ++knob) {
+        if (knob == 1 && !fp64) {
+            // the blocks that fit depend on the chosen tile shape
+            for (Cell* c : cells) apply_tuning(c, best);
+            max_per_sm = fit_per_sm();
+            for (int k = 1; k <= max_per_sm; ++k) cand[1].push_back(k);
+        }
         const pp_tuning inc = best;
         for (int v : cand[knob]) {
             pp_tuning t = inc;
-            int* field = knob == 0 ? &t.push_blocks_per_sm : &t.sort_every[knob - 1];
-            const int cur = knob == 0 ? (inc.push_blocks_per_sm > 0 ? inc.push_blocks_per_sm : max_per_sm) : *field;
+            int* field = knob == 0   ? &t.push_particles_per_thread
+                         : knob == 1 ? &t.push_blocks_per_sm
+                                     : &t.sort_every[knob - 2];
+            int cur = *field;
+            if (knob == 0) {
+                cur = inc.push_particles_per_thread > 0 ? inc.push_particles_per_thread : kPPT;
+                t.push_blocks_per_sm = 0;
+            } else if (knob == 1) {
+                cur = inc.push_blocks_per_sm > 0 ? inc.push_blocks_per_sm : max_per_sm;
+            }
             if (v == cur) continue;
             *field = v;
             double ms = 0, cost = 0;
@@ -986,14 +1009,17 @@ int pp_get_tuning(pp_cell* h, pp_tuning* out) {
         set_error("bad argument to pp_get_tuning");
         return PP_E_ARG;
     }
-    *out = pp_tuning{{c->sort_every[0], c->sort_every[1]}, c->push_per_sm, 0};
+    *out = pp_tuning{{c->sort_every[0], c->sort_every[1]}, c->push_per_sm, c->push_ppt > 0 ? c->push_ppt : kPPT};
     return PP_OK;
 }
 
 int pp_set_tuning(pp_cell* h, const pp_tuning* t) {
     Cell* c = reinterpret_cast<Cell*>(h);
-    if (!c || !t || t->sort_every[0] < 1 || t->sort_every[1] < 1 || t->push_blocks_per_sm < 0) {
-        set_error("bad argument to pp_set_tuning (sort cadences >= 1, blocks per SM >= 0)");
+    const int ppt = t ? t->push_particles_per_thread : 0;
+    if (!c || !t || t->sort_every[0] < 1 || t->sort_every[1] < 1 || t->push_blocks_per_sm < 0 ||
+        !(ppt == 0 || ppt == 4 || ppt == 8 || ppt == 16)) {
+        set_error("bad argument to pp_set_tuning (sort cadences >= 1, blocks per SM >= 0, "
+                  "particles per thread 0, 4, 8 or 16)");
         return PP_E_ARG;
     }
     apply_tuning(c, *t);

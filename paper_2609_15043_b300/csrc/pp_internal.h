@@ -31,8 +31,9 @@ constexpr int kPushThreads = 256;
 #ifndef PP_PUSH_MINB
 #define PP_PUSH_MINB 3
 #endif
-constexpr int kPPT = PP_PPT;                      // particles per thread per chunk (power of two)
-constexpr int kChunk = kPushThreads * kPPT;
+constexpr int kPPT = PP_PPT;                      // default particles per thread per chunk (power of two)
+constexpr int kPptMax = 16;                       // largest tile the particle kernel is built for
+constexpr int kChunk = kPushThreads * kPptMax;    // particle storage is padded to whole chunks of this size
 constexpr int kTileRows = 8;                      // node rows of the shared deposit tile
 constexpr int kMaxNR = 513;                       // node columns supported by the tile
 constexpr int kEventMin = 8192;                   // ionisation events per step, at least
@@ -197,6 +198,7 @@ struct Cell {
     int sort_every[2] = {1, 1};
     int push_per_sm = 0;
     int push_per_sm_max = 0;
+    int push_ppt = 0;                       // particles per thread of the particle kernel's chunks (0: kPPT)
 
     // host-side geometry and circuit
     std::vector<std::vector<int>> turn_nodes;     // full node indices per turn

@@ -17,7 +17,7 @@ namespace pp {
 // ---------------------------------------------------------------- TMA bulk copies
 // 1-D bulk copies between global and shared memory (cp.async.bulk), completed
 // through an mbarrier transaction count; sizes and addresses are multiples of
-// 16 bytes (chunk bases are multiples of kChunk elements; storage is padded).
+// 16 bytes (chunk bases are multiples of the chunk size; storage is padded).
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -208,33 +208,37 @@ static_assert(kTileRows <= kPushThreads / 32, "one warp clears and flushes each 
 // shared-memory layout of one block (dynamic)
 struct PushSmem {
     static constexpr int kArrays = 7;        // cell, dr, dz, vr, vt, vz, uid
-    static size_t bytes(int NR) {
-        return sizeof(float) * kChunk * kArrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * kChunk +
-               256;
+    static size_t bytes(int NR, int ppt) {
+        const size_t ch = (size_t)kPushThreads * ppt;
+        return sizeof(float) * ch * kArrays + sizeof(float) * 2 * kTileRows * NR + sizeof(uint16_t) * ch + 256;
     }
 };
 
-// One block owns a chunk of kChunk consecutive particles of one species at a
+// One block owns a chunk of 256 PPT consecutive particles of one species at a
 // time: TMA bulk copies bring the seven SoA slices into shared memory, each
-// thread advances kPPT consecutive particles (gather, Boris, current and
+// thread advances PPT consecutive particles (gather, Boris, current and
 // charge deposits accumulated in registers, move, boundaries, null test), the
 // few collision candidates are then processed densely, and bulk copies write
 // the six updated slices back.  W: per-particle relative weights, read
-// through the read-only cache (each thread's kPPT consecutive weights share
+// through the read-only cache (each thread's PPT consecutive weights share
 // cache lines; staging them would cost the shared memory of the third block
 // per SM); each particle's charge is then (q W_s) w.  Ions absorbed on a
 // surface may emit a secondary electron (see_emit).
-template <bool W>
+// PPT (particles per thread, a power of two up to 16) sets the chunk, the
+// tile shape the autotuner chooses.
+template <bool W, int PPT>
 __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
+    constexpr int kCh = kPushThreads * PPT;
+    static_assert(PPT >= 1 && PPT <= kPptMax && (PPT & (PPT - 1)) == 0, "PPT: a power of two up to kPptMax");
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t* s_cell = reinterpret_cast<uint32_t*>(smem);
-    float* s_dr = reinterpret_cast<float*>(s_cell + kChunk);
-    float* s_dz = s_dr + kChunk;
-    float* s_vr = s_dz + kChunk;
-    float* s_vt = s_vr + kChunk;
-    float* s_vz = s_vt + kChunk;
-    uint32_t* s_uid = reinterpret_cast<uint32_t*>(s_vz + kChunk);
-    float* t_rho = reinterpret_cast<float*>(s_uid + kChunk);
+    float* s_dr = reinterpret_cast<float*>(s_cell + kCh);
+    float* s_dz = s_dr + kCh;
+    float* s_vr = s_dz + kCh;
+    float* s_vt = s_vr + kCh;
+    float* s_vz = s_vt + kCh;
+    uint32_t* s_uid = reinterpret_cast<uint32_t*>(s_vz + kCh);
+    float* t_rho = reinterpret_cast<float*>(s_uid + kCh);
     float* t_jm = t_rho + kTileRows * a.NR;
     uint16_t* s_cand = reinterpret_cast<uint16_t*>(t_jm + kTileRows * a.NR);
     __shared__ __align__(8) uint64_t s_bar;
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     __shared__ unsigned s_pc[6];            // collision-pass tallies of the block
 
     const int n0 = a.nslot[0], n1 = a.nslot[1];
-    const int ce = (n0 + kChunk - 1) / kChunk, ci = (n1 + kChunk - 1) / kChunk;
+    const int ce = (n0 + kCh - 1) / kCh, ci = (n1 + kCh - 1) / kCh;
     const int nr = a.nr, NR = a.NR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x;
@@ -280,9 +284,9 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         const int chunk = s_chunk;
         if (chunk >= ce + ci) break;
         const int sp = chunk < ce ? 0 : 1;
-        const int base = (chunk - (sp ? ce : 0)) * kChunk;
+        const int base = (chunk - (sp ? ce : 0)) * kCh;
         const int n = sp ? n1 : n0;
-        const int nact = min(kChunk, n - base);
+        const int nact = min(kCh, n - base);
         const ParticleBuf P = a.p[sp];
         const SpeciesConst S = a.sp[sp];
         const uint32_t bytes = (uint32_t)((nact * 4 + 15) & ~15);
@@ -359,13 +363,13 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         DepAcc dq2{-1, 0, 0.f, 0.f, 0.f, 0.f};
         uint32_t fcell = kDead;
         float4 f0, f1, f2, f3, f4;
-        // thread t owns particles t*kPPT .. t*kPPT + kPPT-1 and visits them
-        // starting at offset t/(32/kPPT): the 32 lanes of a warp then hit 32
+        // thread t owns particles t*PPT .. t*PPT + PPT-1 and visits them
+        // starting at offset t/(32/PPT): the 32 lanes of a warp then hit 32
         // different banks
-        const int p0 = t * kPPT, rot = (t / (32 / kPPT)) & (kPPT - 1);
+        const int p0 = t * PPT, rot = (t / (32 / PPT)) & (PPT - 1);
 #pragma unroll 1
-        for (int k = 0; k < kPPT; ++k) {
-            const int p = p0 + ((k + rot) & (kPPT - 1));
+        for (int k = 0; k < PPT; ++k) {
+            const int p = p0 + ((k + rot) & (PPT - 1));
             if (p >= nact) continue;
             const uint32_t cell = s_cell[p];
             if (cell == kDead) continue;
@@ -657,18 +661,32 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
     }
 }
 
+using PushFn = void (*)(PushArgs);
+
+static int push_ppt(const Cell* c) { return c->push_ppt > 0 ? c->push_ppt : kPPT; }
+
+template <bool W>
+static PushFn push_fn_w(int ppt) {
+    switch (ppt) {
+        case 4: return push_kernel<W, 4>;
+        case 16: return push_kernel<W, 16>;
+        default: return push_kernel<W, 8>;
+    }
+}
+
+static PushFn push_fn(const Cell* c) {
+    return c->weighted ? push_fn_w<true>(push_ppt(c)) : push_fn_w<false>(push_ppt(c));
+}
+
 void push_prepare(Cell* c) {
     if (c->push_blocks) return;
-    size_t shm = PushSmem::bytes(c->NR);
-    cudaFuncSetAttribute(push_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(push_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const size_t shm = PushSmem::bytes(c->NR, push_ppt(c));
+    const PushFn fn = push_fn(c);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     int dev = 0, nsm = 148, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (c->weighted)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel<true>, kPushThreads, shm);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel<false>, kPushThreads, shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kPushThreads, shm);
     per = per < 1 ? 1 : per;
     c->push_per_sm_max = per;
     c->push_blocks = nsm * ((c->push_per_sm > 0 && c->push_per_sm < per) ? c->push_per_sm : per);
@@ -698,12 +716,9 @@ void launch_push(Cell* c, cudaStream_t st) {
     a.ev = c->d_events;
     a.ev_cap = c->event_cap;
     a.st = c->d_st;
-    size_t shm = PushSmem::bytes(c->NR);
+    const size_t shm = PushSmem::bytes(c->NR, push_ppt(c));
     push_prepare(c);
-    if (c->weighted)
-        push_kernel<true><<<c->push_blocks, kPushThreads, shm, st>>>(a);
-    else
-        push_kernel<false><<<c->push_blocks, kPushThreads, shm, st>>>(a);
+    push_fn(c)<<<c->push_blocks, kPushThreads, shm, st>>>(a);
     count_launch();
 }
 

@@ -111,7 +111,8 @@ class PPRecord(C.Structure):
 
 
 class PPTuning(C.Structure):
-    _fields_ = [("sort_every", C.c_int32 * 2), ("push_blocks_per_sm", C.c_int32), ("reserved0", C.c_int32)]
+    _fields_ = [("sort_every", C.c_int32 * 2), ("push_blocks_per_sm", C.c_int32),
+                ("push_particles_per_thread", C.c_int32)]
 
 
 class PPVacuumProblem(C.Structure):
@@ -349,7 +350,8 @@ def mlp_forward(params, feats):
 
 def _tuning_dict(t):
     return {"sort_every": [int(t.sort_every[0]), int(t.sort_every[1])],
-            "push_blocks_per_sm": int(t.push_blocks_per_sm)}
+            "push_blocks_per_sm": int(t.push_blocks_per_sm),
+            "push_particles_per_thread": int(t.push_particles_per_thread)}
 
 
 _LAYER_ROWS = (256, 256, 256, 32)
@@ -668,11 +670,12 @@ def _get_tuning(self):
     return _tuning_dict(t)
 
 
-def _set_tuning(self, sort_every=None, push_blocks_per_sm=None):
+def _set_tuning(self, sort_every=None, push_blocks_per_sm=None, push_particles_per_thread=None):
     cur = self.tuning()
     se = cur["sort_every"] if sort_every is None else list(sort_every)
     pb = cur["push_blocks_per_sm"] if push_blocks_per_sm is None else push_blocks_per_sm
-    t = PPTuning((C.c_int32 * 2)(int(se[0]), int(se[1])), int(pb), 0)
+    pt = cur["push_particles_per_thread"] if push_particles_per_thread is None else push_particles_per_thread
+    t = PPTuning((C.c_int32 * 2)(int(se[0]), int(se[1])), int(pb), int(pt))
     _check(lib.pp_set_tuning(self.h, C.byref(t)), "pp_set_tuning")
 
 

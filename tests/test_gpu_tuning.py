@@ -1,6 +1,7 @@
 """Run-time tuning (pp_get_tuning / pp_set_tuning / pp_autotune /
-pp_batch_autotune): the knobs round-trip and are validated, a different
-tuning leaves the physics unchanged (cells whose periods are deterministic up
+pp_batch_autotune): the knobs (sort cadences, blocks per SM and the particle
+kernel's tile shape, particles per thread) round-trip and are validated, a
+different tuning leaves the physics unchanged (cells whose periods are deterministic up
 to float-atomic order give the same records), and the tuner returns a valid
 tuning, leaves the cell on it and the cell keeps running."""
 import numpy as np
@@ -21,14 +22,18 @@ def test_tuning_roundtrip_and_validation():
     cfg = workloads.small()
     g = gpu_cell(cfg, [workloads.population(cfg, sp) for sp in (0, 1)])
     t = g.tuning()
-    assert t == {"sort_every": [cfg.sort_every_e, cfg.sort_every_i], "push_blocks_per_sm": 0}
-    g.set_tuning(sort_every=(4, 25), push_blocks_per_sm=1)
-    assert g.tuning() == {"sort_every": [4, 25], "push_blocks_per_sm": 1}
+    assert t == {"sort_every": [cfg.sort_every_e, cfg.sort_every_i], "push_blocks_per_sm": 0,
+                 "push_particles_per_thread": 8}
+    g.set_tuning(sort_every=(4, 25), push_blocks_per_sm=1, push_particles_per_thread=16)
+    want = {"sort_every": [4, 25], "push_blocks_per_sm": 1, "push_particles_per_thread": 16}
+    assert g.tuning() == want
     with pytest.raises(pp.PhasorPICError):
         g.set_tuning(sort_every=(0, 25))
     with pytest.raises(pp.PhasorPICError):
         g.set_tuning(push_blocks_per_sm=-1)
-    assert g.tuning() == {"sort_every": [4, 25], "push_blocks_per_sm": 1}
+    with pytest.raises(pp.PhasorPICError):
+        g.set_tuning(push_particles_per_thread=5)
+    assert g.tuning() == want
     g.advance_steps(3)
     with pytest.raises(pp.PhasorPICError):       # not on a period boundary
         g.autotune(1)
@@ -50,7 +55,8 @@ def test_tuning_leaves_the_physics_unchanged():
     cfg = base.replace(nr=48, nz=72, seed=base.seed + 1, pressure_pa=0.0)
     pops = [{k: v[:0] for k, v in workloads.population(cfg, 0).items()}, workloads.population(cfg, 1)]
     recs = []
-    for tuning in (None, dict(sort_every=(4, 10), push_blocks_per_sm=1)):
+    for tuning in (None, dict(sort_every=(4, 10), push_blocks_per_sm=1), dict(push_particles_per_thread=4),
+                   dict(push_particles_per_thread=16, push_blocks_per_sm=1)):
         g = gpu_cell(cfg, pops)
         if tuning:
             g.set_tuning(**tuning)
@@ -58,10 +64,11 @@ def test_tuning_leaves_the_physics_unchanged():
         recs.append((g.turn_phasors(), g.counters()["live_i"]))
         assert g.status() == 0
         g.close()
-    (ra, la), (rb, lb) = recs
-    assert la == lb
-    for k in ("icap", "qhat", "x_next", "vp"):
-        assert _rel(rb[k], ra[k]) < 1e-5, k
+    ra, la = recs[0]
+    for rb, lb in recs[1:]:
+        assert la == lb
+        for k in ("icap", "qhat", "x_next", "vp"):
+            assert _rel(rb[k], ra[k]) < 1e-5, k
 
 
 def test_autotune_cell_and_batch():
@@ -74,7 +81,9 @@ def test_autotune_cell_and_batch():
     assert t["sort_every"][0] in _valid_cadences(n_rf, 2, 40) + [cfg.sort_every_e]
     assert t["sort_every"][1] in _valid_cadences(n_rf, 10, 200) + [cfg.sort_every_i]
     assert 0 <= t["push_blocks_per_sm"] <= 8 and t["ms_per_period"] > 0
-    assert {k: t[k] for k in ("sort_every", "push_blocks_per_sm")} == g.tuning()
+    assert t["push_particles_per_thread"] in (4, 8, 16)
+    keys = ("sort_every", "push_blocks_per_sm", "push_particles_per_thread")
+    assert {k: t[k] for k in keys} == g.tuning()
     periods = g.step_index // n_rf
     assert g.step_index % n_rf == 0 and periods >= 2
     g.advance_period(1)
@@ -88,7 +97,7 @@ def test_autotune_cell_and_batch():
             c.set_particles(sp, workloads.population(cf, sp))
     tb = batch.autotune(trial_periods=1)
     for c in batch.cells:
-        assert c.tuning() == {k: tb[k] for k in ("sort_every", "push_blocks_per_sm")}
+        assert c.tuning() == {k: tb[k] for k in keys}
     batch.advance_period(1)
     for c in batch.cells:
         assert c.turn_phasors()["accepted"]
