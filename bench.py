@@ -59,6 +59,8 @@ def parse():
                     help="workload of the time-to-stationary part of the default run")
     ap.add_argument("--tts-periods", type=int, default=400, help="cap of that part (periods per form)")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-stationary part")
+    ap.add_argument("--no-fp64-error", action="store_true",
+                    help="skip the fused-against-FP64 error report of the bench workload")
     ap.add_argument("--form", default="fused", choices=["fused", "fp64"],
                     help="particle form: the fused FP32 kernel or the plain FP64 form")
     ap.add_argument("--time-to-stationary", action="store_true",
@@ -466,6 +468,9 @@ def run_ours(args, cfg, ws, rank, local):
     cell.close()
     del cell
     torch.cuda.empty_cache()
+    if ws == 1 and args.form == "fused" and not args.no_fp64_error:
+        line["config"]["fp64_error"] = fp64_error(cfg, sh)
+        torch.cuda.empty_cache()
     if ws == 1 and not args.no_tts:
         # the second half of the metric: periods and wall time to a stationary
         # state for the fused FP32 and the plain FP64 form, from the same
@@ -638,6 +643,74 @@ def stationary_runs(cfg, forms, max_periods, ml_weights=None, alpha_ml=1.0):
         del cell
         torch.cuda.empty_cache()
     return out, traces
+
+
+def fp64_error(cfg, sh):
+    """Error of the fused FP32 path against FP64 on the bench workload: the
+    fused cell and the plain FP64 cell (FP64 particle state, parity-tested
+    against the FP64 oracle) start from the same seeded populations and draw
+    the same collision numbers; after one PIC step their particles are
+    compared by uid (offsets in cells, velocities relative to each component's
+    scale), after the first RF period their records (phasors, powers, live
+    counts).  The trajectories decorrelate within a few periods (chaotic
+    particle dynamics), so the period-level errors are those of one period."""
+    from paper_2609_15043_b300 import phasorpic as pp, workloads
+    got = {}
+    for form in ("fused", "fp64"):
+        c = cfg.replace(plain_fp64=1 if form == "fp64" else 0)
+        cell = pp.Cell(c)
+        for sp in (0, 1):
+            cell.set_particles(sp, workloads.population(c, sp))
+        cell.prime(sh)
+        cell.advance_steps(1, sh)
+        parts = []
+        for sp in (0, 1):
+            p = cell.get_particles(sp, dtype=np.float64)
+            o = np.argsort(p["uid"])
+            parts.append({k: v[o] for k, v in p.items()})
+        cell.advance_steps(cell.n_rf - 1, sh)
+        got[form] = (parts, cell.turn_phasors(sh))
+        cell.close()
+        del cell
+    (pa, ra), (pb, rb) = got["fused"], got["fp64"]
+    step = {"same_cell_fraction": 0.0}
+    dmax = {k: 0.0 for k in ("dr", "dz", "vr", "vt", "vz")}
+    vrel = []
+    same = tot = 0
+    for sp in (0, 1):
+        common, ia, ib = np.intersect1d(pa[sp]["uid"], pb[sp]["uid"], assume_unique=True, return_indices=True)
+        eq = pa[sp]["cell"][ia] == pb[sp]["cell"][ib]
+        same += int(np.count_nonzero(eq))
+        tot += max(len(pb[sp]["uid"]), 1)
+        for k in dmax:
+            x, y = pa[sp][k][ia][eq], pb[sp][k][ib][eq]
+            if not len(y):
+                continue
+            if k in ("dr", "dz"):
+                e = np.abs(x - y)
+            else:
+                e = np.abs(x - y) / np.maximum(np.abs(y), 1e-3 * np.max(np.abs(y)))
+                vrel.append(e)
+            dmax[k] = max(dmax[k], float(np.max(e)))
+    step["same_cell_fraction"] = same / tot
+    step["max_abs_offset_cells"] = max(dmax["dr"], dmax["dz"])
+    step["max_rel_velocity"] = max(dmax["vr"], dmax["vt"], dmax["vz"])
+    # the largest differences come from the few particles that collided in
+    # the step (scattering angles and energies evaluated in FP32 against FP64)
+    if vrel:
+        v = np.concatenate(vrel)
+        step["rel_velocity_quantiles"] = {"median": float(np.median(v)), "q0.999": float(np.quantile(v, 0.999)),
+                                          "q0.99999": float(np.quantile(v, 0.99999))}
+
+    def rel(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
+    period = {k: rel(ra[k], rb[k]) for k in ("vp", "icap", "qhat", "x_next")}
+    for k in ("p_port", "p_ind", "p_cap", "p_cap_ph", "p_cu", "p_es"):
+        period[k] = float(abs(ra[k] - rb[k]) / max(abs(rb[k]), 1e-300))
+    period["n_live"] = rel(ra["n_live"], rb["n_live"])
+    return {"against": "plain FP64 form (FP64 particle state; parity with the FP64 oracle to 1e-9 per step)",
+            "step1": step, "period1_rel": period}
 
 
 def same_accuracy(out, traces, a="fused", b="fp64"):
