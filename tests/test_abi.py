@@ -77,6 +77,13 @@ def test_config_validation_phase_closure():
     (dict(plain_fp64=2), "plain_fp64"),
     (dict(n_harmonics=5), "n_harmonics"),
     (dict(n_harmonics=-1), "n_harmonics"),
+    (dict(see_gamma=1.5), "see_gamma"),
+    (dict(see_gamma=0.1, see_t_ev=0.0), "see_t_ev"),
+    (dict(particle_weights=2), "particle_weights"),
+    (dict(sm_every=-1), "sm_every"),
+    (dict(sm_every=5), "split-merge needs"),
+    (dict(sm_every=5, sm_target=10, sm_min=20, sm_max=30), "split-merge needs"),
+    (dict(sm_every=5, sm_target=40, sm_min=20, sm_max=30), "split-merge needs"),
     (dict(z_coil=0.128), "coil turn nodes must lie above"),
     (dict(nr=128, nz=192, turn_r=[0.05], winding=[1], wire_radius=0.008), "too many turn nodes"),
 ])
@@ -115,6 +122,9 @@ def test_trainer_and_tuning_arguments_are_checked_before_the_device():
     assert lib.pp_set_tuning(None, None) == -7
     assert lib.pp_autotune(None, 1, None, None, None) == -7
     assert lib.pp_batch_autotune(None, 1, None, None, None) == -7
+    assert lib.pp_get_control_counters(None, None, None) == -7
+    assert lib.pp_get_particle_weights(None, 0, 0, None, None, None) == -7
+    assert lib.pp_set_particles_weighted(None, 0, 0, None, None, None, None, None, None, None, None) == -7
 
 
 def test_vacuum_problem_is_validated_before_the_device():
