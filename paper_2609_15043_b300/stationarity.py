@@ -17,6 +17,14 @@ window of W periods ending at n:
 Quantities whose window mean is below `floor` times the largest power (or
 phasor magnitude) are exempt from the relative drift test: a relative test
 on a mean that is zero up to noise never passes.
+
+With plasma_drift = False the drift test covers the circuit state only, not
+the four powers: the state then counts as stationary when the power balance
+holds within tol_bal (the coupled field-circuit state is converged), the
+controller holds P_port and the circuit phasors have settled, while the
+plasma's particle inventory may still relax on ion time scales (a density
+set by the initial load that the target power cannot sustain decays over
+thousands of periods).
 """
 from dataclasses import dataclass
 from typing import Optional
@@ -31,6 +39,7 @@ class StationarityCriteria:
     tol_bal: float = 0.005
     tol_drift: float = 0.005
     floor: float = 1e-3
+    plasma_drift: bool = True
 
 
 def _drift(series, floor_abs):
@@ -94,5 +103,5 @@ class StationarityMonitor:
         drift_x = _drift(X, self.c.floor * max(np.max(X.mean(axis=0)), 1e-300))
         err_p = abs(p_port - self.p_target) / self.p_target if self.p_target else 0.0
         self.last = dict(periods=len(self.rows), err_p=err_p, bal=bal, drift_p=drift_p, drift_x=drift_x)
-        return err_p <= self.c.tol_p and bal <= self.c.tol_bal and drift_p <= self.c.tol_drift and \
-            drift_x <= self.c.tol_drift
+        return err_p <= self.c.tol_p and bal <= self.c.tol_bal and \
+            (drift_p <= self.c.tol_drift or not self.c.plasma_drift) and drift_x <= self.c.tol_drift

@@ -59,3 +59,21 @@ def test_window_must_fill_first():
     m = StationarityMonitor(3, p_target=60.0, criteria=StationarityCriteria(window=10))
     flags = [m.update(rec) for _ in range(12)]
     assert flags[:9] == [False] * 9 and flags[9] and m.stationary_at == 9
+
+
+def test_balance_criterion_lets_the_plasma_powers_drift():
+    """P_port held at the target and the circuit state constant while the
+    plasma slowly trades inductive for copper power (a decaying density):
+    the balance holds in every period, so the balance criterion is met once
+    a window has passed, while the full criterion (plasma powers settled)
+    is not; an imbalance fails both."""
+    recs = []
+    for k in range(300):
+        pind = 10.0 * np.exp(-k / 400.0)
+        recs.append(_rec(60.0, pind, 0.2, 60.0 - pind - 0.2, [3.0, 2.9, 2.8, 2.7, 100.0, 90.0, 80.0]))
+    full = StationarityMonitor(3, p_target=60.0)
+    bal = StationarityMonitor(3, p_target=60.0, criteria=StationarityCriteria(plasma_drift=False))
+    assert not any(full.update(r) for r in recs)
+    assert any(bal.update(r) for r in recs) and bal.stationary_at == 99
+    bad = StationarityMonitor(3, p_target=60.0, criteria=StationarityCriteria(plasma_drift=False))
+    assert not any(bad.update(dict(r, p_cu=r["p_cu"] * 1.02)) for r in recs)
