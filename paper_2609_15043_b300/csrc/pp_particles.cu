@@ -225,8 +225,9 @@ struct PushSmem {
 // per SM); each particle's charge is then (q W_s) w.  Ions absorbed on a
 // surface may emit a secondary electron (see_emit).
 // PPT (particles per thread, a power of two up to 16) sets the chunk, the
-// tile shape the autotuner chooses.
-template <bool W, int PPT>
+// tile shape the autotuner chooses; IMPL selects the direct-implicit form at
+// compile time.
+template <bool W, int PPT, bool IMPL>
 __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushArgs a) {
     constexpr int kCh = kPushThreads * PPT;
     static_assert(PPT >= 1 && PPT <= kPptMax && (PPT & (PPT - 1)) == 0, "PPT: a power of two up to kPptMax");
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
         }
         // the implicit correction moves a particle by less than a cell: the
         // tile then spans one more row and column on each side
-        const int pad = a.implicit;
+        const int pad = IMPL ? 1 : 0;
         const int tlo = max(bmin - 1 - pad, 0);
         const int thi = min(bmax + 2 + pad, a.i_win);
         const int trows = (bmax < 0) ? 0 : min(thi - tlo + 1, kTileRows);
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             float Bz = w00 * f4.x + w01 * f4.y + w10 * f4.z + w11 * f4.w;
             int ir = ir0, iz = iz0;
             float dr = dr0, dz = dz0, vr = vr0, vz = vz0;
-            if (a.implicit) {
+            if (IMPL) {
                 // the previous step's implicit kick with E^s at the predicted
                 // position: v += (q/m) dt E, x += (q/m) dt^2 E (cells), a pass
                 // through the axis reflects, leaving the plasma region absorbs
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kPushThreads, PP_PUSH_MINB) push_kernel(PushAr
             float vbz = (vz + vnz) * 0.5f;
             float jmv = wq * vbt;
             acc_ind = __fmaf_rn(jmv, Et, acc_ind);
-            if (!a.implicit) acc_es = __fmaf_rn(wq, __fmaf_rn(vbr, Er, vbz * Ez), acc_es);
+            if (!IMPL) acc_es = __fmaf_rn(wq, __fmaf_rn(vbr, Er, vbz * Ez), acc_es);
             ++cnt[0];
             dep_run(dj, tj, iz, ir, jmv * w00, jmv * w01, jmv * w10, jmv * w11);
             // move (cell units): r' = |(r + a, b)| written as r + delta
@@ -665,17 +666,19 @@ using PushFn = void (*)(PushArgs);
 
 static int push_ppt(const Cell* c) { return c->push_ppt > 0 ? c->push_ppt : kPPT; }
 
-template <bool W>
+template <bool W, bool IMPL>
 static PushFn push_fn_w(int ppt) {
     switch (ppt) {
-        case 4: return push_kernel<W, 4>;
-        case 16: return push_kernel<W, 16>;
-        default: return push_kernel<W, 8>;
+        case 4: return push_kernel<W, 4, IMPL>;
+        case 16: return push_kernel<W, 16, IMPL>;
+        default: return push_kernel<W, 8, IMPL>;
     }
 }
 
 static PushFn push_fn(const Cell* c) {
-    return c->weighted ? push_fn_w<true>(push_ppt(c)) : push_fn_w<false>(push_ppt(c));
+    const int ppt = push_ppt(c);
+    if (c->implicit) return c->weighted ? push_fn_w<true, true>(ppt) : push_fn_w<false, true>(ppt);
+    return c->weighted ? push_fn_w<true, false>(ppt) : push_fn_w<false, false>(ppt);
 }
 
 void push_prepare(Cell* c) {
