@@ -29,10 +29,29 @@ def _cases():
     return cfgs, pops
 
 
-def test_batch_matches_cells_run_alone():
+def _mixed_cases():
+    """Cells whose forms differ within one batch: direct-implicit ions-only,
+    explicit particle-free with a retained second harmonic, and
+    direct-implicit ions-only with per-particle weights."""
+    from paper_2609_15043_b300 import workloads
+    base = workloads.small()
+    empty = lambda c, sp: {k: v[:0] for k, v in workloads.population(c, sp).items()}
+    cfgs = [base.replace(nr=48, nz=72, seed=base.seed + 1, pressure_pa=0.0, implicit_es=1),
+            base.replace(n_harmonics=2),
+            base.replace(pressure_pa=0.0, seed=base.seed + 3, implicit_es=1, particle_weights=1)]
+    pops = [[empty(cfgs[0], 0), workloads.population(cfgs[0], 1)],
+            [empty(cfgs[1], 0), empty(cfgs[1], 1)],
+            [empty(cfgs[2], 0), workloads.population(cfgs[2], 1)]]
+    w = np.random.default_rng(4).uniform(0.5, 2.0, len(pops[2][1]["uid"]))
+    pops[2][1] = dict(pops[2][1], w=w)
+    return cfgs, pops
+
+
+@pytest.mark.parametrize("cases", ["plain", "mixed"])
+def test_batch_matches_cells_run_alone(cases):
     require_gpu()
     from paper_2609_15043_b300 import phasorpic as pp
-    cfgs, pops = _cases()
+    cfgs, pops = _cases() if cases == "plain" else _mixed_cases()
     batch = pp.Batch(cfgs)
     assert pp.lib.pp_batch_size(batch.h) == len(cfgs)
     for c, p in zip(batch.cells, pops):
@@ -49,11 +68,15 @@ def test_batch_matches_cells_run_alone():
         assert rb["period"] == ra["period"] == 1, i
         assert rb["n_samples"] == b.n_rf and rb["accepted"], i
         assert b.counters()["live_i"] == a.counters()["live_i"], i
-        tol = 1e-9 if i == 0 else 1e-5
+        particle_free = all(len(x["uid"]) == 0 for x in pops[i])
+        tol = 1e-9 if particle_free else 1e-5
         for k in ("icap", "qhat", "x_next"):
             assert _rel(rb[k], ra[k]) < tol, (i, k)
-        if i > 0:
+        if not particle_free:
             assert _rel(rb["vp"], ra["vp"]) < 1e-5, i
+        assert len(rb["harmonics"]) == len(ra["harmonics"]), i
+        for hb, ha in zip(rb["harmonics"], ra["harmonics"]):
+            assert _rel(hb["x_next"], ha["x_next"]) < tol, i
         assert b.status() == 0
         a.close()
     # a batch cell is destroyed with its batch only

@@ -93,14 +93,16 @@ def test_particle_free_harmonic_periods_against_oracle():
     g.close()
 
 
-def test_ions_only_harmonic_period_against_oracle():
-    """Ions only, no gas, two retained harmonics: the ions respond to the
-    summed E_theta waveform, so every harmonic's current has a V_p; the
-    period's loads, powers and relaxed states agree with the oracle at the
-    tolerances of the one-harmonic ions-only period."""
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_ions_only_harmonic_period_against_oracle(implicit):
+    """Ions only, no gas, two retained harmonics, in both electrostatic
+    forms: the ions respond to the summed E_theta waveform, so every
+    harmonic's current has a V_p; the period's loads, powers and relaxed
+    states agree with the oracle at the tolerances of the one-harmonic
+    ions-only period."""
     require_gpu()
     from paper_2609_15043_b300 import workloads
-    cfg = workloads.small().replace(pressure_pa=0.0, n_harmonics=2)
+    cfg = workloads.small().replace(pressure_pa=0.0, n_harmonics=2, implicit_es=implicit)
     oc, g, recs = _run(cfg, _pops(cfg, False, True), 1)
     ro, rg = recs[0]
     assert rg["n_live"][1] == ro["n_live"][1]
