@@ -224,3 +224,28 @@ def test_weights_need_a_weighted_cell():
     with pytest.raises(pp.PhasorPICError):
         g.set_particles(0, p)
     g.close()
+
+
+def test_control_inside_the_period_graph():
+    """With sm_every dividing N_RF the captured period graph carries the
+    split-merge passes (and the emission branches): two whole periods run
+    through pp_advance_period, the passes act, the live counters equal the
+    stored populations, the applied weights stay positive and the cell's
+    status stays clear."""
+    require_gpu()
+    from paper_2609_15043_b300 import workloads
+    cfg = _sm_cfg(sm_every=100, see_gamma=0.3, implicit_es=1)
+    g = gpu_cell(cfg, [workloads.population(cfg, sp) for sp in (0, 1)])
+    g.prime()
+    g.advance_period(2)
+    cc = g.control_counters()
+    assert cc["split"] > 0 and cc["merged"] > 0 and cc["see"] > 0
+    cnt = g.counters()
+    for sp, key in ((0, "live_e"), (1, "live_i")):
+        p = g.get_particles(sp)
+        assert cnt[key] == len(p["uid"])
+        assert np.all(p["w"] > 0) and len(np.unique(p["uid"])) == len(p["uid"])
+    rec = g.turn_phasors()
+    assert rec["period"] == 1 and rec["accepted"]
+    assert g.status() == 0
+    g.close()
