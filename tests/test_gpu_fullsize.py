@@ -74,3 +74,62 @@ def test_one_step_parity_at_bench_size(cell60_inputs, implicit):
     assert np.max(np.abs(j - info["J"])) <= 1e-6 * np.sum(np.abs(info["J"]))
     check_step_potential(oc, g)
     g.close()
+
+
+def test_particle_control_step_at_bench_size(cell60_inputs):
+    """The particle-control paths at the benchmark size, in the benchmark's
+    electrostatic form: all 8e6 macroparticles with weights uniform in
+    [0.5, 2], ion-induced emission (gamma = 0.1) and a split-merge pass after
+    the step (target 160, split below 100 near the axis, merge above 250 near
+    the wall), with 3e4 ions added next to the surfaces: populations, weights and new uids bit-exact against the
+    oracle, float32 state within 2e-5, emission, split and merge counts
+    equal, deposits within 1e-6 of their totals."""
+    require_gpu()
+    from paper_2609_15043_b300 import phasorpic as pp
+    cfg, pops = cell60_inputs
+    cfg = cfg.replace(implicit_es=1, see_gamma=0.1, sm_every=1, sm_target=160, sm_min=100, sm_max=250)
+    rng = np.random.default_rng(11)
+    # the seeded ions are cold and none reaches a surface in one step: 3e4
+    # more ions one step from the electrode, the wall and the window
+    n_b = 30000
+    nr, i_win = cfg.nr, int(round(cfg.z_win_lo / (cfg.z_max / cfg.nz)))
+    surf = np.arange(n_b) % 3
+    ir = np.where(surf == 1, nr - 1, rng.integers(0, nr, n_b))
+    iz = np.where(surf == 0, 0, np.where(surf == 2, i_win - 1, rng.integers(0, i_win, n_b)))
+    dr = np.where(surf == 1, 0.995, rng.uniform(0.05, 0.95, n_b)).astype(np.float32)
+    dz = np.where(surf == 0, 0.005, np.where(surf == 2, 0.995, rng.uniform(0.05, 0.95, n_b))).astype(np.float32)
+    vr = np.where(surf == 1, 1e6, 0.0).astype(np.float32)
+    vz = np.where(surf == 0, -1e6, np.where(surf == 2, 1e6, 0.0)).astype(np.float32)
+    extra = dict(cell=(iz * nr + ir).astype(np.uint32), dr=dr, dz=dz, vr=vr, vt=np.zeros(n_b, np.float32), vz=vz,
+                 uid=(np.arange(n_b) + len(pops[1]["uid"])).astype(np.uint32))
+    pops = [pops[0], {k: np.concatenate([pops[1][k], extra[k]]) for k in extra}]
+    ws = [rng.uniform(0.5, 2.0, len(p["uid"])).astype(np.float32) for p in pops]
+    oc = oracle_cell(cfg, pops)
+    for sp in (0, 1):
+        oc.P[sp]["w"] = ws[sp].copy()
+    oc.prime(np.float32)
+    g = gpu_cell(cfg, [dict(p, w=w.astype(np.float64)) for p, w in zip(pops, ws)])
+    g.set_potential(oc.phi)
+    info = oc.step(np.float32)
+    g.advance_steps(1)
+    cc = g.control_counters()
+    assert cc["see"] == oc.see_emitted > 0
+    assert cc["split"] == oc.sm_stats["split"] > 0 and cc["merged"] == oc.sm_stats["merged"] > 0
+    assert g.counters()["absorbed"] == info["stats"]["absorbed"]
+    for sp in (0, 1):
+        pg = by_uid(g.get_particles(sp))
+        po = oracle_live(oc.P[sp])
+        assert np.array_equal(pg["uid"], po["uid"].astype(np.uint32))
+        assert np.array_equal(pg["cell"], po["cell"].astype(np.uint32))
+        assert np.array_equal(pg["w"], po["w"].astype(np.float64))
+        for k in ("dr", "dz"):
+            assert np.max(np.abs(pg[k] - po[k])) <= 2e-5
+        for k in ("vr", "vt", "vz"):
+            scale = np.maximum(np.abs(po[k]), 1e-3 * np.max(np.abs(po[k])))
+            assert np.max(np.abs(pg[k] - po[k]) / scale) <= 2e-5
+    q = g.grid(pp.GRID_CHARGE)
+    assert np.max(np.abs(q - info["Q"])) <= 1e-6 * np.sum(np.abs(info["Q"]))
+    j = g.grid(pp.GRID_JMOM)
+    assert np.max(np.abs(j - info["J"])) <= 1e-6 * np.sum(np.abs(info["J"]))
+    assert g.status() == 0
+    g.close()
