@@ -27,8 +27,12 @@ fields        FV Poisson, FD Helmholtz, Gauss-law turn charge, unit fields,
 circuit       turn-resolved network, controller, relaxation, residuals, powers
 philox        Philox4x32-10 counter-based generator (Salmon et al. 2011)
 particles     cross sections, cylindrical Boris push, null-collision MCC,
-              area-weighted deposition
-cell          one RF cell advanced step by step and period by period
+              area-weighted deposition, per-particle weights, secondary
+              emission of absorbed ions
+control       stochastic weighted split-merge particle control
+mlp           the learned proposal's network, summaries, gate and training
+cell          one RF cell advanced step by step and period by period, with
+              the retained circuit harmonics
 verification  the paper's particle-free Tests 1-3 set up on this oracle
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
