@@ -253,6 +253,7 @@ struct Cell {
     double* d_pcg_acc = nullptr;            // per-CTA partial sums
     float* d_pcg_zrow = nullptr;            // per interior row: z couplings below, above, radial weight
     float* d_pcg_mu = nullptr;              // radial eigenvalues of the separable preconditioner
+    float* d_pcg_VT = nullptr;              // the radial eigenbasis transposed, when it is read from global memory
     float* d_pcg_chib = nullptr;            // chi averaged over each node row
     double* d_phi_prev = nullptr;           // the previous step's potential (initial guess)
 

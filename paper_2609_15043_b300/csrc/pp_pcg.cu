@@ -77,6 +77,7 @@ struct PcgArgs {
     int NR, M, rows;
     double inv2pieps0;
     const float* V;         // radial eigenbasis, M x M row-major ([node][mode])
+    const float* VT;        // its transpose ([mode][node]) when V is read from global memory
     const float* zlo;       // per interior row: eps_{i-1} / dz (z coupling below)
     const float* zup;       // eps_i / dz (above)
     const float* zeb;       // (dz / dR) (eps_{i-1} + eps_i) / 2 (radial weight)
@@ -634,10 +635,19 @@ __global__ void __launch_bounds__(kCT, 1) pcg_cluster(PcgArgs a) {
             // (C) backward transform of the band and its halo rows, projected
             // onto the free nodes: z = -(P rho); w = B z on the band,
             // gamma = rho . z, delta = z . w
-            transform<true, VSM>(s_in, Mp, nb + 2, Vs, nqp, M, [&](int r, int j, float v) {
-                const int q = r * M + j;
-                ZF[q] = s_free[q] ? -v : 0.f;
-            });
+            // from global memory the transposed copy is read row-wise, as
+            // the forward transform reads V (coalesced quads)
+            if constexpr (VSM) {
+                transform<true, VSM>(s_in, Mp, nb + 2, Vs, nqp, M, [&](int r, int j, float v) {
+                    const int q = r * M + j;
+                    ZF[q] = s_free[q] ? -v : 0.f;
+                });
+            } else {
+                transform<false, VSM>(s_in, Mp, nb + 2, a.VT, nqp, M, [&](int r, int j, float v) {
+                    const int q = r * M + j;
+                    ZF[q] = s_free[q] ? -v : 0.f;
+                });
+            }
             __syncthreads();
             float pgf = 0.f, pdf = 0.f;
             for (int li = threadIdx.x; li < nbM; li += kCT) {
@@ -850,6 +860,15 @@ void pcg_alloc(Cell* c, const std::vector<double>& az, const std::vector<double>
     // private per-CTA global regions for the band vectors when they are not in
     // shared memory
     c->d_pcg32 = p.vec_sm ? nullptr : c->alloc<float>((size_t)p.C * p.gvec_stride);
+    if (!p.v_sm) {
+        // the transposed eigenbasis for the backward transform from global memory
+        std::vector<float> v((size_t)M * M), vt((size_t)M * M);
+        cudaMemcpy(v.data(), c->ps.Vf, sizeof(float) * v.size(), cudaMemcpyDeviceToHost);
+        for (int r = 0; r < M; ++r)
+            for (int q = 0; q < M; ++q) vt[(size_t)q * M + r] = v[(size_t)r * M + q];
+        c->d_pcg_VT = c->alloc<float>(vt.size());
+        cudaMemcpy(c->d_pcg_VT, vt.data(), sizeof(float) * vt.size(), cudaMemcpyHostToDevice);
+    }
     c->d_pcg_chib = c->alloc<float>((size_t)c->NZ + 2);
     c->d_phi_prev = c->alloc<double>(c->nnodes);
 }
@@ -879,6 +898,7 @@ int pcg_refine(Cell* c, double cs, double sn, cudaStream_t st, const double* ext
     a.rows = c->ps.rows;
     a.inv2pieps0 = 1.0 / (2.0 * kPi * kEps0);
     a.V = c->ps.Vf;
+    a.VT = c->d_pcg_VT;
     a.zlo = c->d_pcg_zrow;
     a.zup = c->d_pcg_zrow + a.rows;
     a.zeb = c->d_pcg_zrow + 2 * a.rows;
