@@ -54,6 +54,7 @@ constexpr int kMaxOuter = 6;              // FP64 refinement steps
 constexpr int kMaxInner = 60;             // CG iterations per refinement step
 constexpr float kInnerTol = 1e-6f;        // inner residual reduction per refinement step at most (FP32)
 constexpr int kPcrLevels = 5;             // cyclic reduction over the 32 lanes
+constexpr int kRQ = 3;                    // row quads per warp task of the transforms from global memory
 
 // per-lane factors of the z systems: 5 per interior row (a, 1/pivot,
 // c/pivot, responses to the lower and the upper separator), then the
@@ -253,6 +254,65 @@ __device__ __forceinline__ void transform(const float* X, int ldx, int nr, const
             for (int c = 0; c < 4; ++c) {
                 const float v = kg == 0 ? acc[0][c] : kg == 1 ? acc[1][c] : kg == 2 ? acc[2][c] : acc[3][c];
                 out(row, 4 * cq + c, v);
+            }
+        }
+    }
+}
+
+// The forward-oriented product with W = V read from global memory (V too
+// large for shared memory; the backward transform passes the transposed
+// copy): the loads of V, not the FMAs, bound it (each quad is an L2 access),
+// so a warp task covers RQ row quads of the same 32 columns and every V quad
+// loaded serves 4 RQ rows.  Lane layout and reduction as in transform().
+template <int RQ, class Out>
+__device__ __forceinline__ void transform_g(const float* X, int ldx, int nr, const float* V, int M, Out out) {
+    const int nq = M / 4, nrc = (nr + 3) / 4, ncb = (nq + 7) / 8, ngr = (nrc + RQ - 1) / RQ;
+    const int lane = threadIdx.x & 31, kg = lane >> 3, cl8 = lane & 7;
+    const int kq_per = (nq + 3) / 4;
+    const int kq0 = kg * kq_per, kq1 = min(nq, kq0 + kq_per);
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    const int ldx4 = ldx / 4;
+    for (int task = threadIdx.x >> 5; task < ngr * ncb; task += kWarps) {
+        const int rg = task / ncb, cq = (task % ncb) * 8 + cl8;
+        const bool colok = cq < nq;
+        const int cqs = colok ? cq : nq - 1;      // idle lanes read a valid quad
+        float acc[RQ * 4][4];
+#pragma unroll
+        for (int r = 0; r < RQ * 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+        for (int kq = kq0; kq < kq1; ++kq) {
+            float4 w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = __ldg(V4 + (size_t)(4 * kq + q) * nq + cqs);
+#pragma unroll
+            for (int r = 0; r < RQ * 4; ++r) {
+                const int row = min(rg * RQ * 4 + r, nr - 1);
+                const float4 x = X4[(size_t)row * ldx4 + kq];
+                acc[r][0] = fmaf(x.x, w[0].x, fmaf(x.y, w[1].x, fmaf(x.z, w[2].x, fmaf(x.w, w[3].x, acc[r][0]))));
+                acc[r][1] = fmaf(x.x, w[0].y, fmaf(x.y, w[1].y, fmaf(x.z, w[2].y, fmaf(x.w, w[3].y, acc[r][1]))));
+                acc[r][2] = fmaf(x.x, w[0].z, fmaf(x.y, w[1].z, fmaf(x.z, w[2].z, fmaf(x.w, w[3].z, acc[r][2]))));
+                acc[r][3] = fmaf(x.x, w[0].w, fmaf(x.y, w[1].w, fmaf(x.z, w[2].w, fmaf(x.w, w[3].w, acc[r][3]))));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RQ * 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], 8);
+                acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], 16);
+            }
+#pragma unroll
+        for (int g = 0; g < RQ; ++g) {
+            const int row = (rg * RQ + g) * 4 + kg;
+            if (colok && row < nr) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float v = kg == 0 ? acc[4 * g][c] : kg == 1 ? acc[4 * g + 1][c]
+                                  : kg == 2 ? acc[4 * g + 2][c] : acc[4 * g + 3][c];
+                    out(row, 4 * cq + c, v);
+                }
             }
         }
     }
@@ -604,9 +664,15 @@ __global__ void __launch_bounds__(kCT, 1) pcg_cluster(PcgArgs a) {
             }
             warp_partial(&sy, 0, rmf, true);
             __syncthreads();
-            transform<false, VSM>(R, M, nb, Vs, nqp, M, [&](int r, int m, float v) {
-                cl.map_shared_rank(s_d, m % C)[(m / C) * rows + lo + r] = v;
-            });
+            if constexpr (VSM) {
+                transform<false, VSM>(R, M, nb, Vs, nqp, M, [&](int r, int m, float v) {
+                    cl.map_shared_rank(s_d, m % C)[(m / C) * rows + lo + r] = v;
+                });
+            } else {
+                transform_g<kRQ>(R, M, nb, a.V, M, [&](int r, int m, float v) {
+                    cl.map_shared_rank(s_d, m % C)[(m / C) * rows + lo + r] = v;
+                });
+            }
             cbar(&sy, gen, C, rank, a.dst, 1, 1u);
             const float rn = pay_all(&sy, gen, C, 0, true);
             // the inner solve stops at half the refinement's target residual
@@ -643,7 +709,7 @@ __global__ void __launch_bounds__(kCT, 1) pcg_cluster(PcgArgs a) {
                     ZF[q] = s_free[q] ? -v : 0.f;
                 });
             } else {
-                transform<false, VSM>(s_in, Mp, nb + 2, a.VT, nqp, M, [&](int r, int j, float v) {
+                transform_g<kRQ>(s_in, Mp, nb + 2, a.VT, M, [&](int r, int j, float v) {
                     const int q = r * M + j;
                     ZF[q] = s_free[q] ? -v : 0.f;
                 });
