@@ -176,3 +176,50 @@ def test_multiharmonic_step_at_bench_size(cell60_inputs):
     assert np.max(np.abs(j - info["J"])) <= 1e-6 * np.sum(np.abs(info["J"]))
     check_step_potential(oc, g)
     g.close()
+
+
+def test_cell100_step_on_sampled_particles():
+    """The larger single cell (256x384 cells, 1.6e7 macroparticles per
+    species, 800 steps per period) in the benchmark's electrostatic form: the
+    GPU advances all 3.2e7 particles one step from the oracle's potential of
+    the full population, and the oracle advances a sample of 1e5 particles per
+    species in the same fields (each particle's step depends only on its own
+    state, the fields and its own draws): the sampled particles' cells and
+    collisions agree bit for bit, their float32 state within 2e-5; and the
+    cluster solve of the step matches the oracle's direct solve of the same
+    operator on the GPU's charges."""
+    require_gpu()
+    from paper_2609_15043_b300 import phasorpic as pp, workloads
+    cfg = workloads.cell100().replace(implicit_es=1)
+    pops = [workloads.population(cfg, sp) for sp in (0, 1)]
+    oc = oracle_cell(cfg, pops)
+    oc.prime(np.float32)                       # the full population's potential and chi
+    g = gpu_cell(cfg, pops)
+    g.set_potential(oc.phi)
+    g.advance_steps(1)
+    rng = np.random.default_rng(100)
+    for sp in (0, 1):
+        P = oc.P[sp]
+        pick = np.sort(rng.choice(len(P["uid"]), 100000, replace=False))
+        oc.P[sp] = {k: v[pick].copy() for k, v in P.items()}
+    oc.step(np.float32)
+    for sp in (0, 1):
+        pg = by_uid(g.get_particles(sp))
+        po = oracle_live(oc.P[sp])
+        idx = np.searchsorted(pg["uid"], po["uid"].astype(np.uint32))
+        assert np.all(idx < len(pg["uid"])) and np.array_equal(pg["uid"][idx], po["uid"].astype(np.uint32))
+        assert np.array_equal(pg["cell"][idx], po["cell"].astype(np.uint32))
+        for k in ("dr", "dz"):
+            assert np.max(np.abs(pg[k][idx] - po[k])) <= 2e-5
+        for k in ("vr", "vt", "vz"):
+            ref = po[k]
+            scale = np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+            assert np.max(np.abs(pg[k][idx] - ref) / scale) <= 2e-5
+    # the step's solve against the oracle's direct solve of the same operator
+    qe, qi = g.grid(pp.GRID_CHARGE_E), g.grid(pp.GRID_CHARGE_I)
+    chi = oc.susceptibility([qe, qi], np.float32)
+    ref = oc.solve_potential(qe + qi + g.grid(pp.GRID_WINDOW), oc.theta(1), chi)
+    phi = g.grid(pp.GRID_PHI)
+    assert np.max(np.abs(phi - ref)) <= 1e-8 * np.max(np.abs(ref))
+    assert g.status() == 0
+    g.close()
