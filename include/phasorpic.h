@@ -581,6 +581,14 @@ int pp_helmholtz_solve(pp_cell* cell, const double* rhs, double* e);
 int pp_poisson_solve_noalloc(pp_cell* cell, const double* d_q, const double* d_turn_phi, double* d_phi,
                              int* d_info, void* stream);
 
+/* pp_wait_selftest -- runs the library's two kinds of bounded device wait on
+ * conditions that never come true (an mbarrier phase no copy completes; a
+ * global flag no one sets, read with acquire loads), each giving up after
+ * max_iters polls (>= 1).  status[0] and status[1] receive PP_ST_TIMEOUT when
+ * the respective wait expired.  No fault, the context stays usable.  Uses the
+ * current device; synchronous. */
+int pp_wait_selftest(int64_t max_iters, uint32_t* status);
+
 /* pp_get_status -- device status bits (PP_ST_*) accumulated since init;
  * synchronises `stream`. */
 int pp_get_status(pp_cell* cell, uint32_t* status, void* stream);

@@ -1346,6 +1346,16 @@ int pp_get_counters(pp_cell* h, int64_t* out, void* stream) {
     return PP_OK;
 }
 
+int pp_wait_selftest(int64_t max_iters, uint32_t* status) {
+    if (max_iters < 1 || !status) {
+        set_error("bad argument to pp_wait_selftest");
+        return PP_E_ARG;
+    }
+    int rc = wait_selftest((long long)max_iters, status);
+    if (rc) set_error("pp_wait_selftest: CUDA error");
+    return rc;
+}
+
 int pp_get_control_counters(pp_cell* h, int64_t* out, void* stream) {
     Cell* c = reinterpret_cast<Cell*>(h);
     if (!c || !out) {

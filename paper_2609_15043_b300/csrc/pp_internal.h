@@ -406,6 +406,7 @@ void launch_append(Cell* c, cudaStream_t st);
 void launch_sort(Cell* c, int sp, cudaStream_t st);
 void launch_deposit_only(Cell* c, cudaStream_t st);
 void launch_split_merge(Cell* c, cudaStream_t st);
+int wait_selftest(long long max_iters, unsigned* status_out);
 // in_step: the step's field preparation already imposed the turn potentials
 // and cleared the bookkeeping, and the step's sample kernel takes the final
 // convergence decision

@@ -725,6 +725,57 @@ void launch_push(Cell* c, cudaStream_t st) {
     count_launch();
 }
 
+// ---------------------------------------------------------------- bounded waits, self-test
+// The two kinds of wait the library's kernels use, each on a condition that
+// never comes true, so that their expiry path runs: an mbarrier phase that no
+// copy completes (the particle kernel's staging wait) and a flag in global
+// memory that no one sets, read with acquire loads (the shape of the cluster
+// solve's barrier).  Each gives up after max_iters polls and records
+// PP_ST_TIMEOUT in *status; nothing faults and the context stays usable.
+__global__ void wait_selftest_kernel(long long max_iters, const unsigned* flag, unsigned* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const uint32_t addr = smem_u32(&bar);
+    bool done = false;
+    for (long long it = 0; it < max_iters && !done; ++it) {
+        uint32_t d;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(d)
+            : "r"(addr), "r"(0u)
+            : "memory");
+        done = d != 0;
+    }
+    if (!done) atomicOr(status, (unsigned)PP_ST_TIMEOUT);
+    bool seen = false;
+    for (long long it = 0; it < max_iters && !seen; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        seen = v != 0u;
+    }
+    if (!seen) atomicOr(status + 1, (unsigned)PP_ST_TIMEOUT);
+}
+
+int wait_selftest(long long max_iters, unsigned* status_out) {
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, 3 * sizeof(unsigned)) != cudaSuccess) return PP_E_CUDA;
+    cudaMemset(d, 0, 3 * sizeof(unsigned));
+    wait_selftest_kernel<<<1, 32>>>(max_iters, d + 2, d);
+    count_launch();
+    unsigned h[2] = {0u, 0u};
+    cudaError_t e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return PP_E_CUDA;
+    status_out[0] = h[0];
+    status_out[1] = h[1];
+    return PP_OK;
+}
+
 // ---------------------------------------------------------------- prime deposit
 template <typename T>
 __global__ void deposit_only(PBuf<T> P, const int* nslot, int sp, T qw, T* rho, int nr, int NR) {

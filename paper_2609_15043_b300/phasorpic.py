@@ -43,7 +43,7 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy",
            "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune", "pp_set_harmonic_state",
            "pp_get_harmonic_state", "pp_set_particles_weighted", "pp_get_particle_weights",
-           "pp_get_control_counters"]
+           "pp_get_control_counters", "pp_wait_selftest"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -170,6 +170,7 @@ def _load():
         "pp_set_particles_weighted": (I, [V, I, C.c_int64, V, V, V, V, V, V, V, V]),
         "pp_get_particle_weights": (I, [V, I, C.c_int64, P(C.c_int64), V, V]),
         "pp_get_control_counters": (I, [V, V, V]),
+        "pp_wait_selftest": (I, [C.c_int64, V]),
         "pp_init_batch": (I, [V, I, P(V)]),
         "pp_mlp_forward": (I, [V, V, I, V]),
         "pp_ml_configure": (I, [V, V, D, I]),
@@ -207,6 +208,14 @@ lib = _load()
 
 class PhasorPICError(RuntimeError):
     pass
+
+
+def wait_selftest(max_iters=1 << 14):
+    """pp_wait_selftest: the library's bounded device waits on conditions that
+    never come true; returns the two status words (PP_ST_TIMEOUT expected)."""
+    st = np.zeros(2, np.uint32)
+    _check(lib.pp_wait_selftest(int(max_iters), _ptr(st)), "pp_wait_selftest")
+    return st
 
 
 def vacuum_impedance(nr, nz, r_max, z_max, freq, sheets, boundary=None, unit_fields=False):

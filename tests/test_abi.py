@@ -123,6 +123,7 @@ def test_trainer_and_tuning_arguments_are_checked_before_the_device():
     assert lib.pp_autotune(None, 1, None, None, None) == -7
     assert lib.pp_batch_autotune(None, 1, None, None, None) == -7
     assert lib.pp_get_control_counters(None, None, None) == -7
+    assert lib.pp_wait_selftest(0, None) == -7
     assert lib.pp_get_particle_weights(None, 0, 0, None, None, None) == -7
     assert lib.pp_set_particles_weighted(None, 0, 0, None, None, None, None, None, None, None, None) == -7
 
