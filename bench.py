@@ -48,6 +48,9 @@ def parse():
                          "at most 80 periods)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cell60")
+    ap.add_argument("--config-json", default=None, metavar="PATH",
+                    help="cell configuration as JSON (paper_2609_15043_b300.workloads.load_config); --cfg and --es "
+                         "still apply on top")
     ap.add_argument("--cfg", action="append", default=[], metavar="KEY=VALUE",
                     help="override a field of the workload's configuration (repeatable), e.g. density=1e15")
     ap.add_argument("--cpu-steps", type=int, default=1, help="PIC steps of the oracle sample")
@@ -833,6 +836,9 @@ def main():
         run_batch(args, ws, rank, local)
         return
     cfg = workloads.WORKLOADS[args.workload if args.workload != "batch32" else "cell60"]()
+    if args.config_json:
+        cfg = workloads.load_config(args.config_json)
+        args.workload = "custom (%s)" % os.path.basename(args.config_json)
     if args.cfg:
         over = {}
         for kv in args.cfg:

@@ -581,6 +581,12 @@ int pp_helmholtz_solve(pp_cell* cell, const double* rhs, double* e);
 int pp_poisson_solve_noalloc(pp_cell* cell, const double* d_q, const double* d_turn_phi, double* d_phi,
                              int* d_info, void* stream);
 
+/* pp_set_nvtx -- host-side NVTX ranges (1 on, 0 off; default off): one per
+ * period advance ("pp periods"), per PIC step ("pp step") and per phase of a
+ * step ("push", "poisson", "sort", "other", "period_end"), around the launches
+ * they enqueue (a replayed period graph shows as one range).  Process-wide. */
+int pp_set_nvtx(int enable);
+
 /* pp_wait_selftest -- runs the library's two kinds of bounded device wait on
  * conditions that never come true (an mbarrier phase no copy completes; a
  * global flag no one sets, read with acquire loads), each giving up after

@@ -9,6 +9,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace pp {
 
 static thread_local std::string g_err;
@@ -20,7 +22,28 @@ unsigned long long g_launches = 0;
 // pool of their own
 static thread_local bool g_capturing = false;
 static std::vector<cudaEvent_t>* pool_of(Cell* c);
+
+// host-side NVTX ranges (pp_set_nvtx): one per step, one per phase of a step
+// and one per period advance, for timeline tools and for filtering kernels by
+// range in a profiler; off by default
+static bool g_nvtx = false;
+static const char* const kPhaseName[PH_N] = {"push", "poisson", "sort", "other", "period_end"};
+struct NvtxRange {
+    bool on;
+    explicit NvtxRange(const char* name) : on(g_nvtx) {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxRange() {
+        if (on) nvtxRangePop();
+    }
+};
 static void phase_mark(Cell* c, int ph, bool start, cudaStream_t st) {
+    if (g_nvtx) {
+        if (start)
+            nvtxRangePushA(kPhaseName[ph]);
+        else
+            nvtxRangePop();
+    }
     if (!c->profiling) return;
     if (c->profile_level < 2 && ph != PH_PUSH) return;
     std::vector<cudaEvent_t>& pool = *pool_of(c);
@@ -88,6 +111,7 @@ static int read_state(Cell* c, cudaStream_t st) {
 
 // one PIC step s -> s+1 (Sec. 2.5), enqueued on st
 static void one_step(Cell* c, cudaStream_t st) {
+    NvtxRange step_range("pp step");
     int64_t s = c->s;
     double th = theta(c, s), th1 = theta(c, s + 1);
     phase_mark(c, PH_OTHER, true, st);
@@ -261,6 +285,7 @@ static int pp_prime_on(Cell* c, cudaStream_t st);
 static int batch_advance(Batch* b, int n_periods, cudaStream_t st);
 
 static int advance_cell_periods(Cell* c, int n_periods, cudaStream_t st) {
+    NvtxRange range("pp periods");
     if (!c->primed) {
         int rc = pp_prime_on(c, st);
         if (rc) return rc;
@@ -1389,6 +1414,11 @@ int pp_get_poisson_stats(pp_cell* h, int* sweeps, double* rel, void* stream) {
             memcpy(&sc, &c->h_st->pnorm[2 * k + 1], sizeof(double));
             rel[k] = (k < n && sc > 0) ? r / sc : 0.0;
         }
+    return PP_OK;
+}
+
+int pp_set_nvtx(int enable) {
+    g_nvtx = enable != 0;
     return PP_OK;
 }
 

@@ -43,7 +43,7 @@ EXPORTS = ["pp_config_size", "pp_record_size", "pp_init_cell", "pp_destroy", "pp
            "pp_trainer_evaluate", "pp_trainer_params", "pp_trainer_steps", "pp_trainer_destroy",
            "pp_get_tuning", "pp_set_tuning", "pp_autotune", "pp_batch_autotune", "pp_set_harmonic_state",
            "pp_get_harmonic_state", "pp_set_particles_weighted", "pp_get_particle_weights",
-           "pp_get_control_counters", "pp_wait_selftest"]
+           "pp_get_control_counters", "pp_wait_selftest", "pp_set_nvtx"]
 PHASES = ["push", "poisson", "sort", "other", "period_end"]
 
 
@@ -171,6 +171,7 @@ def _load():
         "pp_get_particle_weights": (I, [V, I, C.c_int64, P(C.c_int64), V, V]),
         "pp_get_control_counters": (I, [V, V, V]),
         "pp_wait_selftest": (I, [C.c_int64, V]),
+        "pp_set_nvtx": (I, [I]),
         "pp_init_batch": (I, [V, I, P(V)]),
         "pp_mlp_forward": (I, [V, V, I, V]),
         "pp_ml_configure": (I, [V, V, D, I]),
@@ -208,6 +209,11 @@ lib = _load()
 
 class PhasorPICError(RuntimeError):
     pass
+
+
+def set_nvtx(enable=True):
+    """pp_set_nvtx: host-side NVTX ranges per period advance, step and phase."""
+    _check(lib.pp_set_nvtx(1 if enable else 0), "pp_set_nvtx")
 
 
 def wait_selftest(max_iters=1 << 14):

@@ -152,6 +152,44 @@ def batch_cells(n_cells=32, seed=20260915):
 WORKLOADS = {"small": small, "cell60": cell60, "coarse60": coarse60, "cell100": cell100}
 
 
+def load_config(src):
+    """A CellConfig from a JSON object given as a dict, a JSON string or a file
+    path: an optional "workload" key names the starting configuration (one of
+    WORKLOADS; the defaults otherwise) and every other key overrides the field
+    of that name.  Unknown keys and values of the wrong kind are refused."""
+    import json
+    import os
+    if isinstance(src, dict):
+        d = dict(src)
+    elif isinstance(src, str) and os.path.exists(src):
+        with open(src) as fh:
+            d = json.load(fh)
+    else:
+        d = json.loads(src)
+    base = WORKLOADS[d.pop("workload")]() if "workload" in d else CellConfig()
+    names = {f.name: f for f in dataclasses.fields(CellConfig)}
+    over = {}
+    for k, v in d.items():
+        if k not in names:
+            raise KeyError("unknown configuration key %r" % k)
+        cur = getattr(base, k)
+        if isinstance(cur, list):
+            if not isinstance(v, list):
+                raise TypeError("%s must be a list" % k)
+            over[k] = [type(cur[0])(x) for x in v] if cur else list(v)
+        elif isinstance(cur, bool) or not isinstance(v, (int, float)):
+            raise TypeError("%s must be a number" % k)
+        else:
+            over[k] = type(cur)(v)
+    return base.replace(**over)
+
+
+def dump_config(cfg):
+    """The JSON text of a CellConfig (every field), readable by load_config."""
+    import json
+    return json.dumps(dataclasses.asdict(cfg), indent=1)
+
+
 def macro_weight(cfg):
     """Physical particles per macroparticle: n V_plasma / N."""
     v_plasma = math.pi * cfg.r_max ** 2 * cfg.z_win_lo
