@@ -867,6 +867,10 @@ int poisson_refine(Cell* c, double cs, double sn, cudaStream_t st, bool external
     int rows = c->ps.rows, M = c->ps.M;
     int nint = rows * M;
     int maxit = c->cfg.poisson_max_iter < 1 ? 1 : (c->cfg.poisson_max_iter > 15 ? 15 : c->cfg.poisson_max_iter);
+    // a solve outside a step (priming from zero, the period boundary's new
+    // turn potentials, a standalone solve) has no previous step's potential
+    // close to it: up to six sweeps (the converged ones are skipped on the device)
+    if (!in_step && maxit < 6) maxit = 6;
     DevState* dst = c->d_st;
     int* done = &dst->pdone;
     const double* ext = external_targets ? d_targets : nullptr;
