@@ -516,7 +516,8 @@ def run_batch(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     from paper_2609_15043_b300 import phasorpic as pp, workloads
-    cfgs_all = workloads.batch_cells()
+    implicit = 1 if args.es == "implicit" else 0
+    cfgs_all = [c.replace(implicit_es=implicit) for c in workloads.batch_cells()]
     cfgs = batch_slice(cfgs_all, rank, ws)
     batch = pp.Batch(cfgs)
     for c, cfg in zip(batch.cells, cfgs):
@@ -586,8 +587,10 @@ def run_batch(args, ws, rank, local):
             "scaling": "weak" if ws > 1 else "strong", "vs_baseline": None,
             "dtype": "f32 particles, f64 fields/circuit", "data": "synthetic",
             "config": {"workload": "batch32: %d independent cells, nr in 64..192 (nz = 1.5 nr), %.3g "
-                                   "macroparticles/species in total, 3-5 turns, 5-50 mTorr, 20-150 W targets"
-                                   % (len(cfgs_all), sum(c.n_init for c in cfgs_all)),
+                                   "macroparticles/species in total, 3-5 turns, 5-50 mTorr, 20-150 W targets, %s "
+                                   "electrostatics"
+                                   % (len(cfgs_all), sum(c.n_init for c in cfgs_all),
+                                      "direct-implicit" if implicit else "explicit"),
                        "step": "one RF period of every cell (400 PIC steps + period end each)",
                        "l2": "inputs larger than L2",
                        "parallelism": "cells split over ranks" if ws > 1 else "32 cells on per-cell streams",
