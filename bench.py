@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--es", default="implicit", choices=["implicit", "explicit"],
                     help="electrostatics: the paper's direct-implicit form (default) or the explicit push")
+    ap.add_argument("--tts-batch", type=int, default=0,
+                    help="with --time-to-stationary: run this many seeded cells of the workload in one batch per "
+                         "form, until every cell is stationary")
     ap.add_argument("--tts-workload", default="coarse60",
                     help="workload of the time-to-stationary part of the default run")
     ap.add_argument("--tts-periods", type=int, default=400, help="cap of that part (periods per form)")
@@ -655,6 +658,60 @@ def stationary_runs(cfg, forms, max_periods, ml_weights=None, alpha_ml=1.0, crit
     return out, traces
 
 
+def stationary_batch_runs(cfg, forms, max_periods, n_cells, ml_weights=None, alpha_ml=1.0, criterion="full"):
+    """The batched form of the stationary runs: n_cells independent cells of
+    the workload (PIC seeds seed, seed + 1, ...; populations seeded from
+    them) in one pp_batch per form, advanced one RF period at a time.  Every
+    cell's record is read back and fed to its own monitor; a cell that has met
+    the criterion keeps running with the batch.  Per form: the wall time (from
+    before priming) until every cell has met it, the period at which each did,
+    and the ensemble means of the cells' stationary-window means."""
+    import torch
+    from paper_2609_15043_b300 import phasorpic as pp, workloads
+    from paper_2609_15043_b300.stationarity import StationarityMonitor, StationarityCriteria
+    out = {}
+    for form in forms:
+        cfgs = [cfg.replace(plain_fp64=1 if form == "fp64" else 0, seed=cfg.seed + i) for i in range(n_cells)]
+        batch = pp.Batch(cfgs)
+        for c, cc in zip(batch.cells, cfgs):
+            for sp in (0, 1):
+                c.set_particles(sp, workloads.population(cc, sp))
+        if form == "fused_ml":
+            from paper_2609_15043_b300.mlp_train import load_params
+            params = load_params(ml_weights)
+            for c in batch.cells:
+                c.ml_configure(params, alpha_ml=alpha_ml)
+        sh = torch.cuda.current_stream().cuda_stream
+        mons = [StationarityMonitor(len(cc.turn_r), cc.p_target if cc.power_control else None,
+                                    StationarityCriteria(plasma_drift=criterion == "full")) for cc in cfgs]
+        at = [None] * n_cells
+        used = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        periods = 0
+        for periods in range(1, max_periods + 1):
+            batch.advance_period(1, sh)
+            for i, c in enumerate(batch.cells):
+                rec = c.turn_phasors(sh)
+                used += 1 if rec["ml_used"] else 0
+                if at[i] is None and mons[i].update(rec):
+                    at[i] = periods
+            if all(a is not None for a in at):
+                break
+        wall = time.perf_counter() - t0
+        done = [m.window_means() for m, a in zip(mons, at) if a is not None]
+        out[form] = {"cells": n_cells, "stationary_cells": len(done), "periods": periods, "wall_s": wall,
+                     "ms_per_period": 1e3 * wall / periods, "stationary_at": at,
+                     "ensemble_window_means": ({"p": np.mean([d["p"] for d in done], axis=0).tolist(),
+                                                "x_abs": np.mean([d["x_abs"] for d in done], axis=0).tolist()}
+                                               if len(done) == n_cells else None),
+                     "status": [c.status() for c in batch.cells], "proposals_used": used}
+        batch.close()
+        del batch
+        torch.cuda.empty_cache()
+    return out
+
+
 def fp64_error(cfg, sh):
     """Error of the fused FP32 path against FP64 on the bench workload: the
     fused cell and the plain FP64 cell (FP64 particle state, parity-tested
@@ -769,6 +826,36 @@ def run_stationary(args, cfg, local):
     forms = [f for f in args.forms.split(",") if f]
     if args.ml_weights and "fused_ml" not in forms:
         forms.append("fused_ml")
+    if args.tts_batch > 0:
+        out = stationary_batch_runs(cfg, forms, args.max_periods, args.tts_batch, args.ml_weights, args.alpha_ml,
+                                    args.criterion)
+        d = out.get("fp64")
+        full = lambda r: r is not None and r["stationary_cells"] == r["cells"]
+        ratio, lower, acc = {}, {}, {}
+        for name in ("fused", "fused_ml"):
+            f = out.get(name)
+            if not full(f) or d is None:
+                continue
+            if full(d):
+                ratio[name] = d["wall_s"] / f["wall_s"]
+                a, b = np.asarray(f["ensemble_window_means"]["p"]), np.asarray(d["ensemble_window_means"]["p"])
+                xa = np.asarray(f["ensemble_window_means"]["x_abs"])
+                xb = np.asarray(d["ensemble_window_means"]["x_abs"])
+                keep = np.abs(xb) > 1e-3 * np.max(np.abs(xb))
+                acc[name] = {"ensemble_power_rel_diff": float(np.max(np.abs(a - b) / np.abs(b))),
+                             "ensemble_state_rel_diff": float(np.max(np.abs(xa - xb)[keep] / np.abs(xb[keep])))}
+            else:
+                lower[name] = d["wall_s"] / f["wall_s"]
+        line = {"metric": "time to a stationary state of a batch of cells, fused FP32 (+ proposal) vs plain FP64 PIC, "
+                          "1 B300",
+                "time_to_stationary_batched": {
+                    "workload": "%d cells of %s (seeds %d..%d)" % (args.tts_batch, workload_desc(cfg, args.workload),
+                                                                   cfg.seed, cfg.seed + args.tts_batch - 1),
+                    "max_periods": args.max_periods, "criterion": args.criterion, "forms": out,
+                    "fp64_over_wall": ratio or None, "fp64_over_wall_at_least": lower or None,
+                    "same_accuracy": acc or None}}
+        print(json.dumps(line), flush=True)
+        return
     out, traces = stationary_runs(cfg, forms, args.max_periods, args.ml_weights, args.alpha_ml, args.criterion)
     line = {"metric": "time to a stationary state, fused FP32 vs plain FP64 PIC, 1 B300",
             "time_to_stationary": tts_summary(cfg, args.workload, out, traces, args.max_periods, args.criterion)}
