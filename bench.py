@@ -819,6 +819,33 @@ def tts_summary(cfg, name, out, traces, max_periods, criterion="full"):
             "same_accuracy": same_accuracy(out, traces)}
 
 
+def tts_batch_ratios(out):
+    """From the batched stationary runs: per fast form (fused, fused_ml) whose
+    every cell became stationary, the plain FP64 batch's wall time over its
+    own (or, if the FP64 batch did not finish within the cap, that ratio as a
+    lower bound), and where both finished, the largest relative differences
+    of the ensemble window means (powers; |applied circuit state| above 1e-3
+    of its largest entry)."""
+    d = out.get("fp64")
+    full = lambda r: r is not None and r["stationary_cells"] == r["cells"]
+    ratio, lower, acc = {}, {}, {}
+    for name in ("fused", "fused_ml"):
+        f = out.get(name)
+        if not full(f) or d is None:
+            continue
+        if not full(d):
+            lower[name] = d["wall_s"] / f["wall_s"]
+            continue
+        ratio[name] = d["wall_s"] / f["wall_s"]
+        a, b = np.asarray(f["ensemble_window_means"]["p"]), np.asarray(d["ensemble_window_means"]["p"])
+        xa = np.asarray(f["ensemble_window_means"]["x_abs"])
+        xb = np.asarray(d["ensemble_window_means"]["x_abs"])
+        keep = np.abs(xb) > 1e-3 * np.max(np.abs(xb))
+        acc[name] = {"ensemble_power_rel_diff": float(np.max(np.abs(a - b) / np.abs(b))),
+                     "ensemble_state_rel_diff": float(np.max(np.abs(xa - xb)[keep] / np.abs(xb[keep])))}
+    return ratio, lower, acc
+
+
 def run_stationary(args, cfg, local):
     """--time-to-stationary: the stationary runs of the chosen forms alone."""
     import torch
@@ -829,23 +856,7 @@ def run_stationary(args, cfg, local):
     if args.tts_batch > 0:
         out = stationary_batch_runs(cfg, forms, args.max_periods, args.tts_batch, args.ml_weights, args.alpha_ml,
                                     args.criterion)
-        d = out.get("fp64")
-        full = lambda r: r is not None and r["stationary_cells"] == r["cells"]
-        ratio, lower, acc = {}, {}, {}
-        for name in ("fused", "fused_ml"):
-            f = out.get(name)
-            if not full(f) or d is None:
-                continue
-            if full(d):
-                ratio[name] = d["wall_s"] / f["wall_s"]
-                a, b = np.asarray(f["ensemble_window_means"]["p"]), np.asarray(d["ensemble_window_means"]["p"])
-                xa = np.asarray(f["ensemble_window_means"]["x_abs"])
-                xb = np.asarray(d["ensemble_window_means"]["x_abs"])
-                keep = np.abs(xb) > 1e-3 * np.max(np.abs(xb))
-                acc[name] = {"ensemble_power_rel_diff": float(np.max(np.abs(a - b) / np.abs(b))),
-                             "ensemble_state_rel_diff": float(np.max(np.abs(xa - xb)[keep] / np.abs(xb[keep])))}
-            else:
-                lower[name] = d["wall_s"] / f["wall_s"]
+        ratio, lower, acc = tts_batch_ratios(out)
         line = {"metric": "time to a stationary state of a batch of cells, fused FP32 (+ proposal) vs plain FP64 PIC, "
                           "1 B300",
                 "time_to_stationary_batched": {
